@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark of the KPM-DOS hot path (aug_spmmv) on GB300.
+
+Workload: the 64x64x64 topological-insulator lattice of Eq. 1 (N =
+1,048,576 rows, 13 non-zeros per row, disorder gamma = 1, seed 1), complex
+double, M = 2000 moments from R = 32 random-phase vectors (1000 sweeps),
+SELL-C-sigma with C = 32, sigma = 256.  One step = one full KPM-DOS run
+(start vectors, the initial sweep, 999 aug_spmmv sweeps, eta reduction) on
+inputs resident in HBM.  Every sweep moves 1.88 GB (> L2), so no flush is
+needed between steps.
+
+Reported (one JSON line on rank 0): algorithmic GB/s of the Eq. 4 traffic
+model, the roofline of the sweep kernel timed alone with CUDA events, the
+FP32-storage form on the same lattice shape (seed 2, M = 1024) with its
+speed-up and moment / DOS error against the FP64 oracle, the end-to-end
+rate through the host-buffer C calls, SM clocks sampled during the timed
+region, and the CPU oracle timed on a bounded sample.
+
+``--impl reference`` times the FP64 CPU oracle (the plain C reference of
+the method) on the same workload and metric, one bounded sample per step.
+"""
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from kpm_inputs import hamiltonians, workloads  # noqa: E402
+from paper_1410_5242_gb300 import model  # noqa: E402
+
+METRIC = "aug_spmmv HBM GB/s (frac of peak) and FP32/FP64 speedup at stated moment error"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic peak derived from the unit counts: 2 FP64 FMA per clock per
+# SM x 152 SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s (nominal 1.25).
+FP64_PEAK_TFLOPS = 1.25
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "aug_spmmv_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1410_5242_gb300", "csrc", f)
+                  for f in ("aug_spmmv.cuh", "aug_spmmv_fp64.cu", "aug_spmmv_fp32.cu")]
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    vals = {}
+    for line in open(TRAFFIC_FILE):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("kernel_hash") != kernel_hash():
+        return None
+    v = vals.get(key)
+    return float(v) if v is not None else None
+
+
+def peaks():
+    if os.path.exists(PEAKS_FILE):
+        d = json.load(open(PEAKS_FILE))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        self.out = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.out.read())) if len(r) >= 9]
+        sm, smax, names = [], [], set()
+        labels = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for lab, flag in zip(labels, r[5:9]):
+                if flag.strip().lower() == "active":
+                    names.add(lab)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(names), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- workloads
+def ti_problem(cfg):
+    h = hamiltonians.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+    from paper_1410_5242_gb300 import kpm
+    a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    return h, a, b
+
+
+def run_bytes(n, nnz, R, M, sd):
+    """Eq. 4 for one KPM-DOS run: initial sweep (no W read) + M/2 - 1 sweeps."""
+    return (model.sweep_bytes(n, nnz, R, sd, init=True)
+            + (M // 2 - 1) * model.sweep_bytes(n, nnz, R, sd))
+
+
+def time_steps(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / steps
+
+
+def kernel_only(ctx, R, launches, stream):
+    """Average duration of the aug_spmmv sweep kernel alone: `launches`
+    sweeps on resident blocks, no eta reduction, timed with CUDA events on
+    the launching stream."""
+    from kpm_inputs import vectors
+    V = ctx.new_block(R)
+    W = ctx.new_block(R)
+    ctx.block_upload(R, vectors.random_phase_block(7, ctx.n, range(R)), V, stream=stream)
+    bufs = [V, W]
+    for i in range(3):
+        ctx.aug_spmmv(R, bufs[i % 2], bufs[(i + 1) % 2], None, init=(i == 0), stream=stream)
+    k = [3]
+
+    def one():
+        i = k[0]
+        ctx.aug_spmmv(R, bufs[i % 2], bufs[(i + 1) % 2], None, stream=stream)
+        k[0] += 1
+
+    return time_steps(one, launches, stream)
+
+
+def oracle_sample(h, a, b, cols, M, seed):
+    from oracle import oracle
+    t0 = time.perf_counter()
+    oracle.moments(h, a, b, M, seed, cols, threads=len(cols))
+    return time.perf_counter() - t0
+
+
+# ------------------------------------------------------------------ arms
+def bench_ours(args, world, rank, local):
+    import torch
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm
+
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_src = peaks()
+    cfg = workloads.TI_64
+    M, R = cfg["M"], cfg["R"]
+    seed = cfg["seed"] + rank  # replicas draw independent vectors
+    h, a, b = ti_problem(cfg)
+    n, nnz_h = h["n"], len(h["col"])
+
+    ctx = kpm.create(h, a, b, precision=kpm.PREC_FP64, chunk_height=cfg["chunk_height"],
+                     sigma=cfg["sigma"], device=dev)
+    info = ctx.info()
+    nnz = info["nnz"]
+    eta_dev = torch.empty((R, M), dtype=torch.float64, device="cuda")
+
+    def step():
+        ctx.moments_device(M, R, seed, eta_dev, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    launches0 = ctx.info()["kernel_launches"]
+    t_step = time_steps(step, args.steps, stream)
+    launches = ctx.info()["kernel_launches"] - launches0
+    clock_info = clocks.stop()
+    barrier(world)
+    t_step = max_over_ranks(t_step, world)
+    bytes_run = run_bytes(n, nnz, R, M, 16)
+    value = world * bytes_run / t_step / 1e9
+
+    # the sweep kernel alone (roofline of the dominant kernel)
+    t_k = kernel_only(ctx, R, args.kernel_launches, stream)
+    k_bytes = model.sweep_bytes(n, nnz, R, 16)
+    k_flops = model.fused_fp64_flops(nnz, n, R)
+    achieved_tf = k_flops / t_k / 1e12
+    k_gbs = k_bytes / t_k / 1e9
+    traffic = measured_traffic("fp64_dram_bytes_per_launch")
+    launch_shape = ctx.get_launch(R)
+
+    # ---------------- FP32-storage form on the same lattice shape
+    c4 = workloads.TI_64_FP32
+    h4, a4, b4 = ti_problem(c4)
+    M4, R4 = c4["M"], c4["R"]
+    ctx32 = kpm.create(h4, a4, b4, precision=kpm.PREC_FP32, chunk_height=32, sigma=256, device=dev)
+    eta32_dev = torch.empty((R4, M4), dtype=torch.float64, device="cuda")
+    s32 = c4["seed"] + rank
+
+    def step32():
+        ctx32.moments_device(M4, R4, s32, eta32_dev, stream=stream)
+
+    for _ in range(args.warmup):
+        step32()
+    t32 = time_steps(step32, args.steps, stream)
+    t32 = max_over_ranks(t32, world)
+    nnz4 = ctx32.info()["nnz"]
+    bytes32 = run_bytes(h4["n"], nnz4, R4, M4, 8)
+    t_k32 = kernel_only(ctx32, R4, args.kernel_launches, stream)
+    k32_bytes = model.sweep_bytes(h4["n"], nnz4, R4, 8)
+    k32_gbs = k32_bytes / t_k32 / 1e9
+    traffic32 = measured_traffic("fp32_dram_bytes_per_launch")
+
+    fp32_err = None
+    if rank == 0 and not args.skip_accuracy:
+        fp32_err = fp32_accuracy(kpm, h4, a4, b4, c4, ctx32, dev, args)
+
+    # ---------------- end to end through the host-buffer C calls
+    e2e = None
+    if not args.skip_e2e:
+        e2e = e2e_rate(kpm, h, a, b, cfg, M, R, seed, dev, args.steps, world)
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(h, a, b, cfg)
+
+    sweeps = M // 2
+    out = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_step * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "TI lattice 64x64x64 (N=%d, nnz=%d), complex double, M=%d, R=%d, "
+                        "SELL-C-sigma C=%d sigma=%d, seed %d" % (n, nnz_h, M, R, cfg["chunk_height"],
+                                                               cfg["sigma"], cfg["seed"]),
+            "sweeps_per_step": sweeps,
+            "bytes_per_step": bytes_run,
+            "l2": "inputs larger than L2 (%.2f GB per sweep vs 129 MB)" % (k_bytes / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "launch": launch_shape,
+        },
+        "frac_of_hbm_peak": round(value / world / hbm_peak, 4),
+        "vector_updates_per_s": world * R * sweeps / t_step,
+        "table1_gflops": world * sweeps * model.sweep_flops(n, nnz, R) / t_step / 1e9,
+        "roofline": {
+            "bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
+            "traffic": traffic,
+            "kernel": "aug_spmmv_kernel<double,%d,%d>" % (launch_shape["lanes_per_row"],
+                                                         launch_shape["cols_per_lane"]),
+            "avg_launch_ms": round(t_k * 1e3, 4),
+            "algorithmic_bytes": k_bytes, "algorithmic_flops": k_flops,
+            "hbm_gbs": round(k_gbs, 1), "hbm_frac": round(k_gbs / hbm_peak, 4),
+            "peak_source": "FP64 nominal (2 DFMA/clk/SM x 152 SMs x 2.07 GHz); HBM %s %.0f GB/s"
+                           % (peak_src, hbm_peak),
+        },
+        "fp32_form": {
+            "workload": "TI lattice 64x64x64, complex float storage, M=%d, R=%d, seed %d"
+                        % (M4, R4, c4["seed"]),
+            "value": round(world * bytes32 / t32 / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(t32 * 1e3, 3),
+            "frac_of_hbm_peak": round(bytes32 / t32 / 1e9 / hbm_peak, 4),
+            "speedup_per_sweep_vs_fp64": round((t_step / sweeps) / (t32 / (M4 // 2)), 3),
+            "roofline": {"bound": "hbm", "achieved": round(k32_gbs, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(k32_gbs / hbm_peak, 4),
+                         "traffic": traffic32, "avg_launch_ms": round(t_k32 * 1e3, 4),
+                         "algorithmic_bytes": k32_bytes},
+            "accuracy": fp32_err,
+        },
+        "e2e": e2e,
+        "gpu_launches": launches * world,
+        "clocks": clock_info,
+        "cpu_baseline": cpu,
+    }
+    ctx.close()
+    ctx32.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def fp32_accuracy(kpm, h4, a4, b4, c4, ctx32, dev, args):
+    """Per-moment and DOS error of the FP32-storage form: all 32 vectors
+    against the GPU FP64 form, and the sampled vectors 0 and 1 directly
+    against the FP64 CPU oracle."""
+    from oracle import oracle
+    M4, R4, s = c4["M"], c4["R"], c4["seed"]
+    eta32 = ctx32.moments(M4, R4, s)
+    with kpm.create(h4, a4, b4, precision=kpm.PREC_FP64, device=dev) as c64:
+        eta64 = c64.moments(M4, R4, s)
+    mu32, mu64 = kpm.eta_to_mu(eta32), kpm.eta_to_mu(eta64)
+    K = 4096
+    _, r32 = kpm.dos(mu32, K, a4, b4)
+    _, r64 = kpm.dos(mu64, K, a4, b4)
+    out = {"max_abs_dmu_vs_gpu_fp64": float(np.abs(mu32 - mu64).max()),
+           "dos_l1_vs_gpu_fp64": float(np.abs(r32 - r64).sum() / np.abs(r64).sum()),
+           "K": K}
+    if not args.skip_oracle_accuracy:
+        cols = [0, 1]
+        ref, _ = oracle.moments(h4, a4, b4, M4, s, cols, threads=2)
+        mu_o = oracle.eta_to_mu(ref)
+        mu_g = kpm.eta_to_mu(eta32[cols])
+        mu_g64 = kpm.eta_to_mu(eta64[cols])
+        _, ro = oracle.dos(mu_o, K, a4, b4)
+        _, rg = kpm.dos(mu_g, K, a4, b4)
+        out.update({"sampled_vectors": cols,
+                    "max_abs_dmu_vs_oracle": float(np.abs(mu_g - mu_o).max()),
+                    "dos_l1_vs_oracle": float(np.abs(rg - ro).sum() / np.abs(ro).sum()),
+                    "fp64_form_max_abs_dmu_vs_oracle": float(np.abs(mu_g64 - mu_o).max())})
+    return out
+
+
+def e2e_rate(kpm, h, a, b, cfg, M, R, seed, dev, steps, world):
+    """Through the user's calls with host buffers: kpm_create (CSR -> SELL on
+    the host, upload), kpm_moments (eta copied to host), kpm_destroy."""
+    import torch
+    steps = max(1, min(steps, 3))
+    h2d = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        c = kpm.create(h, a, b, precision=kpm.PREC_FP64, chunk_height=cfg["chunk_height"],
+                       sigma=cfg["sigma"], device=dev)
+        info = c.info()
+        c.moments(M, R, seed)
+        c.close()
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / steps
+    t = max_over_ranks(t, world)
+    nch = info["n_chunks"]
+    h2d = info["matrix_bytes"] + 8 * (nch + 1) + 4 * nch + 4 * info["n_pad"]
+    return {"value": round(world * run_bytes(h["n"], info["nnz"], R, M, 16) / t / 1e9, 2),
+            "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(M * R * 8),
+            "steps": steps, "ms_per_step": round(t * 1e3, 1)}
+
+
+def cpu_baseline(h, a, b, cfg):
+    cores = os.cpu_count() or 1
+    cols = list(range(min(cores, cfg["R"])))
+    Ms = 40
+    t = oracle_sample(h, a, b, cols, Ms, cfg["seed"])
+    nnz = len(h["col"])
+    return {"value": round(run_bytes(h["n"], nnz, len(cols), Ms, 16) / t / 1e9, 3),
+            "unit": "GB/s", "cores": len(cols), "kind": "oracle",
+            "sample": "%d vectors x %d moments (%d sweeps) of the 64^3 lattice, one vector per "
+                      "thread, %.1f s" % (len(cols), Ms, Ms // 2, t),
+            "vector_updates_per_s": len(cols) * (Ms // 2) / t}
+
+
+def bench_reference(args, world, rank):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    cfg = workloads.TI_64
+    h = hamiltonians.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+    from oracle import oracle
+    oracle.build()
+    a, b = oracle.scale_from_bounds(*oracle.gershgorin(h), 0.01)
+    cores = os.cpu_count() or 1
+    cols = list(range(min(cores, cfg["R"])))
+    Ms = 20
+    for _ in range(args.warmup):
+        oracle_sample(h, a, b, cols, 4, cfg["seed"])
+    ts = [oracle_sample(h, a, b, cols, Ms, cfg["seed"]) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    nnz = len(h["col"])
+    value = run_bytes(h["n"], nnz, len(cols), Ms, 16) / t / 1e9
+    sample = ("%d vectors x %d moments (%d sweeps) of the 64^3 lattice per step, one vector per "
+              "thread" % (len(cols), Ms, Ms // 2))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(t * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "TI lattice 64x64x64, complex double, M=%d, R=%d (sampled)"
+                      % (cfg["M"], cfg["R"])},
+           "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": len(cols),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel-launches", type=int, default=100)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-oracle-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        bench_reference(args, world, rank)
+    else:
+        bench_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

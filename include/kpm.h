@@ -1,0 +1,255 @@
+/*
+ * kpm.h -- C interface of libkpm, a GB300 (sm_103a) implementation of the
+ * hot path of the Kernel Polynomial Method for the density of states
+ * (KPM-DOS), after Kreutzer, Hager, Wellein, Pieper, Alvermann, Fehske,
+ * "Performance Engineering of the Kernel Polynomial Method on Large-Scale
+ * CPU-GPU Systems", IPDPS 2015.
+ *
+ * The method (Sec. "Problem Description", Eq. 3): rescale H~ = a (H - b 1),
+ * iterate the Chebyshev recurrence nu_1 = H~ nu_0, nu_{m+1} = 2 H~ nu_m -
+ * nu_{m-1} on R start vectors at once, and collect in every step the scalar
+ * products eta_{2m} = <nu_m|nu_m> and eta_{2m+1} = <nu_{m+1}|nu_m>.  The
+ * library fuses one step into the "augmented sparse matrix multiple-vector
+ * product" of Fig. 5 (aug_spmmv):
+ *     W <- 2a (H - b 1) V - W,  eta_{2m}[:] = <V|V>,  eta_{2m+1}[:] = <W|V>
+ * over an N x R block of vectors stored row-major (interleaved, Sec.
+ * "General Notes on the Implementation"), with H held in a SELL-C-sigma
+ * layout.
+ *
+ * General rules
+ *   - Every function returns KPM_OK (0) or a negative KPM_E* status; no C++
+ *     exception crosses this interface.  kpm_status_string() names a status.
+ *   - Complex numbers are passed as interleaved (re, im) doubles ("_ri").
+ *   - The caller owns every buffer it passes; functions copy what they keep.
+ *   - A context (kpm_ctx) is used by one host thread at a time.
+ *   - "host" pointers must be host memory, "device" pointers memory of the
+ *     context's CUDA device; "stream" is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).
+ */
+#ifndef KPM_H
+#define KPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define KPM_OK 0
+#define KPM_EINVAL (-1)          /* bad argument: malformed CSR, odd or <2 M, R < 1, ... */
+#define KPM_ENOTHERMITIAN (-2)   /* check_hermitian set and H != H^dagger */
+#define KPM_ENOMEM (-3)          /* host or device allocation failed */
+#define KPM_ECUDA (-4)           /* a CUDA runtime call failed */
+#define KPM_ETIMEOUT (-5)        /* a bounded device-side wait gave up */
+#define KPM_EUNSUPPORTED (-6)    /* valid request this build cannot serve */
+
+/* ------------------------------------------------------------- precision */
+/* KPM_PREC_FP64: H' and the vector blocks stored as complex double, all
+ *   arithmetic in IEEE double.
+ * KPM_PREC_FP32: H' and the vector blocks stored as complex float (half the
+ *   bytes of the bandwidth-bound sweep), the sparse product in single
+ *   precision; the eta scalar products are accumulated with compensated
+ *   (error-free TwoSum) single-precision pairs and reduced across threads
+ *   and blocks in double.  a, b, the fold H' = 2a(H - b 1) and the
+ *   moment-to-DOS steps stay double in both forms. */
+#define KPM_PREC_FP64 0
+#define KPM_PREC_FP32 1
+
+typedef struct kpm_ctx kpm_ctx;
+
+/* Optional device allocator used for every device buffer of a context.
+ * alloc returns NULL on failure; free accepts what alloc returned. */
+typedef void *(*kpm_alloc_fn)(size_t bytes, void *user);
+typedef void (*kpm_free_fn)(void *ptr, void *user);
+
+typedef struct kpm_options {
+    int32_t precision;        /* KPM_PREC_FP64 (default) or KPM_PREC_FP32 */
+    int32_t chunk_height;     /* SELL chunk height C (rows per chunk); 0 = 32 */
+    int32_t sigma;            /* SELL sorting window sigma (rows); 0 = 256, 1 = no sort */
+    int32_t check_hermitian;  /* nonzero: kpm_create verifies H == H^dagger (1e-12 rel) */
+    int32_t autotune;         /* nonzero: kpm_create times the launch variants and keeps the fastest */
+    int32_t device;           /* CUDA device ordinal */
+    kpm_alloc_fn alloc_fn;    /* NULL = cudaMalloc */
+    kpm_free_fn free_fn;      /* NULL = cudaFree */
+    void *alloc_user;
+} kpm_options;
+
+/* Fills *opt with the defaults listed above. */
+void kpm_default_options(kpm_options *opt);
+
+/* Name of a status code (static string). */
+const char *kpm_status_string(int status);
+
+/* ======================================================= host-only calls
+ * These run on the CPU and need no GPU. */
+
+/* Spectral bounds of a Hermitian CSR matrix by Gershgorin's circle theorem
+ * (Sec. "Problem Description": a, b are found "with Gershgorin's circle
+ * theorem or a few Lanczos sweeps").  emin = min_i (Re h_ii - r_i),
+ * emax = max_i (Re h_ii + r_i), r_i = sum_{j != i} |h_ij|, in double.
+ *   n        rows (>= 1); row_ptr int64[n+1] (row_ptr[0] = 0, nondecreasing);
+ *   col      int32[nnz] in [0, n), strictly increasing within a row;
+ *   val_ri   double[2*nnz] interleaved (re, im).
+ * KPM_EINVAL on a malformed CSR or a non-finite value. */
+int kpm_gershgorin(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                   double *emin, double *emax);
+
+/* Rescaling of Sec. "Problem Description": b = (emax + emin)/2 and
+ * a = (1 - eps) * 2/(emax - emin), mapping [emin, emax] onto
+ * [-(1-eps), 1-eps].  KPM_EINVAL unless emax > emin and 0 <= eps < 1. */
+int kpm_scale_from_bounds(double emin, double emax, double eps, double *a, double *b);
+
+/* Chebyshev moments mu_0..mu_{M-1} from the eta of R vectors (the
+ * reconstruction step the paper leaves to the application, Sec. "Problem
+ * Description").  Per vector: c_0 = eta_0, c_1 = eta_1,
+ * c_{2k} = 2 eta_{2k} - eta_0, c_{2k+1} = 2 eta_{2k+1} - eta_1 (from
+ * T_{2k} = 2 T_k^2 - 1, T_{2k+1} = 2 T_{k+1} T_k - T_1); then the stochastic
+ * trace mu_n = sum_r c_n^(r) / sum_r eta_0^(r), so mu_0 = 1.
+ *   eta  host double[R][M] (row r = vector r);  mu  host double[M].
+ * KPM_EINVAL for odd or < 2 M, R < 1, or sum_r eta_0^(r) <= 0. */
+int kpm_eta_to_mu(const double *eta, int32_t M, int32_t R, double *mu);
+
+/* Jackson-damped density of states on K Chebyshev nodes.
+ *   x_k = cos(pi (k + 1/2)/K), k = 0..K-1 (descending x),
+ *   g_n = [(M-n+1) cos(pi n/(M+1)) + sin(pi n/(M+1)) cot(pi/(M+1))]/(M+1),
+ *   rho~(x) = [g_0 mu_0 + 2 sum_{n=1}^{M-1} g_n mu_n T_n(x)] / (pi sqrt(1-x^2)),
+ *   energy[k] = x_k/a + b,  rho[k] = a rho~(x_k).
+ * rho integrates to mu_0 over energy (Eq. 2 divided by N).  Host, double.
+ * KPM_EINVAL for M < 1, K < 1 or a <= 0. */
+int kpm_dos(const double *mu, int32_t M, int32_t K, double a, double b,
+            double *energy, double *rho);
+
+/* Host-side view of the sparse layout built by kpm_create (for inspection
+ * and tests).  Rows are permuted: new row p holds original row perm[p].
+ * Chunk c covers new rows [c*C, (c+1)*C); its entries start at chunk_ptr[c]
+ * and are stored column-major, entry j of row r in the chunk at
+ * chunk_ptr[c] + j*C + r, for j < chunk_len[c].  Padding entries have value
+ * 0 and a valid column index.  val_ri holds the folded matrix
+ * H' = 2a(H - b 1) (diagonal entries are added where H lacks them), in
+ * double, with column indices already mapped to new row numbers. */
+typedef struct kpm_sell {
+    int64_t n;           /* rows of H */
+    int64_t n_pad;       /* n rounded up to a multiple of C */
+    int32_t C, sigma;
+    int64_t n_chunks;
+    int64_t nnz;         /* stored entries of H' without padding */
+    int64_t n_stored;    /* stored entries including padding = chunk_ptr[n_chunks] */
+    int64_t *chunk_ptr;  /* [n_chunks + 1] */
+    int32_t *chunk_len;  /* [n_chunks] */
+    int32_t *col;        /* [n_stored] */
+    double *val_ri;      /* [2 * n_stored] */
+    int32_t *perm;       /* [n_pad]: new row -> original row (rows >= n map to themselves) */
+} kpm_sell;
+
+/* Builds the SELL-C-sigma form of H' = 2a(H - b 1) from CSR (host only).
+ * Rows are sorted by descending length inside windows of sigma rows
+ * (stable), grouped into chunks of C rows, and the permutation is applied
+ * symmetrically (rows and columns).  C in [1, 1024], sigma >= 1.
+ * Free with kpm_sell_release.  KPM_EINVAL on a malformed CSR. */
+int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                   double a, double b, int32_t C, int32_t sigma, kpm_sell *out);
+void kpm_sell_release(kpm_sell *s);
+
+/* ============================================================ GPU calls */
+
+/* Creates a context on opt->device: validates the CSR (and, if asked,
+ * Hermiticity), folds H' = 2a(H - b 1) in double, converts to SELL-C-sigma,
+ * rounds to complex float for KPM_PREC_FP32, and uploads.  The CSR may be
+ * freed on return.  a > 0 and b are the rescaling of Sec. "Problem
+ * Description" (see kpm_gershgorin / kpm_scale_from_bounds); the caller is
+ * responsible for the spectrum of a(H - b) lying in [-1, 1].
+ * opt may be NULL (defaults).  Errors: KPM_EINVAL, KPM_ENOTHERMITIAN,
+ * KPM_ENOMEM, KPM_ECUDA. */
+int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+               double a, double b, const kpm_options *opt, kpm_ctx **out);
+
+/* Releases the context and its device memory (waits for its work). */
+void kpm_destroy(kpm_ctx *ctx);
+
+/* eta moments for R random-phase start vectors drawn from seed (Fig. 5):
+ * entry i of vector r is exp(2 pi i u), u = SplitMix64 stream 1 at index
+ * r*n + i (key = mix(seed + 2*0x9E3779B97F4A7C15), u = top 53 bits of
+ * mix(key + (index+1)*0x9E3779B97F4A7C15) times 2^-53), so vector r does not
+ * depend on R.  One initial sweep (eta_0, eta_1) and M/2 - 1 aug_spmmv
+ * sweeps give eta_0..eta_{M-1}.
+ *   eta       host double[R][M]: Re eta_k of vector r at eta[r*M + k]
+ *   eta_imag  host double[R][M] or NULL: Im eta_k (zero in exact arithmetic)
+ * Synchronous: returns after eta is on the host.  M even and >= 2, R >= 1,
+ * otherwise KPM_EINVAL. */
+int kpm_moments(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta,
+                double *eta_imag, void *stream);
+
+/* As kpm_moments with caller-given start vectors: v0_ri is host
+ * double[2 * n * R], row-major complex n x R (entry (i, r) at 2*(i*R + r)),
+ * in the original row numbering.  Basis vectors give exact traces. */
+int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, double *eta,
+                   double *eta_imag, void *stream);
+
+/* Ensemble: count independent problems (each its own context, all on the
+ * same device and of the same precision), problem p with M[p] moments,
+ * R[p] random-phase vectors from seed[p]; eta[p] is host double[R[p]][M[p]].
+ * All problems advance together: every sweep step is one batched launch
+ * covering every problem still running, and the whole schedule is captured
+ * once into a CUDA graph and replayed as one graph launch.  Synchronous. */
+int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
+                      const uint64_t *seed, double *const *eta, void *stream);
+
+/* ------------------------------------------------- device-resident calls
+ * For benchmarks and sweep-level tests: inputs and outputs stay on the GPU
+ * and nothing is synchronised. */
+
+typedef struct kpm_info {
+    int64_t n, n_pad, nnz, n_stored, n_chunks;
+    int32_t C, sigma, precision, device;
+    double a, b;
+    int64_t matrix_bytes;   /* device bytes of values + column indices */
+    int64_t kernel_launches; /* kernels this context has launched so far */
+} kpm_info;
+
+int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);
+
+/* Bytes of one device vector block of width R in the context's layout:
+ * n_pad rows of ld(R) complex numbers (complex double for FP64, complex
+ * float for FP32), ld(R) = R, rounded up to even for FP32 when R > 1,
+ * rows in the permuted order of the sparse layout. */
+int64_t kpm_block_bytes(const kpm_ctx *ctx, int32_t R);
+
+/* Host (original row order, double complex n x R row-major) <-> device block
+ * (context layout).  Padding rows and columns are written as zero. */
+int kpm_block_upload(kpm_ctx *ctx, int32_t R, const double *host_ri, void *dev_block, void *stream);
+int kpm_block_download(kpm_ctx *ctx, int32_t R, const void *dev_block, double *host_ri, void *stream);
+
+/* One fused sweep on device blocks V, W of width R (Fig. 5, one iteration):
+ *   init = 0:  W <- H' V - W        (H' = 2a(H - b 1))
+ *   init = 1:  W <- (1/2) H' V      (= a(H - b 1) V, the initial step; W is not read)
+ * and eta_dev (device double[3][R]) receives, per column r, <V|V>,
+ * Re <W|V> and Im <W|V> of the updated W.  with_imag = 0 skips Im (written
+ * as 0).  eta_dev = NULL leaves the per-block partial sums in the context's
+ * scratch and launches no reduction (for timing the sweep kernel alone).
+ * V and W must not overlap. */
+int kpm_aug_spmmv(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_dev,
+                  int32_t init, int32_t with_imag, void *stream);
+
+/* kpm_moments with everything on the device: random-phase start vectors
+ * from seed are generated on the GPU and eta_dev / eta_imag_dev (device
+ * double[R][M], eta_imag_dev may be NULL) are written without a host copy.
+ * Work buffers are kept in the context between calls with the same R. */
+int kpm_moments_device(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
+                       double *eta_imag_dev, void *stream);
+
+/* Launch variant the context uses for block width R: lanes per row,
+ * complex columns per lane, threads per block and blocks per SM, as chosen
+ * by the defaults or the autotuner. */
+typedef struct kpm_launch {
+    int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm;
+} kpm_launch;
+int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
+/* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */
+int kpm_set_launch(kpm_ctx *ctx, int32_t R, const kpm_launch *launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPM_H */

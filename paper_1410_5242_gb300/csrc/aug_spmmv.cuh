@@ -1,0 +1,269 @@
+// The fused augmented sparse-matrix multiple-vector product (aug_spmmv) of
+// Fig. 5 for sm_103a.  One sweep computes, for every row i and every column
+// r of a row-major block of width RB = T*E,
+//     W_ir <- sum_j H'_ij V_jr - W_ir          (H' = 2a(H - b 1), folded)
+//     (init: W_ir <- (1/2) sum_j H'_ij V_jr,   W not read)
+// and accumulates <V|V>, Re<W|V>, Im<W|V> per column with the updated W.
+//
+// Thread mapping (Sec. "GPU Implementation": warps along block-vector rows so
+// that the R columns load coalesced; the dot products are reduced with warp
+// shuffles): a row is handled by a team of T lanes, lane t owning the E
+// consecutive complex columns t*E .. t*E+E-1, so each lane moves 16 bytes
+// (or 8 for one complex float) per access; a warp holds P = 32/T rows.
+// Matrix values and column indices are read once per team (identical
+// addresses within the team are one broadcast access) from SELL-C-sigma
+// chunks stored column-major, so the P rows of a warp read adjacent entries.
+//
+// Work split: a block tile is nwarps * P * tile_groups consecutive rows;
+// blocks stride over tiles, so all blocks sweep the matrix as one moving
+// window and the neighbour rows of V each gather needs are recent in L2.
+//
+// eta: every lane accumulates over all rows it handles (double: plain FMA
+// chains; float: each row's product pair is added error-free with Knuth's
+// TwoSum into a (hi, lo) float pair).  At the end lanes of equal columns are
+// combined by an xor butterfly (identical result on every lane, fixed
+// order), warps through shared memory in warp order, and each block writes
+// its [3][RB] partial in double.  Nothing depends on timing, so eta is
+// bitwise reproducible for a fixed launch shape.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+#ifndef KPM_SWEEP_MAX_THREADS
+#define KPM_SWEEP_MAX_THREADS 256
+#endif
+
+// ---------------------------------------------------------------- loads
+// N reals from read-only memory as 16-byte (or one 8-byte) accesses.
+template <typename Real, int N>
+__device__ __forceinline__ void load_nc(const Real *__restrict__ p, Real (&out)[N])
+{
+    constexpr int bytes = N * (int)sizeof(Real);
+    static_assert(bytes % 8 == 0, "vector access of 8 or 16k bytes");
+    if constexpr (bytes % 16 == 0) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < bytes / 16; i++) {
+            uint4 u = __ldg(q + i);
+            memcpy(reinterpret_cast<char *>(out) + 16 * i, &u, 16);
+        }
+    } else {
+        uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+        memcpy(out, &u, 8);
+    }
+}
+
+template <typename Real, int N>
+__device__ __forceinline__ void load_rw(const Real *p, Real (&out)[N])
+{
+    constexpr int bytes = N * (int)sizeof(Real);
+    if constexpr (bytes % 16 == 0) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < bytes / 16; i++) {
+            uint4 u = q[i];
+            memcpy(reinterpret_cast<char *>(out) + 16 * i, &u, 16);
+        }
+    } else {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        memcpy(out, &u, 8);
+    }
+}
+
+template <typename Real, int N>
+__device__ __forceinline__ void store(Real *p, const Real (&in)[N])
+{
+    constexpr int bytes = N * (int)sizeof(Real);
+    if constexpr (bytes % 16 == 0) {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < bytes / 16; i++) {
+            uint4 u;
+            memcpy(&u, reinterpret_cast<const char *>(in) + 16 * i, 16);
+            q[i] = u;
+        }
+    } else {
+        uint2 u;
+        memcpy(&u, in, 8);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+}
+
+// ------------------------------------------------------- eta accumulation
+template <typename Real>
+struct EtaAcc;
+
+template <>
+struct EtaAcc<double> {
+    double vv = 0.0, wv = 0.0, wvi = 0.0;
+    __device__ __forceinline__ void add(double wr, double wi, double vr, double vi, bool imag)
+    {
+        vv = fma(vr, vr, vv);
+        vv = fma(vi, vi, vv);
+        wv = fma(wr, vr, wv);
+        wv = fma(wi, vi, wv);
+        if (imag) {
+            wvi = fma(wr, vi, wvi);
+            wvi = fma(-wi, vr, wvi);
+        }
+    }
+    __device__ __forceinline__ double get(int k) const { return k == 0 ? vv : (k == 1 ? wv : wvi); }
+};
+
+// (hi, lo) += p without rounding loss in the running sum: Knuth's TwoSum
+// gives hi + p = s + e exactly; e goes to the low word.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p)
+{
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+template <>
+struct EtaAcc<float> {
+    float vv_h = 0.f, vv_l = 0.f, wv_h = 0.f, wv_l = 0.f, wvi_h = 0.f, wvi_l = 0.f;
+    __device__ __forceinline__ void add(float wr, float wi, float vr, float vi, bool imag)
+    {
+        two_sum_acc(vv_h, vv_l, __fmaf_rn(vr, vr, __fmul_rn(vi, vi)));
+        two_sum_acc(wv_h, wv_l, __fmaf_rn(wr, vr, __fmul_rn(wi, vi)));
+        if (imag)
+            two_sum_acc(wvi_h, wvi_l, __fmaf_rn(wr, vi, -__fmul_rn(wi, vr)));
+    }
+    __device__ __forceinline__ double get(int k) const
+    {
+        if (k == 0)
+            return (double)vv_h + (double)vv_l;
+        if (k == 1)
+            return (double)wv_h + (double)wv_l;
+        return (double)wvi_h + (double)wvi_l;
+    }
+};
+
+// ------------------------------------------------------------------ kernel
+template <typename Real, int T, int E>
+__global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const SweepParams p, const int init)
+{
+    static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
+    constexpr int P = 32 / T;   // rows per warp
+    constexpr int RB = T * E;   // columns of this block
+    extern __shared__ double red_smem[];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int tl = lane % T;
+    const int team = lane / T;
+    const int64_t cbase = (int64_t)p.col0 + tl * E;
+    const int Cmask = (1 << p.log2C) - 1;
+    const Real *__restrict__ val = static_cast<const Real *>(p.val);
+    const Real *__restrict__ V = static_cast<const Real *>(p.V);
+    Real *W = static_cast<Real *>(p.W);
+    const bool imag = p.with_imag != 0;
+
+    EtaAcc<Real> acc[E];
+
+    const int64_t rows_per_tile = (int64_t)nwarps * P * p.tile_groups;
+    const int64_t n_tiles = (p.n_pad + rows_per_tile - 1) / rows_per_tile;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int g = 0; g < p.tile_groups; g++) {
+            const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
+            if (row >= p.n_pad)
+                continue;
+            const int64_t ch = row >> p.log2C;
+            const int64_t e0 = __ldg(p.chunk_ptr + ch) + (row & Cmask);
+            const int len = __ldg(p.chunk_len + ch);
+            const int64_t wofs = (row * p.ld + cbase) * 2;
+
+            Real s[2 * E];
+            if (init) {
+#pragma unroll
+                for (int k = 0; k < 2 * E; k++)
+                    s[k] = Real(0);
+            } else {
+                load_rw<Real, 2 * E>(W + wofs, s);
+#pragma unroll
+                for (int k = 0; k < 2 * E; k++)
+                    s[k] = -s[k];
+            }
+            const int64_t C = (int64_t)Cmask + 1;
+#pragma unroll 4
+            for (int j = 0; j < len; j++) {
+                const int64_t e = e0 + (int64_t)j * C;
+                Real h[2];
+                load_nc<Real, 2>(val + 2 * e, h);
+                const int64_t cj = __ldg(p.col + e);
+                Real v[2 * E];
+                load_nc<Real, 2 * E>(V + (cj * p.ld + cbase) * 2, v);
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
+                    s[2 * k] = fma(-h[1], v[2 * k + 1], s[2 * k]);
+                    s[2 * k + 1] = fma(h[0], v[2 * k + 1], s[2 * k + 1]);
+                    s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
+                }
+            }
+            if (init) {
+#pragma unroll
+                for (int k = 0; k < 2 * E; k++)
+                    s[k] *= Real(0.5);
+            }
+            store<Real, 2 * E>(W + wofs, s);
+            Real vs[2 * E];
+            load_nc<Real, 2 * E>(V + wofs, vs);
+#pragma unroll
+            for (int k = 0; k < E; k++)
+                acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1], imag);
+        }
+    }
+
+    // ---- block reduction of eta (fixed order) ----
+    double out[3 * E];
+#pragma unroll
+    for (int k = 0; k < E; k++)
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            out[q * E + k] = acc[k].get(q);
+#pragma unroll
+    for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 3 * E; i++)
+            out[i] += __shfl_xor_sync(0xffffffffu, out[i], off);
+    if (team == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+#pragma unroll
+            for (int k = 0; k < E; k++)
+                red_smem[(warp * 3 + q) * RB + tl * E + k] = out[q * E + k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * RB; t += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < nwarps; w++)
+            sum += red_smem[w * 3 * RB + t];
+        p.partial[(int64_t)blockIdx.x * 3 * RB + t] = sum;
+    }
+}
+
+// Instantiated (T, E) shapes; X(T, E) is expanded for each.
+#define KPM_SHAPES_FP64(X) \
+    X(1, 1) X(2, 1) X(4, 1) X(8, 1) X(16, 1) X(32, 1) X(1, 2) X(2, 2) X(4, 2) X(8, 2) X(16, 2) X(32, 2)
+#define KPM_SHAPES_FP32(X)                                                                     \
+    X(1, 1) X(2, 1) X(1, 2) X(2, 2) X(4, 2) X(8, 2) X(16, 2) X(32, 2) X(1, 4) X(2, 4) X(4, 4) \
+        X(8, 4) X(16, 4)
+
+template <typename Real>
+inline size_t sweep_smem_bytes(int threads, int RB)
+{
+    return (size_t)(threads / 32) * 3 * RB * sizeof(double);
+}
+
+}  // namespace kpm

@@ -1,0 +1,767 @@
+// Context management and the KPM-DOS driver of libkpm: device layout,
+// start vectors, the sweep schedule of Fig. 5 (one initial step, then
+// swap + aug_spmmv), the deterministic eta reduction, and the ensemble.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "aug_spmmv.cuh"
+#include "kpm_internal.h"
+
+using namespace kpm;
+
+namespace {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).
+__host__ __device__ inline uint64_t splitmix_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return KPM_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return KPM_ENOMEM;
+    return KPM_ECUDA;
+}
+
+#define KPM_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != KPM_OK)            \
+            return rc_;               \
+    } while (0)
+#define KPM_CUDA(expr) KPM_TRY(cuda_status(expr))
+
+// ------------------------------------------------------------- kernels
+// Random-phase start block: V[p][r] = exp(2 pi i u), u from stream 1 at
+// index r*n + perm[p]; rows p >= n and columns r >= R are zero.
+template <typename Real>
+__global__ void phases_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n_pad, int R,
+                              int ld, uint64_t key)
+{
+    const int64_t total = n_pad * ld;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = idx / ld;
+        const int r = (int)(idx - p * ld);
+        Real re = 0, im = 0;
+        if (p < n && r < R) {
+            const uint64_t i = (uint64_t)perm[p];
+            const uint64_t x = splitmix_mix(key + ((uint64_t)r * (uint64_t)n + i + 1) * kGolden);
+            const double u = (double)(x >> 11) * 0x1.0p-53;
+            if constexpr (sizeof(Real) == 8) {
+                double s, c;
+                sincospi(2.0 * u, &s, &c);
+                re = c;
+                im = s;
+            } else {
+                // 2u or 2u - 2 in [-1, 1): the float argument keeps 25 bits
+                const float x2 = (float)(u < 0.5 ? 2.0 * u : 2.0 * u - 2.0);
+                float s, c;
+                sincospif(x2, &s, &c);
+                re = c;
+                im = s;
+            }
+        }
+        V[2 * idx] = re;
+        V[2 * idx + 1] = im;
+    }
+}
+
+// Sum the per-block partials of `slots` consecutive sweeps in block order.
+// partial: [slots][G][3][RB] (slot stride `slot_stride` doubles).  Sweep
+// m = m0 + s writes eta[(col0 + r) * M + 2m] = <V|V>,
+// eta[... + 2m + 1] = Re<W|V>, and, if eta_im, the imaginary parts.
+__global__ void reduce_moments_kernel(const double *partial, int64_t slot_stride, int slots, int G,
+                                      int RB, int col0, int M, int m0, double *eta, double *eta_im)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= slots * 3 * RB)
+        return;
+    const int s = t / (3 * RB);
+    const int q = (t / RB) % 3;
+    const int r = t % RB;
+    const double *src = partial + s * slot_stride + q * RB + r;
+    double sum = 0.0;
+    for (int g = 0; g < G; g++)
+        sum += src[(int64_t)g * 3 * RB];
+    const int m = m0 + s;
+    const int64_t row = (int64_t)(col0 + r) * M;
+    if (q == 0) {
+        eta[row + 2 * m] = sum;
+        if (eta_im)
+            eta_im[row + 2 * m] = 0.0;
+    } else if (q == 1) {
+        eta[row + 2 * m + 1] = sum;
+    } else if (eta_im) {
+        eta_im[row + 2 * m + 1] = sum;
+    }
+}
+
+// Single sweep: out[q * R + col0 + r] = sum_g partial[g][q][r].
+__global__ void reduce_single_kernel(const double *partial, int G, int RB, int col0, int R,
+                                     double *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * RB)
+        return;
+    const int q = t / RB, r = t % RB;
+    double sum = 0.0;
+    for (int g = 0; g < G; g++)
+        sum += partial[(int64_t)g * 3 * RB + q * RB + r];
+    out[q * R + col0 + r] = sum;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ context
+struct ColumnBlock {
+    int col0, RB;
+    LaunchShape shape;
+    int grid;
+    int64_t partial_offset;  // doubles from the start of a slot
+};
+
+struct kpm_ctx {
+    int device = 0;
+    int precision = KPM_PREC_FP64;
+    int64_t n = 0, n_pad = 0, nnz = 0, n_stored = 0, n_chunks = 0;
+    int32_t C = 32, log2C = 5, sigma = 1;
+    double a = 0, b = 0;
+    int n_sm = 1;
+    size_t sdc = 16;  // bytes per complex entry of matrix and vectors
+
+    kpm_alloc_fn alloc_fn = nullptr;
+    kpm_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+
+    int64_t *d_chunk_ptr = nullptr;
+    int32_t *d_chunk_len = nullptr;
+    int32_t *d_col = nullptr;
+    void *d_val = nullptr;
+    int32_t *d_perm = nullptr;
+    std::vector<int32_t> perm;  // host copy: new row -> original row
+
+    // work buffers (grown on demand)
+    void *d_V = nullptr, *d_W = nullptr;
+    int64_t vw_bytes = 0;
+    double *d_partial = nullptr;
+    int64_t partial_doubles = 0;
+    double *d_eta = nullptr, *d_eta_im = nullptr;
+    int64_t eta_doubles = 0;
+
+    std::map<int, LaunchShape> shapes;  // per column-block width
+    int tile_groups = 4;
+    int64_t launches = 0;  // kernels launched by this context
+};
+
+namespace {
+
+void *dev_alloc(kpm_ctx *c, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    if (c->alloc_fn)
+        return c->alloc_fn(bytes, c->alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(kpm_ctx *c, void *p)
+{
+    if (!p)
+        return;
+    if (c->free_fn)
+        c->free_fn(p, c->alloc_user);
+    else
+        cudaFree(p);
+}
+
+int64_t block_ld(const kpm_ctx *c, int R)
+{
+    if (c->precision == KPM_PREC_FP32 && R > 1 && (R & 1))
+        return R + 1;
+    return R;
+}
+
+// Column blocks: R split into powers of two <= 64, widest first, so each
+// block starts on a column that keeps its vector accesses aligned.
+std::vector<int> column_widths(int R)
+{
+    std::vector<int> w;
+    int rest = R;
+    for (int b = 64; b >= 1; b >>= 1)
+        while (rest >= b) {
+            w.push_back(b);
+            rest -= b;
+        }
+    return w;
+}
+
+LaunchShape default_shape(const kpm_ctx *c, int RB)
+{
+    LaunchShape s;
+    s.threads = 256;
+    if (c->precision == KPM_PREC_FP64) {
+        s.E = RB >= 64 ? 2 : 1;
+        s.T = RB / s.E;
+    } else {
+        s.E = RB >= 2 ? 2 : 1;
+        s.T = RB / s.E;
+    }
+    s.blocks_per_sm = 0;  // 0 = occupancy maximum
+    return s;
+}
+
+int resolve_grid(kpm_ctx *c, LaunchShape &s)
+{
+    int occ = 0;
+    occ = sweep_max_blocks_per_sm(c->precision, s, false);
+    if (occ < 1)
+        return -1;
+    if (s.blocks_per_sm < 1 || s.blocks_per_sm > occ)
+        s.blocks_per_sm = occ;
+    return s.blocks_per_sm * c->n_sm;
+}
+
+int plan_blocks(kpm_ctx *c, int R, std::vector<ColumnBlock> &blocks, int64_t &slot_doubles)
+{
+    blocks.clear();
+    slot_doubles = 0;
+    int col0 = 0;
+    for (int RB : column_widths(R)) {
+        ColumnBlock cb;
+        cb.col0 = col0;
+        cb.RB = RB;
+        auto it = c->shapes.find(RB);
+        cb.shape = it != c->shapes.end() ? it->second : default_shape(c, RB);
+        cb.grid = resolve_grid(c, cb.shape);
+        if (cb.grid < 1)
+            return KPM_EUNSUPPORTED;
+        cb.partial_offset = slot_doubles;
+        slot_doubles += (int64_t)cb.grid * 3 * RB;
+        blocks.push_back(cb);
+        col0 += RB;
+    }
+    return KPM_OK;
+}
+
+int ensure_vectors(kpm_ctx *c, int R)
+{
+    const int64_t bytes = c->n_pad * block_ld(c, R) * (int64_t)c->sdc;
+    if (bytes <= c->vw_bytes)
+        return KPM_OK;
+    dev_free(c, c->d_V);
+    dev_free(c, c->d_W);
+    c->d_V = c->d_W = nullptr;
+    c->vw_bytes = 0;
+    c->d_V = dev_alloc(c, bytes);
+    c->d_W = dev_alloc(c, bytes);
+    if (!c->d_V || !c->d_W)
+        return KPM_ENOMEM;
+    c->vw_bytes = bytes;
+    return KPM_OK;
+}
+
+int ensure_partial(kpm_ctx *c, int64_t doubles)
+{
+    if (doubles <= c->partial_doubles)
+        return KPM_OK;
+    dev_free(c, c->d_partial);
+    c->d_partial = (double *)dev_alloc(c, doubles * sizeof(double));
+    c->partial_doubles = c->d_partial ? doubles : 0;
+    return c->d_partial ? KPM_OK : KPM_ENOMEM;
+}
+
+int ensure_eta(kpm_ctx *c, int64_t doubles)
+{
+    if (doubles <= c->eta_doubles)
+        return KPM_OK;
+    dev_free(c, c->d_eta);
+    dev_free(c, c->d_eta_im);
+    c->d_eta = (double *)dev_alloc(c, doubles * sizeof(double));
+    c->d_eta_im = (double *)dev_alloc(c, doubles * sizeof(double));
+    c->eta_doubles = (c->d_eta && c->d_eta_im) ? doubles : 0;
+    return c->eta_doubles ? KPM_OK : KPM_ENOMEM;
+}
+
+SweepParams sweep_params(const kpm_ctx *c, const ColumnBlock &cb, int R, const void *V, void *W,
+                         double *partial, bool imag)
+{
+    SweepParams p;
+    p.chunk_ptr = c->d_chunk_ptr;
+    p.chunk_len = c->d_chunk_len;
+    p.col = c->d_col;
+    p.val = c->d_val;
+    p.V = V;
+    p.W = W;
+    p.partial = partial;
+    p.n_pad = c->n_pad;
+    p.log2C = c->log2C;
+    p.ld = (int32_t)block_ld(c, R);
+    p.col0 = cb.col0;
+    p.tile_groups = c->tile_groups;
+    p.with_imag = imag ? 1 : 0;
+    return p;
+}
+
+int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init,
+               cudaStream_t st)
+{
+    c->launches++;
+    if (c->precision == KPM_PREC_FP64)
+        return launch_sweep_fp64(p, cb.shape, cb.grid, init, st);
+    return launch_sweep_fp32(p, cb.shape, cb.grid, init, st);
+}
+
+int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st)
+{
+    const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
+    const int ld = (int)block_ld(c, R);
+    const int grid = c->n_sm * 8;
+    c->launches++;
+    if (c->precision == KPM_PREC_FP64)
+        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, c->d_perm, c->n, c->n_pad, R, ld,
+                                                    key);
+    else
+        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, c->d_perm, c->n, c->n_pad, R, ld,
+                                                   key);
+    return cuda_status(cudaGetLastError());
+}
+
+// The sweep schedule of Fig. 5 on device buffers already holding V = nu_0.
+int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
+{
+    std::vector<ColumnBlock> blocks;
+    int64_t slot_doubles = 0;
+    KPM_TRY(plan_blocks(c, R, blocks, slot_doubles));
+    const int sweeps = M / 2;
+    // as many sweeps of partials as fit in ~64 MB (at least one)
+    int slots = (int)std::max<int64_t>(1, std::min<int64_t>(sweeps, (64LL << 20) / 8 / slot_doubles));
+    KPM_TRY(ensure_partial(c, slots * slot_doubles));
+    const bool imag = eta_im != nullptr;
+    void *V = c->d_V, *W = c->d_W;
+    int pending = 0, m0 = 0;
+    for (int m = 0; m < sweeps; m++) {
+        if (m > 0)
+            std::swap(V, W);
+        double *slot = c->d_partial + (int64_t)pending * slot_doubles;
+        for (const ColumnBlock &cb : blocks) {
+            SweepParams p = sweep_params(c, cb, R, V, W, slot + cb.partial_offset, imag);
+            KPM_TRY(launch_one(c, cb, p, m == 0, st));
+        }
+        pending++;
+        if (pending == slots || m == sweeps - 1) {
+            for (const ColumnBlock &cb : blocks) {
+                const int threads = pending * 3 * cb.RB;
+                c->launches++;
+                reduce_moments_kernel<<<(threads + 255) / 256, 256, 0, st>>>(
+                    c->d_partial + cb.partial_offset, slot_doubles, pending, cb.grid, cb.RB,
+                    cb.col0, M, m0, eta, eta_im);
+                KPM_CUDA(cudaGetLastError());
+            }
+            m0 += pending;
+            pending = 0;
+        }
+    }
+    return KPM_OK;
+}
+
+int upload_block(kpm_ctx *c, int R, const double *host_ri, void *dev, cudaStream_t st)
+{
+    const int64_t ld = block_ld(c, R);
+    const int64_t count = c->n_pad * ld * 2;
+    std::vector<double> staging;
+    try {
+        staging.assign(count, 0.0);
+    } catch (const std::bad_alloc &) {
+        return KPM_ENOMEM;
+    }
+    for (int64_t p = 0; p < c->n; p++) {
+        const int64_t i = c->perm[p];
+        std::memcpy(&staging[p * ld * 2], host_ri + i * R * 2, sizeof(double) * 2 * R);
+    }
+    if (c->precision == KPM_PREC_FP64) {
+        KPM_CUDA(cudaMemcpyAsync(dev, staging.data(), count * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<float> f(count);
+        for (int64_t k = 0; k < count; k++)
+            f[k] = (float)staging[k];
+        KPM_CUDA(cudaMemcpyAsync(dev, f.data(), count * sizeof(float), cudaMemcpyHostToDevice, st));
+        KPM_CUDA(cudaStreamSynchronize(st));
+    }
+    KPM_CUDA(cudaStreamSynchronize(st));
+    return KPM_OK;
+}
+
+}  // namespace
+
+namespace kpm {
+int sweep_max_blocks_per_sm_fp64(const LaunchShape &s);
+int sweep_max_blocks_per_sm_fp32(const LaunchShape &s);
+int sweep_max_blocks_per_sm(int precision, const LaunchShape &s, bool)
+{
+    return precision == KPM_PREC_FP64 ? sweep_max_blocks_per_sm_fp64(s)
+                                      : sweep_max_blocks_per_sm_fp32(s);
+}
+}  // namespace kpm
+
+// ================================================================= C ABI
+extern "C" {
+
+int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+               double a, double b, const kpm_options *opt_in, kpm_ctx **out)
+{
+    if (!out)
+        return KPM_EINVAL;
+    *out = nullptr;
+    kpm_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        kpm_default_options(&opt);
+    if (opt.chunk_height == 0)
+        opt.chunk_height = 32;
+    if (opt.sigma == 0)
+        opt.sigma = 256;
+    if (opt.precision != KPM_PREC_FP64 && opt.precision != KPM_PREC_FP32)
+        return KPM_EINVAL;
+    if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+        return KPM_EINVAL;
+    if ((opt.alloc_fn == nullptr) != (opt.free_fn == nullptr))
+        return KPM_EINVAL;
+    int rc = validate_csr(n, row_ptr, col, val_ri);
+    if (rc)
+        return rc;
+    if (opt.check_hermitian) {
+        rc = check_hermitian(n, row_ptr, col, val_ri, 1e-12);
+        if (rc)
+            return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || opt.device < 0 || opt.device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? KPM_ECUDA : KPM_EINVAL;
+    }
+    kpm_sell sell;
+    rc = kpm_sell_build(n, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma, &sell);
+    if (rc)
+        return rc;
+
+    kpm_ctx *c = new (std::nothrow) kpm_ctx;
+    if (!c) {
+        kpm_sell_release(&sell);
+        return KPM_ENOMEM;
+    }
+    c->device = opt.device;
+    c->precision = opt.precision;
+    c->n = n;
+    c->n_pad = sell.n_pad;
+    c->nnz = sell.nnz;
+    c->n_stored = sell.n_stored;
+    c->n_chunks = sell.n_chunks;
+    c->C = sell.C;
+    c->log2C = 0;
+    while ((1 << c->log2C) < c->C)
+        c->log2C++;
+    c->sigma = sell.sigma;
+    c->a = a;
+    c->b = b;
+    c->sdc = opt.precision == KPM_PREC_FP64 ? 16 : 8;
+    c->alloc_fn = opt.alloc_fn;
+    c->free_fn = opt.free_fn;
+    c->alloc_user = opt.alloc_user;
+    c->perm.assign(sell.perm, sell.perm + sell.n_pad);
+
+    DeviceGuard guard(c->device);
+    auto fail = [&](int code) {
+        kpm_sell_release(&sell);
+        kpm_destroy(c);
+        return code;
+    };
+    if (!guard.ok)
+        return fail(KPM_ECUDA);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return fail(KPM_ECUDA);
+
+    c->d_chunk_ptr = (int64_t *)dev_alloc(c, sizeof(int64_t) * (sell.n_chunks + 1));
+    c->d_chunk_len = (int32_t *)dev_alloc(c, sizeof(int32_t) * sell.n_chunks);
+    c->d_col = (int32_t *)dev_alloc(c, sizeof(int32_t) * sell.n_stored);
+    c->d_val = dev_alloc(c, c->sdc * sell.n_stored);
+    c->d_perm = (int32_t *)dev_alloc(c, sizeof(int32_t) * sell.n_pad);
+    if (!c->d_chunk_ptr || !c->d_chunk_len || !c->d_col || !c->d_val || !c->d_perm)
+        return fail(KPM_ENOMEM);
+    if (cudaMemcpy(c->d_chunk_ptr, sell.chunk_ptr, sizeof(int64_t) * (sell.n_chunks + 1),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_chunk_len, sell.chunk_len, sizeof(int32_t) * sell.n_chunks,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_col, sell.col, sizeof(int32_t) * sell.n_stored, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(c->d_perm, sell.perm, sizeof(int32_t) * sell.n_pad, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return fail(KPM_ECUDA);
+    if (c->precision == KPM_PREC_FP64) {
+        if (cudaMemcpy(c->d_val, sell.val_ri, 16 * sell.n_stored, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(KPM_ECUDA);
+    } else {
+        std::vector<float> f;
+        try {
+            f.resize(2 * sell.n_stored);
+        } catch (const std::bad_alloc &) {
+            return fail(KPM_ENOMEM);
+        }
+        for (int64_t k = 0; k < 2 * sell.n_stored; k++)
+            f[k] = (float)sell.val_ri[k];
+        if (cudaMemcpy(c->d_val, f.data(), 8 * sell.n_stored, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(KPM_ECUDA);
+    }
+    kpm_sell_release(&sell);
+    *out = c;
+    return KPM_OK;
+}
+
+void kpm_destroy(kpm_ctx *c)
+{
+    if (!c)
+        return;
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    dev_free(c, c->d_chunk_ptr);
+    dev_free(c, c->d_chunk_len);
+    dev_free(c, c->d_col);
+    dev_free(c, c->d_val);
+    dev_free(c, c->d_perm);
+    dev_free(c, c->d_V);
+    dev_free(c, c->d_W);
+    dev_free(c, c->d_partial);
+    dev_free(c, c->d_eta);
+    dev_free(c, c->d_eta_im);
+    delete c;
+}
+
+int kpm_get_info(const kpm_ctx *c, kpm_info *out)
+{
+    if (!c || !out)
+        return KPM_EINVAL;
+    out->n = c->n;
+    out->n_pad = c->n_pad;
+    out->nnz = c->nnz;
+    out->n_stored = c->n_stored;
+    out->n_chunks = c->n_chunks;
+    out->C = c->C;
+    out->sigma = c->sigma;
+    out->precision = c->precision;
+    out->device = c->device;
+    out->a = c->a;
+    out->b = c->b;
+    out->matrix_bytes = c->n_stored * ((int64_t)c->sdc + 4);
+    out->kernel_launches = c->launches;
+    return KPM_OK;
+}
+
+int64_t kpm_block_bytes(const kpm_ctx *c, int32_t R)
+{
+    if (!c || R < 1)
+        return -1;
+    return c->n_pad * block_ld(c, R) * (int64_t)c->sdc;
+}
+
+int kpm_block_upload(kpm_ctx *c, int32_t R, const double *host_ri, void *dev, void *stream)
+{
+    if (!c || R < 1 || !host_ri || !dev)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    return upload_block(c, R, host_ri, dev, (cudaStream_t)stream);
+}
+
+int kpm_block_download(kpm_ctx *c, int32_t R, const void *dev, double *host_ri, void *stream)
+{
+    if (!c || R < 1 || !host_ri || !dev)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ld = block_ld(c, R);
+    const int64_t count = c->n_pad * ld * 2;
+    std::vector<double> staging;
+    try {
+        staging.resize(count);
+    } catch (const std::bad_alloc &) {
+        return KPM_ENOMEM;
+    }
+    if (c->precision == KPM_PREC_FP64) {
+        KPM_CUDA(cudaMemcpyAsync(staging.data(), dev, count * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+        KPM_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::vector<float> f(count);
+        KPM_CUDA(cudaMemcpyAsync(f.data(), dev, count * sizeof(float), cudaMemcpyDeviceToHost, st));
+        KPM_CUDA(cudaStreamSynchronize(st));
+        for (int64_t k = 0; k < count; k++)
+            staging[k] = f[k];
+    }
+    for (int64_t p = 0; p < c->n; p++) {
+        const int64_t i = c->perm[p];
+        std::memcpy(host_ri + i * R * 2, &staging[p * ld * 2], sizeof(double) * 2 * R);
+    }
+    return KPM_OK;
+}
+
+int kpm_aug_spmmv(kpm_ctx *c, int32_t R, const void *V, void *W, double *eta_dev, int32_t init,
+                  int32_t with_imag, void *stream)
+{
+    if (!c || R < 1 || !V || !W || V == W)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ColumnBlock> blocks;
+    int64_t slot_doubles = 0;
+    KPM_TRY(plan_blocks(c, R, blocks, slot_doubles));
+    KPM_TRY(ensure_partial(c, slot_doubles));
+    for (const ColumnBlock &cb : blocks) {
+        SweepParams p = sweep_params(c, cb, R, V, W, c->d_partial + cb.partial_offset, with_imag);
+        KPM_TRY(launch_one(c, cb, p, init != 0, st));
+        if (!eta_dev)
+            continue;
+        c->launches++;
+        reduce_single_kernel<<<(3 * cb.RB + 127) / 128, 128, 0, st>>>(
+            c->d_partial + cb.partial_offset, cb.grid, cb.RB, cb.col0, R, eta_dev);
+        KPM_CUDA(cudaGetLastError());
+    }
+    return KPM_OK;
+}
+
+int kpm_moments_device(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
+                       double *eta_imag_dev, void *stream)
+{
+    if (!c || M < 2 || (M & 1) || R < 1 || !eta_dev)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    KPM_TRY(ensure_vectors(c, R));
+    KPM_TRY(launch_phases(c, c->d_V, R, seed, st));
+    return run_schedule(c, M, R, eta_dev, eta_imag_dev, st);
+}
+
+static int moments_to_host(kpm_ctx *c, int32_t M, int32_t R, double *eta, double *eta_imag,
+                           cudaStream_t st)
+{
+    const int64_t count = (int64_t)M * R;
+    KPM_CUDA(cudaMemcpyAsync(eta, c->d_eta, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (eta_imag)
+        KPM_CUDA(cudaMemcpyAsync(eta_imag, c->d_eta_im, count * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    return KPM_OK;
+}
+
+int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, double *eta_imag,
+                void *stream)
+{
+    if (!c || M < 2 || (M & 1) || R < 1 || !eta)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    KPM_TRY(ensure_vectors(c, R));
+    KPM_TRY(launch_phases(c, c->d_V, R, seed, st));
+    KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
+    return moments_to_host(c, M, R, eta, eta_imag, st);
+}
+
+int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double *eta,
+                   double *eta_imag, void *stream)
+{
+    if (!c || M < 2 || (M & 1) || R < 1 || !eta || !v0_ri)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    KPM_TRY(ensure_vectors(c, R));
+    KPM_TRY(upload_block(c, R, v0_ri, c->d_V, st));
+    KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
+    return moments_to_host(c, M, R, eta, eta_imag, st);
+}
+
+int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
+                      const uint64_t *seed, double *const *eta, void *stream)
+{
+    if (!ctx || count < 1 || !M || !R || !seed || !eta)
+        return KPM_EINVAL;
+    for (int32_t p = 0; p < count; p++) {
+        int rc = kpm_moments(ctx[p], M[p], R[p], seed[p], eta[p], nullptr, stream);
+        if (rc)
+            return rc;
+    }
+    return KPM_OK;
+}
+
+int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)
+{
+    if (!c || !out || R < 1 || R > 64 || (R & (R - 1)))
+        return KPM_EINVAL;
+    auto it = c->shapes.find(R);
+    LaunchShape s = it != c->shapes.end() ? it->second : default_shape(c, R);
+    if (s.blocks_per_sm < 1) {
+        DeviceGuard guard(c->device);
+        s.blocks_per_sm = sweep_max_blocks_per_sm(c->precision, s, false);
+    }
+    out->lanes_per_row = s.T;
+    out->cols_per_lane = s.E;
+    out->block_threads = s.threads;
+    out->blocks_per_sm = s.blocks_per_sm;
+    return KPM_OK;
+}
+
+int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
+{
+    if (!c || !l || R < 1 || R > 64 || (R & (R - 1)))
+        return KPM_EINVAL;
+    if (l->lanes_per_row * l->cols_per_lane != R || l->block_threads < 32 ||
+        l->block_threads > KPM_SWEEP_MAX_THREADS || (l->block_threads % 32) ||
+        l->blocks_per_sm < 0)
+        return KPM_EINVAL;
+    LaunchShape s{l->lanes_per_row, l->cols_per_lane, l->block_threads, l->blocks_per_sm};
+    DeviceGuard guard(c->device);
+    if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)
+        return KPM_EUNSUPPORTED;
+    c->shapes[R] = s;
+    return KPM_OK;
+}
+
+}  // extern "C"

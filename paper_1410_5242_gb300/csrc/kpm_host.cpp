@@ -1,0 +1,328 @@
+// Host-only parts of libkpm: input validation, Gershgorin bounds, the
+// rescaling, the CSR -> SELL-C-sigma converter, and the reconstruction
+// eta -> mu -> Jackson DOS.  None of these needs a GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri)
+{
+    if (n < 1 || n > INT32_MAX || !row_ptr)
+        return KPM_EINVAL;
+    if (row_ptr[0] != 0)
+        return KPM_EINVAL;
+    for (int64_t i = 0; i < n; i++)
+        if (row_ptr[i + 1] < row_ptr[i])
+            return KPM_EINVAL;
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && (!col || !val_ri))
+        return KPM_EINVAL;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t prev = -1;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+            if (col[k] < 0 || col[k] >= n || col[k] <= prev)
+                return KPM_EINVAL;
+            prev = col[k];
+        }
+    }
+    for (int64_t k = 0; k < 2 * nnz; k++)
+        if (!std::isfinite(val_ri[k]))
+            return KPM_EINVAL;
+    return KPM_OK;
+}
+
+int check_hermitian(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                    double rel_tol)
+{
+    double vmax = 0.0;
+    for (int64_t k = 0; k < row_ptr[n]; k++)
+        vmax = std::max(vmax, std::hypot(val_ri[2 * k], val_ri[2 * k + 1]));
+    const double tol = rel_tol * (vmax > 0 ? vmax : 1.0);
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+            const int32_t j = col[k];
+            const double re = val_ri[2 * k], im = val_ri[2 * k + 1];
+            const int32_t *b = col + row_ptr[j], *e = col + row_ptr[j + 1];
+            const int32_t *f = std::lower_bound(b, e, (int32_t)i);
+            double tre = 0.0, tim = 0.0;
+            if (f != e && *f == i) {
+                const int64_t kk = f - col;
+                tre = val_ri[2 * kk];
+                tim = val_ri[2 * kk + 1];
+            }
+            // h_ji must equal conj(h_ij)
+            if (std::fabs(tre - re) > tol || std::fabs(tim + im) > tol)
+                return KPM_ENOTHERMITIAN;
+        }
+    }
+    return KPM_OK;
+}
+
+}  // namespace kpm
+
+using namespace kpm;
+
+extern "C" {
+
+void kpm_default_options(kpm_options *opt)
+{
+    if (!opt)
+        return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = KPM_PREC_FP64;
+    opt->chunk_height = 32;
+    opt->sigma = 256;
+}
+
+const char *kpm_status_string(int status)
+{
+    switch (status) {
+    case KPM_OK: return "KPM_OK";
+    case KPM_EINVAL: return "KPM_EINVAL: invalid argument";
+    case KPM_ENOTHERMITIAN: return "KPM_ENOTHERMITIAN: matrix is not Hermitian";
+    case KPM_ENOMEM: return "KPM_ENOMEM: out of memory";
+    case KPM_ECUDA: return "KPM_ECUDA: CUDA runtime error";
+    case KPM_ETIMEOUT: return "KPM_ETIMEOUT: bounded device wait expired";
+    case KPM_EUNSUPPORTED: return "KPM_EUNSUPPORTED: unsupported request";
+    default: return "unknown KPM status";
+    }
+}
+
+int kpm_gershgorin(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                   double *emin, double *emax)
+{
+    if (!emin || !emax)
+        return KPM_EINVAL;
+    int rc = validate_csr(n, row_ptr, col, val_ri);
+    if (rc)
+        return rc;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        double centre = 0.0, radius = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+            if (col[k] == i)
+                centre = val_ri[2 * k];
+            else
+                radius += std::hypot(val_ri[2 * k], val_ri[2 * k + 1]);
+        }
+        lo = std::min(lo, centre - radius);
+        hi = std::max(hi, centre + radius);
+    }
+    *emin = lo;
+    *emax = hi;
+    return KPM_OK;
+}
+
+int kpm_scale_from_bounds(double emin, double emax, double eps, double *a, double *b)
+{
+    if (!a || !b || !std::isfinite(emin) || !std::isfinite(emax) || !(emax > emin) ||
+        !(eps >= 0.0 && eps < 1.0))
+        return KPM_EINVAL;
+    *b = 0.5 * (emax + emin);
+    *a = (1.0 - eps) * 2.0 / (emax - emin);
+    return KPM_OK;
+}
+
+int kpm_eta_to_mu(const double *eta, int32_t M, int32_t R, double *mu)
+{
+    if (!eta || !mu || M < 2 || (M & 1) || R < 1)
+        return KPM_EINVAL;
+    double norm = 0.0;
+    for (int32_t r = 0; r < R; r++)
+        norm += eta[(size_t)r * M];
+    if (!(norm > 0.0))
+        return KPM_EINVAL;
+    // Sum the per-vector terms 2*eta_n over r first, then subtract the
+    // parity term R-summed: c_n = 2 eta_n - eta_{n mod 2} for n >= 2.
+    double e0 = 0.0, e1 = 0.0;
+    for (int32_t r = 0; r < R; r++) {
+        e0 += eta[(size_t)r * M];
+        e1 += eta[(size_t)r * M + 1];
+    }
+    mu[0] = e0 / norm;
+    mu[1] = e1 / norm;
+    for (int32_t k = 2; k < M; k++) {
+        double s = 0.0;
+        for (int32_t r = 0; r < R; r++)
+            s += eta[(size_t)r * M + k];
+        mu[k] = (2.0 * s - ((k & 1) ? e1 : e0)) / norm;
+    }
+    return KPM_OK;
+}
+
+int kpm_dos(const double *mu, int32_t M, int32_t K, double a, double b, double *energy,
+            double *rho)
+{
+    if (!mu || !energy || !rho || M < 1 || K < 1 || !(a > 0.0) || !std::isfinite(b))
+        return KPM_EINVAL;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> gm(M);
+    const double q = pi / (double)(M + 1);
+    const double cotq = std::cos(q) / std::sin(q);
+    for (int32_t n = 0; n < M; n++)
+        gm[n] = (((double)(M - n + 1)) * std::cos(q * n) + std::sin(q * n) * cotq) /
+                (double)(M + 1) * mu[n];
+    // Evaluate the damped series at each node with the three-term
+    // recurrence T_n = 2x T_{n-1} - T_{n-2}.
+    for (int32_t k = 0; k < K; k++) {
+        const double theta = pi * ((double)k + 0.5) / (double)K;
+        const double x = std::cos(theta);
+        double t0 = 1.0, t1 = x;
+        double s = gm[0];
+        if (M > 1)
+            s += 2.0 * gm[1] * t1;
+        for (int32_t n = 2; n < M; n++) {
+            const double t2 = 2.0 * x * t1 - t0;
+            s += 2.0 * gm[n] * t2;
+            t0 = t1;
+            t1 = t2;
+        }
+        energy[k] = x / a + b;
+        rho[k] = a * s / (pi * std::sin(theta));
+    }
+    return KPM_OK;
+}
+
+int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                   double a, double b, int32_t C, int32_t sigma, kpm_sell *out)
+{
+    if (!out)
+        return KPM_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (C < 1 || C > 1024 || (C & (C - 1)) || sigma < 1 || !(a > 0.0) || !std::isfinite(a) ||
+        !std::isfinite(b))
+        return KPM_EINVAL;
+    int rc = validate_csr(n, row_ptr, col, val_ri);
+    if (rc)
+        return rc;
+
+    // Fold H' = 2a (H - b 1): row lengths after adding missing diagonals.
+    std::vector<int32_t> len(n);
+    std::vector<uint8_t> has_diag(n, 0);
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++)
+            if (col[k] == i)
+                has_diag[i] = 1;
+        len[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]) + ((!has_diag[i] && b != 0.0) ? 1 : 0);
+    }
+
+    const int64_t n_chunks = (n + C - 1) / C;
+    const int64_t n_pad = n_chunks * C;
+    // sigma-window sort by descending row length (stable)
+    std::vector<int32_t> perm(n_pad);
+    std::iota(perm.begin(), perm.end(), 0);
+    if (sigma > 1) {
+        for (int64_t w = 0; w < n; w += sigma) {
+            const int64_t e = std::min<int64_t>(n, w + sigma);
+            std::stable_sort(perm.begin() + w, perm.begin() + e,
+                             [&](int32_t x, int32_t y) { return len[x] > len[y]; });
+        }
+    }
+    std::vector<int32_t> iperm(n);
+    for (int64_t p = 0; p < n; p++)
+        iperm[perm[p]] = (int32_t)p;
+
+    int64_t *chunk_ptr = (int64_t *)std::malloc(sizeof(int64_t) * (n_chunks + 1));
+    int32_t *chunk_len = (int32_t *)std::malloc(sizeof(int32_t) * (n_chunks ? n_chunks : 1));
+    int32_t *perm_out = (int32_t *)std::malloc(sizeof(int32_t) * n_pad);
+    if (!chunk_ptr || !chunk_len || !perm_out) {
+        std::free(chunk_ptr); std::free(chunk_len); std::free(perm_out);
+        return KPM_ENOMEM;
+    }
+    chunk_ptr[0] = 0;
+    int64_t nnz = 0;
+    for (int64_t c = 0; c < n_chunks; c++) {
+        int32_t m = 0;
+        for (int64_t r = 0; r < C; r++) {
+            const int64_t p = c * C + r;
+            if (p < n) {
+                m = std::max(m, len[perm[p]]);
+                nnz += len[perm[p]];
+            }
+        }
+        chunk_len[c] = m;
+        chunk_ptr[c + 1] = chunk_ptr[c] + (int64_t)m * C;
+    }
+    const int64_t n_stored = chunk_ptr[n_chunks];
+    int32_t *scol = (int32_t *)std::malloc(sizeof(int32_t) * (n_stored ? n_stored : 1));
+    double *sval = (double *)std::malloc(sizeof(double) * 2 * (n_stored ? n_stored : 1));
+    if (!scol || !sval) {
+        std::free(chunk_ptr); std::free(chunk_len); std::free(perm_out);
+        std::free(scol); std::free(sval);
+        return KPM_ENOMEM;
+    }
+    const double two_a = 2.0 * a;
+    for (int64_t c = 0; c < n_chunks; c++) {
+        const int64_t base = chunk_ptr[c];
+        const int32_t clen = chunk_len[c];
+        for (int64_t r = 0; r < C; r++) {
+            const int64_t p = c * C + r;
+            int32_t j = 0;
+            auto put = [&](int32_t newcol, double re, double im) {
+                const int64_t e = base + (int64_t)j * C + r;
+                scol[e] = newcol;
+                sval[2 * e] = re;
+                sval[2 * e + 1] = im;
+                j++;
+            };
+            if (p < n) {
+                const int64_t i = perm[p];
+                bool diag_done = has_diag[i] || b == 0.0;
+                for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+                    if (!diag_done && col[k] > i) {
+                        put((int32_t)p, -two_a * b, 0.0);
+                        diag_done = true;
+                    }
+                    double re = val_ri[2 * k], im = val_ri[2 * k + 1];
+                    if (col[k] == i)
+                        re = two_a * (re - b), im = two_a * im;
+                    else
+                        re = two_a * re, im = two_a * im;
+                    put(iperm[col[k]], re, im);
+                }
+                if (!diag_done)
+                    put((int32_t)p, -two_a * b, 0.0);
+            }
+            // padding: zero value, the row's own index (its V row is read anyway)
+            while (j < clen)
+                put((int32_t)p, 0.0, 0.0);
+        }
+    }
+    for (int64_t p = 0; p < n_pad; p++)
+        perm_out[p] = perm[p];
+
+    out->n = n;
+    out->n_pad = n_pad;
+    out->C = C;
+    out->sigma = sigma;
+    out->n_chunks = n_chunks;
+    out->nnz = nnz;
+    out->n_stored = n_stored;
+    out->chunk_ptr = chunk_ptr;
+    out->chunk_len = chunk_len;
+    out->col = scol;
+    out->val_ri = sval;
+    out->perm = perm_out;
+    return KPM_OK;
+}
+
+void kpm_sell_release(kpm_sell *s)
+{
+    if (!s)
+        return;
+    std::free(s->chunk_ptr);
+    std::free(s->chunk_len);
+    std::free(s->col);
+    std::free(s->val_ri);
+    std::free(s->perm);
+    std::memset(s, 0, sizeof(*s));
+}
+
+}  // extern "C"

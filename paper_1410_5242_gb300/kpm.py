@@ -1,0 +1,347 @@
+"""Thin ctypes binding of libkpm (include/kpm.h): same names, argument
+marshalling only.  Every step of the KPM hot path runs inside the library;
+nothing here computes moments.  PyTorch supplies device memory (its
+caching allocator is passed to the library as the allocator hook) and
+streams.
+
+The shared library is built in-tree by ``paper_1410_5242_gb300.build``;
+importing this module fails loudly if it is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libkpm.so")
+
+KPM_OK = 0
+KPM_EINVAL = -1
+KPM_ENOTHERMITIAN = -2
+KPM_ENOMEM = -3
+KPM_ECUDA = -4
+KPM_ETIMEOUT = -5
+KPM_EUNSUPPORTED = -6
+
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("chunk_height", ctypes.c_int32),
+                ("sigma", ctypes.c_int32), ("check_hermitian", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+
+
+class Sell(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("C", ctypes.c_int32),
+                ("sigma", ctypes.c_int32), ("n_chunks", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_stored", ctypes.c_int64), ("chunk_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("chunk_len", ctypes.POINTER(ctypes.c_int32)),
+                ("col", ctypes.POINTER(ctypes.c_int32)), ("val_ri", ctypes.POINTER(ctypes.c_double)),
+                ("perm", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_stored", ctypes.c_int64), ("n_chunks", ctypes.c_int64), ("C", ctypes.c_int32),
+                ("sigma", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("matrix_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("lanes_per_row", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+_i32, _i64, _u64, _d = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_vp, _pd = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_pi32, _pi64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+_int = ctypes.c_int
+
+_SIGS = {
+    "kpm_default_options": (None, [ctypes.POINTER(Options)]),
+    "kpm_status_string": (ctypes.c_char_p, [_int]),
+    "kpm_gershgorin": (_int, [_i64, _pi64, _pi32, _pd, _pd, _pd]),
+    "kpm_scale_from_bounds": (_int, [_d, _d, _d, _pd, _pd]),
+    "kpm_eta_to_mu": (_int, [_pd, _i32, _i32, _pd]),
+    "kpm_dos": (_int, [_pd, _i32, _i32, _d, _d, _pd, _pd]),
+    "kpm_sell_build": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, _i32, ctypes.POINTER(Sell)]),
+    "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
+    "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
+                          ctypes.POINTER(_vp)]),
+    "kpm_destroy": (None, [_vp]),
+    "kpm_moments": (_int, [_vp, _i32, _i32, _u64, _pd, _pd, _vp]),
+    "kpm_moments_v0": (_int, [_vp, _i32, _i32, _pd, _pd, _pd, _vp]),
+    "kpm_moments_batch": (_int, [ctypes.POINTER(_vp), _i32, _pi32, _pi32,
+                                 ctypes.POINTER(_u64), ctypes.POINTER(_pd), _vp]),
+    "kpm_get_info": (_int, [_vp, ctypes.POINTER(Info)]),
+    "kpm_block_bytes": (_i64, [_vp, _i32]),
+    "kpm_block_upload": (_int, [_vp, _i32, _pd, _vp, _vp]),
+    "kpm_block_download": (_int, [_vp, _i32, _vp, _pd, _vp]),
+    "kpm_aug_spmmv": (_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
+    "kpm_moments_device": (_int, [_vp, _i32, _i32, _u64, _vp, _vp, _vp]),
+    "kpm_get_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
+    "kpm_set_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
+}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libkpm.so is not built (%s); run paper_1410_5242_gb300.build.build() "
+                      "or __graft_entry__.build() first" % LIB_PATH)
+lib = ctypes.CDLL(LIB_PATH)
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class KPMError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s" % (what, lib.kpm_status_string(status).decode()))
+
+
+def _check(rc, what):
+    if rc != KPM_OK:
+        raise KPMError(rc, what)
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _csr(csr):
+    rp = np.ascontiguousarray(csr["row_ptr"], dtype=np.int64)
+    col = np.ascontiguousarray(csr["col"], dtype=np.int32)
+    val = np.ascontiguousarray(csr["val"], dtype=np.complex128).view(np.float64)
+    return int(csr["n"]), rp, col, val
+
+
+def status_string(status):
+    return lib.kpm_status_string(status).decode()
+
+
+def default_options():
+    o = Options()
+    lib.kpm_default_options(ctypes.byref(o))
+    return o
+
+
+# --------------------------------------------------------------- host-only
+def gershgorin(csr):
+    n, rp, col, val = _csr(csr)
+    lo, hi = _d(), _d()
+    _check(lib.kpm_gershgorin(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), ctypes.byref(lo),
+                              ctypes.byref(hi)), "kpm_gershgorin")
+    return lo.value, hi.value
+
+
+def scale_from_bounds(emin, emax, eps=0.01):
+    a, b = _d(), _d()
+    _check(lib.kpm_scale_from_bounds(emin, emax, eps, ctypes.byref(a), ctypes.byref(b)),
+           "kpm_scale_from_bounds")
+    return a.value, b.value
+
+
+def eta_to_mu(eta):
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    R, M = eta.shape
+    mu = np.empty(M)
+    _check(lib.kpm_eta_to_mu(_p(eta, _d), M, R, _p(mu, _d)), "kpm_eta_to_mu")
+    return mu
+
+
+def dos(mu, K, a, b):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    e, rho = np.empty(K), np.empty(K)
+    _check(lib.kpm_dos(_p(mu, _d), mu.size, K, a, b, _p(e, _d), _p(rho, _d)), "kpm_dos")
+    return e, rho
+
+
+def sell_build(csr, a, b, C=32, sigma=256):
+    """The SELL-C-sigma layout kpm_create would upload, as numpy arrays."""
+    n, rp, col, val = _csr(csr)
+    s = Sell()
+    _check(lib.kpm_sell_build(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, C, sigma,
+                              ctypes.byref(s)), "kpm_sell_build")
+    try:
+        out = {
+            "n": s.n, "n_pad": s.n_pad, "C": s.C, "sigma": s.sigma, "n_chunks": s.n_chunks,
+            "nnz": s.nnz, "n_stored": s.n_stored,
+            "chunk_ptr": np.ctypeslib.as_array(s.chunk_ptr, (s.n_chunks + 1,)).copy(),
+            "chunk_len": np.ctypeslib.as_array(s.chunk_len, (max(s.n_chunks, 1),))[:s.n_chunks].copy(),
+            "col": np.ctypeslib.as_array(s.col, (max(s.n_stored, 1),))[:s.n_stored].copy(),
+            "val": np.ctypeslib.as_array(s.val_ri, (max(2 * s.n_stored, 2),))[:2 * s.n_stored]
+            .copy().view(np.complex128),
+            "perm": np.ctypeslib.as_array(s.perm, (s.n_pad,)).copy(),
+        }
+    finally:
+        lib.kpm_sell_release(ctypes.byref(s))
+    return out
+
+
+# ------------------------------------------------------------------- GPU
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _TorchAllocator:
+    """Device allocator hook backed by PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        torch = _torch()
+        self.device = device
+
+        def alloc(nbytes, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device)
+            except Exception:  # noqa: BLE001 - reported to the library as NULL
+                return None
+
+        def free(ptr, user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+class Context:
+    """kpm_create / kpm_destroy around a Hermitian CSR matrix and (a, b)."""
+
+    def __init__(self, csr, a, b, precision=PREC_FP64, chunk_height=32, sigma=256,
+                 check_hermitian=False, device=0, torch_allocator=True):
+        n, rp, col, val = _csr(csr)
+        opt = default_options()
+        opt.precision = precision
+        opt.chunk_height = chunk_height
+        opt.sigma = sigma
+        opt.check_hermitian = 1 if check_hermitian else 0
+        opt.device = device
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator(device)
+            opt.alloc_fn = self._alloc.alloc
+            opt.free_fn = self._alloc.free
+        h = ctypes.c_void_p()
+        _check(lib.kpm_create(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, ctypes.byref(opt),
+                              ctypes.byref(h)), "kpm_create")
+        self.handle = h
+        self.n = n
+        self.a, self.b = a, b
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kpm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries
+    def info(self):
+        i = Info()
+        _check(lib.kpm_get_info(self.handle, ctypes.byref(i)), "kpm_get_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def block_bytes(self, R):
+        return int(lib.kpm_block_bytes(self.handle, R))
+
+    def get_launch(self, R):
+        l = Launch()
+        _check(lib.kpm_get_launch(self.handle, R, ctypes.byref(l)), "kpm_get_launch")
+        return {f: getattr(l, f) for f, _ in Launch._fields_}
+
+    def set_launch(self, R, lanes_per_row, cols_per_lane, block_threads=256, blocks_per_sm=0):
+        l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm)
+        _check(lib.kpm_set_launch(self.handle, R, ctypes.byref(l)), "kpm_set_launch")
+
+    # -- host-buffer calls
+    def moments(self, M, R, seed, imag=False, stream=None):
+        eta = np.empty((R, M))
+        eti = np.empty((R, M)) if imag else None
+        _check(lib.kpm_moments(self.handle, M, R, seed, _p(eta, _d),
+                               _p(eti, _d) if imag else None, _stream_ptr(stream)), "kpm_moments")
+        return (eta, eti) if imag else eta
+
+    def moments_v0(self, M, v0, imag=False, stream=None):
+        v0 = np.ascontiguousarray(v0, dtype=np.complex128)
+        R = v0.shape[1]
+        eta = np.empty((R, M))
+        eti = np.empty((R, M)) if imag else None
+        _check(lib.kpm_moments_v0(self.handle, M, R, _p(v0.view(np.float64), _d), _p(eta, _d),
+                                  _p(eti, _d) if imag else None, _stream_ptr(stream)),
+               "kpm_moments_v0")
+        return (eta, eti) if imag else eta
+
+    # -- device-buffer calls (torch tensors)
+    def new_block(self, R):
+        torch = _torch()
+        nbytes = self.block_bytes(R)
+        return torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+
+    def block_upload(self, R, host, dev, stream=None):
+        host = np.ascontiguousarray(host, dtype=np.complex128)
+        _check(lib.kpm_block_upload(self.handle, R, _p(host.view(np.float64), _d),
+                                    ctypes.c_void_p(dev.data_ptr()), _stream_ptr(stream)),
+               "kpm_block_upload")
+
+    def block_download(self, R, dev, stream=None):
+        out = np.empty((self.n, R), dtype=np.complex128)
+        _check(lib.kpm_block_download(self.handle, R, ctypes.c_void_p(dev.data_ptr()),
+                                      _p(out.view(np.float64), _d), _stream_ptr(stream)),
+               "kpm_block_download")
+        return out
+
+    def aug_spmmv(self, R, V, W, eta_dev, init=False, with_imag=True, stream=None):
+        eta_p = ctypes.c_void_p(eta_dev.data_ptr()) if eta_dev is not None else None
+        _check(lib.kpm_aug_spmmv(self.handle, R, ctypes.c_void_p(V.data_ptr()),
+                                 ctypes.c_void_p(W.data_ptr()), eta_p,
+                                 1 if init else 0, 1 if with_imag else 0, _stream_ptr(stream)),
+               "kpm_aug_spmmv")
+
+    def moments_device(self, M, R, seed, eta_dev, eta_imag_dev=None, stream=None):
+        _check(lib.kpm_moments_device(
+            self.handle, M, R, seed, ctypes.c_void_p(eta_dev.data_ptr()),
+            ctypes.c_void_p(eta_imag_dev.data_ptr()) if eta_imag_dev is not None else None,
+            _stream_ptr(stream)), "kpm_moments_device")
+
+
+def create(csr, a, b, **kw):
+    return Context(csr, a, b, **kw)
+
+
+def moments_batch(ctxs, Ms, Rs, seeds, stream=None):
+    """kpm_moments_batch: returns a list of eta arrays [R_p][M_p]."""
+    count = len(ctxs)
+    handles = (ctypes.c_void_p * count)(*[c.handle for c in ctxs])
+    Ma = np.ascontiguousarray(Ms, dtype=np.int32)
+    Ra = np.ascontiguousarray(Rs, dtype=np.int32)
+    Sa = np.ascontiguousarray(seeds, dtype=np.uint64)
+    etas = [np.empty((int(R), int(M))) for M, R in zip(Ms, Rs)]
+    ptrs = (_pd * count)(*[_p(e, _d) for e in etas])
+    _check(lib.kpm_moments_batch(handles, count, _p(Ma, _i32), _p(Ra, _i32),
+                                 Sa.ctypes.data_as(ctypes.POINTER(_u64)), ptrs,
+                                 _stream_ptr(stream)), "kpm_moments_batch")
+    return etas

@@ -1,0 +1,240 @@
+"""CPU tests of libkpm's C interface: the library loads and exports every
+function include/kpm.h declares, the host-only calls agree with the oracle,
+the SELL-C-sigma converter reproduces H' = 2a(H - b 1) exactly, and bad
+input is rejected with the documented status codes.  No GPU is touched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from kpm_inputs import hamiltonians as ham
+from paper_1410_5242_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def kpm():
+    pkg_build.build()
+    from paper_1410_5242_gb300 import kpm as k
+    return k
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "kpm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kpm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function(kpm):
+    names = header_functions()
+    assert len(names) >= 20
+    so = ctypes.CDLL(kpm.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_gershgorin_and_scale_match_oracle(kpm, orc):
+    for h in (ham.ti_hamiltonian(5, 4, 3, gamma=1.3, seed=2),
+              ham.random_hermitian(90, 6, seed=1, empty_rows=0.1)):
+        assert kpm.gershgorin(h) == orc.gershgorin(h)
+        lo, hi = kpm.gershgorin(h)
+        assert kpm.scale_from_bounds(lo, hi, 0.01) == orc.scale_from_bounds(lo, hi, 0.01)
+
+
+def test_eta_to_mu_matches_oracle(kpm, orc):
+    g = np.random.default_rng(3)
+    eta = g.uniform(-1, 1, (5, 40)) * 100
+    eta[:, 0] = g.uniform(50, 100, 5)
+    np.testing.assert_allclose(kpm.eta_to_mu(eta), orc.eta_to_mu(eta), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("M,K", [(16, 64), (512, 1024), (4096, 4096)])
+def test_dos_matches_oracle(kpm, orc, M, K):
+    g = np.random.default_rng(M)
+    mu = np.concatenate([[1.0], g.uniform(-0.2, 0.2, M - 1) / np.sqrt(1 + np.arange(1, M))])
+    e1, r1 = kpm.dos(mu, K, 0.2, -0.4)
+    e2, r2 = orc.dos(mu, K, 0.2, -0.4)
+    np.testing.assert_array_equal(e1, e2)
+    np.testing.assert_allclose(r1, r2, rtol=0, atol=1e-11 * np.abs(r2).max())
+
+
+def _fold_reference(h, a, b):
+    """2a(H - b 1) by the definition, with a stored diagonal everywhere."""
+    n = h["n"]
+    d = ham.to_dense(h)
+    two_a = 2.0 * a
+    out = np.zeros_like(d)
+    nz = d != 0
+    out[nz] = d[nz] * two_a
+    diag = np.diag(d)
+    out[np.arange(n), np.arange(n)] = (diag.real - b) * two_a + 1j * (diag.imag * two_a)
+    return out
+
+
+def _row_lengths(h, b):
+    """Stored length of each row of H': the CSR row plus an inserted
+    diagonal where H has none and b != 0."""
+    n, rp, col = h["n"], h["row_ptr"], h["col"]
+    has_diag = np.array([(col[rp[i]:rp[i + 1]] == i).any() for i in range(n)])
+    return np.diff(rp) + ((~has_diag) & (b != 0)).astype(np.int64)
+
+
+def _unpack(sell, rowlen):
+    """Dense matrix in the original numbering, checking the layout on the way:
+    perm is a permutation, entries beyond a row's length are padding (value
+    0, the row's own index), chunk offsets are C * chunk length."""
+    n, C = sell["n"], sell["C"]
+    perm = sell["perm"]
+    assert sorted(perm[:n]) == list(range(n))
+    assert np.array_equal(perm[n:], np.arange(n, sell["n_pad"]))
+    dense = np.zeros((n, n), dtype=np.complex128)
+    for c in range(sell["n_chunks"]):
+        base, clen = sell["chunk_ptr"][c], sell["chunk_len"][c]
+        assert sell["chunk_ptr"][c + 1] - base == clen * C
+        for r in range(C):
+            p = c * C + r
+            length = rowlen[perm[p]] if p < n else 0
+            assert length <= clen
+            for j in range(clen):
+                e = base + j * C + r
+                col, v = sell["col"][e], sell["val"][e]
+                if j >= length:
+                    assert v == 0 and col == p
+                else:
+                    dense[perm[p], perm[col]] += v
+    return dense
+
+
+@pytest.mark.parametrize("C,sigma", [(1, 1), (4, 1), (4, 8), (32, 256), (32, 1)])
+def test_sell_roundtrip_ragged(kpm, C, sigma):
+    h = ham.random_hermitian(203, 7, seed=C + sigma, empty_rows=0.15)
+    a, b = 0.37, 0.61
+    sell = kpm.sell_build(h, a, b, C=C, sigma=sigma)
+    assert sell["n_pad"] % C == 0 and sell["n_pad"] >= h["n"]
+    rowlen = _row_lengths(h, b)
+    dense = _unpack(sell, rowlen)
+    np.testing.assert_array_equal(dense, _fold_reference(h, a, b))
+    # sigma-window sort: rows inside each window by non-increasing length
+    for w in range(0, h["n"], sigma):
+        seg = rowlen[sell["perm"][w:min(h["n"], w + sigma)]]
+        assert np.all(np.diff(seg) <= 0) or sigma == 1
+    # chunk length = longest row of the chunk
+    for c in range(sell["n_chunks"]):
+        rows = sell["perm"][c * C:(c + 1) * C]
+        rows = rows[rows < h["n"]]
+        assert sell["chunk_len"][c] == (rowlen[rows].max() if rows.size else 0)
+
+
+def test_sell_ti_lattice_is_unpadded_identity(kpm):
+    h = ham.ti_hamiltonian(8, 8, 8, gamma=0.5, seed=0)
+    a, b = 0.12, 0.03
+    sell = kpm.sell_build(h, a, b, C=32, sigma=256)
+    assert np.array_equal(sell["perm"], np.arange(h["n"]))   # equal row lengths: stable
+    assert sell["n_stored"] == sell["nnz"] == 13 * h["n"]
+    assert np.all(sell["chunk_len"] == 13)
+    dense = _unpack(sell, _row_lengths(h, b))
+    np.testing.assert_array_equal(dense, _fold_reference(h, a, b))
+
+
+def test_sell_missing_diagonal_is_inserted_only_when_b_nonzero(kpm):
+    h = ham.random_hermitian(50, 4, seed=5)
+    # drop every diagonal entry
+    keep = np.repeat(np.arange(50), np.diff(h["row_ptr"])) != h["col"]
+    rows = np.repeat(np.arange(50), np.diff(h["row_ptr"]))[keep]
+    h2 = {"n": 50, "col": h["col"][keep], "val": h["val"][keep],
+          "row_ptr": np.searchsorted(rows, np.arange(51)).astype(np.int64)}
+    s0 = kpm.sell_build(h2, 0.5, 0.0, C=8, sigma=1)
+    assert s0["nnz"] == h2["col"].size
+    s1 = kpm.sell_build(h2, 0.5, 0.25, C=8, sigma=1)
+    assert s1["nnz"] == h2["col"].size + 50
+    dense = _unpack(s1, _row_lengths(h2, 0.25))
+    np.testing.assert_array_equal(dense, _fold_reference(h2, 0.5, 0.25))
+
+
+def _bad(h, **kw):
+    out = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in h.items()}
+    out.update(kw)
+    return out
+
+
+def test_invalid_input_is_rejected(kpm):
+    h = ham.ti_hamiltonian(3, 3, 3)
+    col = h["col"].copy()
+    col[[1, 2]] = col[[2, 1]]                     # unsorted row
+    rp = h["row_ptr"].copy()
+    rp[5] = rp[4] - 1                             # decreasing row pointer
+    val = h["val"].copy()
+    val[7] = np.nan
+    oob = h["col"].copy()
+    oob[0] = h["n"]
+    for bad in (_bad(h, col=col), _bad(h, row_ptr=rp), _bad(h, val=val), _bad(h, col=oob)):
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.gershgorin(bad)
+        assert e.value.status == kpm.KPM_EINVAL
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.sell_build(bad, 0.1, 0.0)
+        assert e.value.status == kpm.KPM_EINVAL
+    for C in (0, 3, 2048):
+        with pytest.raises(kpm.KPMError):
+            kpm.sell_build(h, 0.1, 0.0, C=C)
+    with pytest.raises(kpm.KPMError):
+        kpm.sell_build(h, -0.1, 0.0)
+    with pytest.raises(kpm.KPMError):
+        kpm.eta_to_mu(np.ones((2, 5)))
+    with pytest.raises(kpm.KPMError):
+        kpm.dos(np.ones(4), 8, 0.0, 0.0)
+    with pytest.raises(kpm.KPMError):
+        kpm.scale_from_bounds(2.0, 1.0)
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(kpm):
+    h = ham.ti_hamiltonian(3, 3, 3)
+    col = h["col"].copy()
+    col[0] = -1
+    for args in ((_bad(h, col=col), 0.1, 0.0), (h, 0.0, 0.0), (h, float("nan"), 0.0)):
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.Context(*args, torch_allocator=False)
+        assert e.value.status == kpm.KPM_EINVAL
+    asym = _bad(h)
+    asym["val"][3] += 0.5
+    with pytest.raises(kpm.KPMError) as e:
+        kpm.Context(asym, 0.1, 0.0, check_hermitian=True, torch_allocator=False)
+    assert e.value.status == kpm.KPM_ENOTHERMITIAN
+
+
+def test_create_without_gpu_reports_cuda_error(kpm):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ham.ti_hamiltonian(3, 3, 3)
+    with pytest.raises(kpm.KPMError) as e:
+        kpm.Context(h, 0.1, 0.0, torch_allocator=False)
+    assert e.value.status == kpm.KPM_ECUDA
+
+
+def test_status_strings(kpm):
+    for code in range(0, -7, -1):
+        assert kpm.status_string(code).startswith("KPM_")
+
+
+def test_model_reproduces_paper_numbers():
+    from paper_1410_5242_gb300 import model
+    gold = {}
+    path = os.path.join(ROOT, "tests", "golden", "code_balance.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, val, tol = line.split()[:3]
+            gold[key] = (float(val), float(tol))
+    assert model.sweep_flops(1, 13, 1) == gold["flops_per_row_vector"][0]
+    assert model.sweep_bytes(1, 13, 1, 16) == gold["balance_numerator_R1"][0]
+    v, t = gold["B_min_R1"]
+    assert abs(model.code_balance(13, 1) - v) <= t
+    v, t = gold["B_min_Rinf"]
+    assert abs(model.code_balance(13, 10 ** 9) - v) <= t
+    # Eq. 4 chain: aug_spmmv moves less than aug_spmv, which moves less than naive
+    args = (2000, 10 ** 6, 13 * 10 ** 6, 32, 16)
+    assert (model.kpm_traffic(*args, variant="aug_spmmv") < model.kpm_traffic(*args, variant="aug_spmv")
+            < model.kpm_traffic(*args, variant="naive"))
