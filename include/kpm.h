@@ -232,6 +232,30 @@ int kpm_block_download(kpm_ctx *ctx, int32_t R, const void *dev_block, double *h
 int kpm_aug_spmmv(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_dev,
                   int32_t init, int32_t with_imag, void *stream);
 
+/* Allocation-free variant of kpm_aug_spmmv (the paper has no counterpart;
+ * it serves callers that may not allocate device memory at the time of the
+ * call: code whose device memory is owned by another allocator or pool,
+ * and latency-critical loops in which cudaMalloc/cudaFree would implicitly
+ * synchronise the device).  Same arguments, same kernels and the same
+ * results as kpm_aug_spmmv; the caller still passes V, W and eta_dev.  The
+ * per-block partial sums go to a fixed scratch array of 1,048,576 doubles
+ * (8 MiB) that every GPU loading this library holds until the process
+ * exits; the call makes no cudaMalloc, cudaFree or other allocating call.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture on that device.
+ *   - R needing more partials than the scratch holds is rejected with
+ *     KPM_EINVAL before anything is launched.  The need is the sum over
+ *     column blocks of grid * 3 * width doubles; with the default launch
+ *     shapes (256-thread blocks) every R <= 256 fits.
+ *   - Nothing in the scratch has to start at zero: every call writes each
+ *     partial it later reads.  Calls share the one array and it keeps the
+ *     last call's contents, so calls that overlap on the GPU (other streams,
+ *     other host threads, other contexts on the same device) race; order
+ *     them on one stream. */
+int kpm_aug_spmmv_static(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_dev,
+                         int32_t init, int32_t with_imag, void *stream);
+
 /* kpm_moments with everything on the device: random-phase start vectors
  * from seed are generated on the GPU and eta_dev / eta_imag_dev (device
  * double[R][M], eta_imag_dev may be NULL) are written without a host copy.

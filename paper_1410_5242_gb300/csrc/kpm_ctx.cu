@@ -765,3 +765,107 @@ int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
 }
 
 }  // extern "C"
+
+// =====================================================================
+// Allocation-free sweep (kpm_aug_spmmv_static).
+//
+// kpm_aug_spmmv keeps the per-block partial sums of eta in a device buffer
+// that it allocates on first use.  This variant runs the same kernels but
+// takes that scratch from the fixed array below.  The CUDA runtime places
+// the array in device memory when this library's module is loaded on a
+// device and keeps it there until the process exits, so a call never
+// allocates.  Host code cannot use the symbol as a pointer; its device
+// address is looked up once per device with cudaGetSymbolAddress.
+// =====================================================================
+#include <mutex>
+
+#define KPM_STATIC_SCRATCH_DOUBLES (1024 * 1024)  // 8 MiB per device
+
+static __device__ __align__(256) double g_static_scratch[KPM_STATIC_SCRATCH_DOUBLES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_scratch_lock;
+double *g_static_scratch_addr[kMaxStaticDevices] = {};
+
+// Device address of g_static_scratch on `device`, which must be current.
+int static_scratch_address(int device, double **out)
+{
+    if (device < 0 || device >= kMaxStaticDevices)
+        return KPM_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_scratch_lock);
+    if (!g_static_scratch_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return KPM_ECUDA;
+        }
+        g_static_scratch_addr[device] = static_cast<double *>(p);
+    }
+    *out = g_static_scratch_addr[device];
+    return KPM_OK;
+}
+
+}  // namespace
+
+extern "C" int kpm_aug_spmmv_static(kpm_ctx *c, int32_t R, const void *V, void *W,
+                                    double *eta_dev, int32_t init, int32_t with_imag,
+                                    void *stream)
+{
+    if (!c || R < 1 || !V || !W || V == W)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    if (!guard.ok)
+        return KPM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *scratch = nullptr;
+    KPM_TRY(static_scratch_address(c->device, &scratch));
+
+    // Column blocks as in kpm_aug_spmmv (powers of two <= 64, widest first),
+    // visited twice without any container: first to size the scratch, then
+    // to launch.
+    auto block_shape = [&](int RB, LaunchShape &s, int &grid) {
+        auto it = c->shapes.find(RB);
+        s = it != c->shapes.end() ? it->second : default_shape(c, RB);
+        grid = resolve_grid(c, s);
+        return grid >= 1;
+    };
+    int64_t need = 0;
+    for (int rest = R, RB = 64; RB >= 1; RB >>= 1) {
+        for (; rest >= RB; rest -= RB) {
+            LaunchShape s;
+            int grid = 0;
+            if (!block_shape(RB, s, grid))
+                return KPM_EUNSUPPORTED;
+            need += (int64_t)grid * 3 * RB;
+        }
+    }
+    if (need > KPM_STATIC_SCRATCH_DOUBLES)
+        return KPM_EINVAL;
+
+    int64_t offset = 0;
+    int col0 = 0;
+    for (int rest = R, RB = 64; RB >= 1; RB >>= 1) {
+        for (; rest >= RB; rest -= RB) {
+            ColumnBlock cb;
+            cb.col0 = col0;
+            cb.RB = RB;
+            block_shape(RB, cb.shape, cb.grid);
+            cb.partial_offset = offset;
+            SweepParams p = sweep_params(c, cb, R, V, W, scratch + offset, with_imag != 0);
+            KPM_TRY(launch_one(c, cb, p, init != 0, st));
+            if (eta_dev) {
+                c->launches++;
+                reduce_single_kernel<<<(3 * RB + 127) / 128, 128, 0, st>>>(scratch + offset,
+                                                                           cb.grid, RB, col0, R,
+                                                                           eta_dev);
+                KPM_CUDA(cudaGetLastError());
+            }
+            offset += (int64_t)cb.grid * 3 * RB;
+            col0 += RB;
+        }
+    }
+    return KPM_OK;
+}

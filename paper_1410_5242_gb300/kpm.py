@@ -86,6 +86,7 @@ _SIGS = {
     "kpm_block_download": (_int, [_vp, _i32, _vp, _pd, _vp]),
     "kpm_aug_spmmv": (_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
     "kpm_moments_device": (_int, [_vp, _i32, _i32, _u64, _vp, _vp, _vp]),
+    "kpm_aug_spmmv_static": (_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
     "kpm_get_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
     "kpm_set_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
 }
@@ -320,6 +321,15 @@ class Context:
                                  ctypes.c_void_p(W.data_ptr()), eta_p,
                                  1 if init else 0, 1 if with_imag else 0, _stream_ptr(stream)),
                "kpm_aug_spmmv")
+
+    def aug_spmmv_static(self, R, V, W, eta_dev, init=False, with_imag=True, stream=None):
+        """kpm_aug_spmmv_static: the sweep with its scratch in the library's
+        fixed device array (no allocation inside the call)."""
+        eta_p = ctypes.c_void_p(eta_dev.data_ptr()) if eta_dev is not None else None
+        _check(lib.kpm_aug_spmmv_static(self.handle, R, ctypes.c_void_p(V.data_ptr()),
+                                        ctypes.c_void_p(W.data_ptr()), eta_p, 1 if init else 0,
+                                        1 if with_imag else 0, _stream_ptr(stream)),
+               "kpm_aug_spmmv_static")
 
     def moments_device(self, M, R, seed, eta_dev, eta_imag_dev=None, stream=None):
         _check(lib.kpm_moments_device(
