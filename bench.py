@@ -461,6 +461,23 @@ def bench_reference(args, world, rank):
     print(json.dumps(out))
 
 
+def profile_sweeps(args):
+    """A short program for ncu: 3 warm-up sweeps, then --kernel-launches
+    sweeps of the 64^3 lattice at R = 32 in one form, nothing else."""
+    import torch
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm
+    cfg = workloads.TI_64 if args.profile_sweeps == "fp64" else workloads.TI_64_FP32
+    h, a, b = ti_problem(cfg)
+    prec = kpm.PREC_FP64 if args.profile_sweeps == "fp64" else kpm.PREC_FP32
+    ctx = kpm.create(h, a, b, precision=prec, chunk_height=32, sigma=256)
+    t = kernel_only(ctx, cfg["R"], args.kernel_launches, torch.cuda.current_stream())
+    print(json.dumps({"profile_sweeps": args.profile_sweeps, "launch": ctx.get_launch(cfg["R"]),
+                      "avg_launch_ms": round(t * 1e3, 4)}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,7 +489,12 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-oracle-accuracy", action="store_true")
+    ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
+                    help="only run a few sweep launches of one form (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_sweeps:
+        profile_sweeps(args)
+        return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     world, rank, local = dist_setup()

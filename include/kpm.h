@@ -263,11 +263,13 @@ int kpm_aug_spmmv_static(kpm_ctx *ctx, int32_t R, const void *V, void *W, double
 int kpm_moments_device(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
                        double *eta_imag_dev, void *stream);
 
-/* Launch variant the context uses for block width R: lanes per row,
- * complex columns per lane, threads per block and blocks per SM, as chosen
- * by the defaults or the autotuner. */
+/* Launch variant the context uses for block width R: lanes per row (T),
+ * complex columns per lane (E, T*E = R), threads per block, blocks per SM
+ * (0 = occupancy maximum) and row groups per warp in one block tile (a
+ * tile is threads/32 * (32/T) * tile_groups consecutive rows; 0 = 4), as
+ * chosen by the defaults or the autotuner. */
 typedef struct kpm_launch {
-    int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm;
+    int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
 } kpm_launch;
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */

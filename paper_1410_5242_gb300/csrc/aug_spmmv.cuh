@@ -38,6 +38,16 @@ namespace kpm {
 #ifndef KPM_SWEEP_MAX_THREADS
 #define KPM_SWEEP_MAX_THREADS 256
 #endif
+#ifndef KPM_SWEEP_INDEX_RUN
+#define KPM_SWEEP_INDEX_RUN 4
+#endif
+#ifndef KPM_SWEEP_MIN_BLOCKS
+#define KPM_SWEEP_MIN_BLOCKS 2
+#endif
+#ifndef KPM_SWEEP_PREFETCH
+#define KPM_SWEEP_PREFETCH 1
+#endif
+
 
 // ---------------------------------------------------------------- loads
 // N reals from read-only memory as 16-byte (or one 8-byte) accesses.
@@ -95,25 +105,71 @@ __device__ __forceinline__ void store(Real *p, const Real (&in)[N])
     }
 }
 
-// ------------------------------------------------------- eta accumulation
+// Bulk prefetch of a contiguous range into L2 (a hint: no completion to
+// wait for).  Start and size must be multiples of 16 bytes.
+__device__ __forceinline__ void prefetch_l2(const void *ptr, uint64_t bytes)
+{
+    const char *p = static_cast<const char *>(ptr);
+    while (bytes > 0) {
+        const uint32_t n = bytes > (1u << 20) ? (1u << 20) : (uint32_t)bytes;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
+        p += n;
+        bytes -= n;
+    }
+}
+
+// The streamed inputs of one block tile (rows [r0, r1)): the SELL entries
+// of the chunks covering it, the old W rows and the tile's own V rows.
+// Every range starts and ends on a multiple of 16 bytes: chunk offsets are
+// multiples of C entries, and a block row holds ld complex numbers with ld
+// even in the float form.
 template <typename Real>
+__device__ __forceinline__ void prefetch_tile(const SweepParams &p, int64_t tile,
+                                              int64_t rows_per_tile, bool read_w)
+{
+    const int64_t r0 = tile * rows_per_tile;
+    const int64_t r1 = min(p.n_pad, r0 + rows_per_tile);
+    if (r0 >= r1)
+        return;
+    const int64_t e0 = __ldg(p.chunk_ptr + (r0 >> p.log2C));
+    const int64_t e1 = __ldg(p.chunk_ptr + ((r1 - 1) >> p.log2C) + 1);
+    constexpr int64_t cplx = 2 * (int64_t)sizeof(Real);
+    if (e1 > e0) {
+        prefetch_l2(static_cast<const char *>(p.val) + e0 * cplx, (e1 - e0) * cplx);
+        if (((e0 | e1) & 3) == 0)
+            prefetch_l2(p.col + e0, (e1 - e0) * 4);
+    }
+    const int64_t row_bytes = (int64_t)p.ld * cplx;
+    if ((row_bytes & 15) == 0) {
+        prefetch_l2(static_cast<const char *>(p.V) + r0 * row_bytes, (r1 - r0) * row_bytes);
+        if (read_w)
+            prefetch_l2(static_cast<const char *>(p.W) + r0 * row_bytes, (r1 - r0) * row_bytes);
+    }
+}
+
+// ------------------------------------------------------- eta accumulation
+// IMAG: also accumulate Im<W|V> (only needed for the Hermiticity check).
+template <typename Real, bool IMAG>
 struct EtaAcc;
 
-template <>
-struct EtaAcc<double> {
+template <bool IMAG>
+struct EtaAcc<double, IMAG> {
     double vv = 0.0, wv = 0.0, wvi = 0.0;
-    __device__ __forceinline__ void add(double wr, double wi, double vr, double vi, bool imag)
+    __device__ __forceinline__ void add(double wr, double wi, double vr, double vi)
     {
         vv = fma(vr, vr, vv);
         vv = fma(vi, vi, vv);
         wv = fma(wr, vr, wv);
         wv = fma(wi, vi, wv);
-        if (imag) {
+        if constexpr (IMAG) {
             wvi = fma(wr, vi, wvi);
             wvi = fma(-wi, vr, wvi);
         }
     }
-    __device__ __forceinline__ double get(int k) const { return k == 0 ? vv : (k == 1 ? wv : wvi); }
+    __device__ __forceinline__ double get(int k) const
+    {
+        return k == 0 ? vv : (k == 1 ? wv : (IMAG ? wvi : 0.0));
+    }
 };
 
 // (hi, lo) += p without rounding loss in the running sum: Knuth's TwoSum
@@ -128,14 +184,14 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p)
     lo = __fadd_rn(lo, e);
 }
 
-template <>
-struct EtaAcc<float> {
+template <bool IMAG>
+struct EtaAcc<float, IMAG> {
     float vv_h = 0.f, vv_l = 0.f, wv_h = 0.f, wv_l = 0.f, wvi_h = 0.f, wvi_l = 0.f;
-    __device__ __forceinline__ void add(float wr, float wi, float vr, float vi, bool imag)
+    __device__ __forceinline__ void add(float wr, float wi, float vr, float vi)
     {
         two_sum_acc(vv_h, vv_l, __fmaf_rn(vr, vr, __fmul_rn(vi, vi)));
         two_sum_acc(wv_h, wv_l, __fmaf_rn(wr, vr, __fmul_rn(wi, vi)));
-        if (imag)
+        if constexpr (IMAG)
             two_sum_acc(wvi_h, wvi_l, __fmaf_rn(wr, vi, -__fmul_rn(wi, vr)));
     }
     __device__ __forceinline__ double get(int k) const
@@ -144,14 +200,16 @@ struct EtaAcc<float> {
             return (double)vv_h + (double)vv_l;
         if (k == 1)
             return (double)wv_h + (double)wv_l;
-        return (double)wvi_h + (double)wvi_l;
+        return IMAG ? (double)wvi_h + (double)wvi_l : 0.0;
     }
 };
 
 // ------------------------------------------------------------------ kernel
-template <typename Real, int T, int E>
-__global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const SweepParams p, const int init)
+template <typename Real, int T, int E, bool IMAG>
+__global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
+    aug_spmmv_kernel(const SweepParams p, const int init)
 {
+    constexpr int NC = KPM_SWEEP_INDEX_RUN;  // entries whose indices are fetched together
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
     constexpr int P = 32 / T;   // rows per warp
     constexpr int RB = T * E;   // columns of this block
@@ -167,13 +225,20 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const 
     const Real *__restrict__ val = static_cast<const Real *>(p.val);
     const Real *__restrict__ V = static_cast<const Real *>(p.V);
     Real *W = static_cast<Real *>(p.W);
-    const bool imag = p.with_imag != 0;
-
-    EtaAcc<Real> acc[E];
+    EtaAcc<Real, IMAG> acc[E];
 
     const int64_t rows_per_tile = (int64_t)nwarps * P * p.tile_groups;
     const int64_t n_tiles = (p.n_pad + rows_per_tile - 1) / rows_per_tile;
+    // One thread keeps the next KPM_SWEEP_PREFETCH tiles of this block
+    // requested in L2, so that the threads' own loads of the streamed data
+    // (matrix, old W, own V rows) are L2 hits rather than DRAM round trips.
+    constexpr int D = KPM_SWEEP_PREFETCH;
+    if (D > 0 && threadIdx.x == 0)
+        for (int k = 0; k < D; k++)
+            prefetch_tile<Real>(p, blockIdx.x + (int64_t)k * gridDim.x, rows_per_tile, !init);
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (D > 0 && threadIdx.x == 0)
+            prefetch_tile<Real>(p, tile + (int64_t)D * gridDim.x, rows_per_tile, !init);
         for (int g = 0; g < p.tile_groups; g++) {
             const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
             if (row >= p.n_pad)
@@ -183,6 +248,8 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const 
             const int len = __ldg(p.chunk_len + ch);
             const int64_t wofs = (row * p.ld + cbase) * 2;
 
+            // Row-invariant loads first: the old W (not read by the initial
+            // sweep) and this row's own V entries for the scalar products.
             Real s[2 * E];
             if (init) {
 #pragma unroll
@@ -194,21 +261,32 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const 
                 for (int k = 0; k < 2 * E; k++)
                     s[k] = -s[k];
             }
+            // Entries in runs of NC: all column indices of a run are fetched
+            // first (one memory latency), then the gathers follow in groups
+            // of NB whose loads are in flight together.
             const int64_t C = (int64_t)Cmask + 1;
-#pragma unroll 4
-            for (int j = 0; j < len; j++) {
-                const int64_t e = e0 + (int64_t)j * C;
-                Real h[2];
-                load_nc<Real, 2>(val + 2 * e, h);
-                const int64_t cj = __ldg(p.col + e);
-                Real v[2 * E];
-                load_nc<Real, 2 * E>(V + (cj * p.ld + cbase) * 2, v);
+            for (int j0 = 0; j0 < len; j0 += NC) {
+                const int nb = min(NC, len - j0);
+                const int64_t eb = e0 + (int64_t)j0 * C;
+                int cj[NC];
 #pragma unroll
-                for (int k = 0; k < E; k++) {
-                    s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
-                    s[2 * k] = fma(-h[1], v[2 * k + 1], s[2 * k]);
-                    s[2 * k + 1] = fma(h[0], v[2 * k + 1], s[2 * k + 1]);
-                    s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
+                for (int q = 0; q < NC; q++)
+                    cj[q] = q < nb ? __ldg(p.col + eb + (int64_t)q * C) : 0;
+#pragma unroll
+                for (int q = 0; q < NC; q++) {
+                    if (q < nb) {
+                        Real h[2];
+                        load_nc<Real, 2>(val + 2 * (eb + (int64_t)q * C), h);
+                        Real v[2 * E];
+                        load_nc<Real, 2 * E>(V + ((int64_t)cj[q] * p.ld + cbase) * 2, v);
+#pragma unroll
+                        for (int k = 0; k < E; k++) {
+                            s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
+                            s[2 * k] = fma(-h[1], v[2 * k + 1], s[2 * k]);
+                            s[2 * k + 1] = fma(h[0], v[2 * k + 1], s[2 * k + 1]);
+                            s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
+                        }
+                    }
                 }
             }
             if (init) {
@@ -217,11 +295,12 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS) aug_spmmv_kernel(const 
                     s[k] *= Real(0.5);
             }
             store<Real, 2 * E>(W + wofs, s);
+            // the row's own V entries (recently touched by the diagonal gather)
             Real vs[2 * E];
             load_nc<Real, 2 * E>(V + wofs, vs);
 #pragma unroll
             for (int k = 0; k < E; k++)
-                acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1], imag);
+                acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
         }
     }
 

@@ -1,5 +1,11 @@
 // Instantiations and launcher of the aug_spmmv sweep for complex double
 // storage (one translation unit per precision so they compile in parallel).
+// The double form is bound by the FP64 pipe: more warps per SM and longer
+// index runs measured best (3.66 ms per sweep at 64^3, R = 32).
+#define KPM_SWEEP_MAX_THREADS 256
+#define KPM_SWEEP_MIN_BLOCKS 3
+#define KPM_SWEEP_INDEX_RUN 8
+#define KPM_SWEEP_PREFETCH 2
 #include "aug_spmmv.cuh"
 
 namespace kpm {
@@ -7,13 +13,16 @@ namespace kpm {
 int launch_sweep_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool init,
                       void *stream)
 {
-    if (s.threads < 32 || s.threads > 512 || (s.threads % 32) || grid < 1)
+    if (s.threads < 32 || s.threads > KPM_SWEEP_MAX_THREADS || (s.threads % 32) || grid < 1)
         return KPM_EINVAL;
     const size_t smem = sweep_smem_bytes<double>(s.threads, s.T * s.E);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
     if (s.T == T_ && s.E == E_) {                                                              \
-        aug_spmmv_kernel<double, T_, E_><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0);       \
+        if (p.with_imag)                                                                       \
+            aug_spmmv_kernel<double, T_, E_, true><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0);  \
+        else                                                                                   \
+            aug_spmmv_kernel<double, T_, E_, false><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0); \
         return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;                         \
     }
     KPM_SHAPES_FP64(KPM_CASE)
@@ -24,10 +33,12 @@ int launch_sweep_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool
 int sweep_max_blocks_per_sm_fp64(const LaunchShape &s)
 {
     int nb = 0;
+    if (s.threads < 32 || s.threads > KPM_SWEEP_MAX_THREADS || (s.threads % 32))
+        return 0;
     const size_t smem = sweep_smem_bytes<double>(s.threads, s.T * s.E);
 #define KPM_CASE(T_, E_)                                                                       \
     if (s.T == T_ && s.E == E_) {                                                              \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aug_spmmv_kernel<double, T_, E_>, \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aug_spmmv_kernel<double, T_, E_, false>, \
                                                           s.threads, smem) != cudaSuccess)    \
             return 0;                                                                          \
         return nb;                                                                             \

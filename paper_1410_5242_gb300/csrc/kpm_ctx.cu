@@ -180,7 +180,6 @@ struct kpm_ctx {
     int64_t eta_doubles = 0;
 
     std::map<int, LaunchShape> shapes;  // per column-block width
-    int tile_groups = 4;
     int64_t launches = 0;  // kernels launched by this context
 };
 
@@ -234,15 +233,16 @@ std::vector<int> column_widths(int R)
 LaunchShape default_shape(const kpm_ctx *c, int RB)
 {
     LaunchShape s;
-    s.threads = 256;
+    s.threads = 128;
     if (c->precision == KPM_PREC_FP64) {
         s.E = RB >= 64 ? 2 : 1;
         s.T = RB / s.E;
     } else {
-        s.E = RB >= 2 ? 2 : 1;
+        s.E = RB >= 4 ? 4 : RB;
         s.T = RB / s.E;
     }
     s.blocks_per_sm = 0;  // 0 = occupancy maximum
+    s.tile_groups = c->precision == KPM_PREC_FP64 ? 4 : 1;
     return s;
 }
 
@@ -333,7 +333,7 @@ SweepParams sweep_params(const kpm_ctx *c, const ColumnBlock &cb, int R, const v
     p.log2C = c->log2C;
     p.ld = (int32_t)block_ld(c, R);
     p.col0 = cb.col0;
-    p.tile_groups = c->tile_groups;
+    p.tile_groups = cb.shape.tile_groups > 0 ? cb.shape.tile_groups : 4;
     p.with_imag = imag ? 1 : 0;
     return p;
 }
@@ -745,6 +745,7 @@ int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)
     out->cols_per_lane = s.E;
     out->block_threads = s.threads;
     out->blocks_per_sm = s.blocks_per_sm;
+    out->tile_groups = s.tile_groups;
     return KPM_OK;
 }
 
@@ -753,10 +754,11 @@ int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
     if (!c || !l || R < 1 || R > 64 || (R & (R - 1)))
         return KPM_EINVAL;
     if (l->lanes_per_row * l->cols_per_lane != R || l->block_threads < 32 ||
-        l->block_threads > KPM_SWEEP_MAX_THREADS || (l->block_threads % 32) ||
-        l->blocks_per_sm < 0)
+        l->block_threads > 1024 || (l->block_threads % 32) ||
+        l->blocks_per_sm < 0 || l->tile_groups < 0 || l->tile_groups > 1024)
         return KPM_EINVAL;
-    LaunchShape s{l->lanes_per_row, l->cols_per_lane, l->block_threads, l->blocks_per_sm};
+    LaunchShape s{l->lanes_per_row, l->cols_per_lane, l->block_threads, l->blocks_per_sm,
+                  l->tile_groups > 0 ? l->tile_groups : 4};
     DeviceGuard guard(c->device);
     if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)
         return KPM_EUNSUPPORTED;

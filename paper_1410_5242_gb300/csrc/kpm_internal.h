@@ -33,7 +33,7 @@ struct SweepParams {
 };
 
 struct LaunchShape {
-    int T, E, threads, blocks_per_sm;
+    int T, E, threads, blocks_per_sm, tile_groups;
 };
 
 // Launch one sweep of the given shape; grid = blocks_per_sm * n_sm.

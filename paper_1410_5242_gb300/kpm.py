@@ -56,7 +56,8 @@ class Info(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("lanes_per_row", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("tile_groups", ctypes.c_int32)]
 
 
 _i32, _i64, _u64, _d = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -274,8 +275,9 @@ class Context:
         _check(lib.kpm_get_launch(self.handle, R, ctypes.byref(l)), "kpm_get_launch")
         return {f: getattr(l, f) for f, _ in Launch._fields_}
 
-    def set_launch(self, R, lanes_per_row, cols_per_lane, block_threads=256, blocks_per_sm=0):
-        l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm)
+    def set_launch(self, R, lanes_per_row, cols_per_lane, block_threads=256, blocks_per_sm=0,
+                   tile_groups=0):
+        l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups)
         _check(lib.kpm_set_launch(self.handle, R, ctypes.byref(l)), "kpm_set_launch")
 
     # -- host-buffer calls
