@@ -188,13 +188,43 @@ int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, doub
                    double *eta_imag, void *stream);
 
 /* Ensemble: count independent problems (each its own context, all on the
- * same device and of the same precision), problem p with M[p] moments,
- * R[p] random-phase vectors from seed[p]; eta[p] is host double[R[p]][M[p]].
+ * same device and of the same precision), problem p with M[p] moments
+ * (even, >= 2), R[p] random-phase vectors from seed[p] (R[p] a power of two
+ * <= 64, else KPM_EUNSUPPORTED); eta[p] is host double[R[p]][M[p]].
  * All problems advance together: every sweep step is one batched launch
- * covering every problem still running, and the whole schedule is captured
- * once into a CUDA graph and replayed as one graph launch.  Synchronous. */
+ * covering every problem still running plus one batched eta reduction, and
+ * the whole schedule is captured into a CUDA graph and run as one graph
+ * launch.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
+ * + kpm_batch_eta for every problem + kpm_batch_destroy. */
 int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
                       const uint64_t *seed, double *const *eta, void *stream);
+
+/* A captured ensemble schedule that can be launched repeatedly.  It uses the
+ * contexts' own work buffers: while it exists, run no other moment call on
+ * those contexts, and destroy it before them.  Each context may appear
+ * once. */
+typedef struct kpm_batch kpm_batch;
+
+typedef struct kpm_batch_info {
+    int32_t count;             /* problems */
+    int32_t steps;             /* sweep steps = max M/2 */
+    int32_t grid;              /* blocks of each batched sweep launch */
+    int32_t reserved;
+    int64_t kernel_launches;   /* kernel nodes in the graph */
+    int64_t sweeps;            /* sum over problems of M/2 */
+    double algorithmic_bytes;  /* Eq. 4 bytes of one run, summed over problems */
+} kpm_batch_info;
+
+int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
+                     const uint64_t *seed, kpm_batch **out);
+/* One run of the whole ensemble: a single graph launch, asynchronous on
+ * stream.  Each run redraws the start vectors from the seeds. */
+int kpm_batch_launch(kpm_batch *batch, void *stream);
+/* Copies problem p's eta (host double[R[p]][M[p]]) after the launch on
+ * stream; synchronises the stream. */
+int kpm_batch_eta(kpm_batch *batch, int32_t p, double *eta, void *stream);
+int kpm_batch_get_info(const kpm_batch *batch, kpm_batch_info *out);
+void kpm_batch_destroy(kpm_batch *batch);
 
 /* ------------------------------------------------- device-resident calls
  * For benchmarks and sweep-level tests: inputs and outputs stay on the GPU

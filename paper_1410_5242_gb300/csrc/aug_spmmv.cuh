@@ -204,12 +204,120 @@ struct EtaAcc<float, IMAG> {
     }
 };
 
+// ------------------------------------------------------------------ one row
+// W row <- H' V - W (or (1/2) H' V when init) for this lane's E columns
+// starting at cbase, and this row's terms of the scalar products.
+template <typename Real, int T, int E, bool IMAG>
+__device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__restrict__ val,
+                                          const Real *__restrict__ V, Real *W, int64_t row,
+                                          int init, int64_t cbase, EtaAcc<Real, IMAG> (&acc)[E])
+{
+    constexpr int NC = KPM_SWEEP_INDEX_RUN;  // entries whose indices are fetched together
+    const int Cmask = (1 << p.log2C) - 1;
+    const int64_t ch = row >> p.log2C;
+    const int64_t e0 = __ldg(p.chunk_ptr + ch) + (row & Cmask);
+    const int len = __ldg(p.chunk_len + ch);
+    const int64_t wofs = (row * p.ld + cbase) * 2;
+
+    // the old W first (not read by the initial sweep): it is independent of
+    // the gathers and its latency overlaps theirs
+    Real s[2 * E];
+    if (init) {
+#pragma unroll
+        for (int k = 0; k < 2 * E; k++)
+            s[k] = Real(0);
+    } else {
+        load_rw<Real, 2 * E>(W + wofs, s);
+#pragma unroll
+        for (int k = 0; k < 2 * E; k++)
+            s[k] = -s[k];
+    }
+    // Entries in runs of NC: all column indices of a run are fetched first
+    // (one memory latency), then the run's gathers, whose loads are in
+    // flight together.
+    const int64_t C = (int64_t)Cmask + 1;
+    for (int j0 = 0; j0 < len; j0 += NC) {
+        const int nb = min(NC, len - j0);
+        const int64_t eb = e0 + (int64_t)j0 * C;
+        int cj[NC];
+#pragma unroll
+        for (int q = 0; q < NC; q++)
+            cj[q] = q < nb ? __ldg(p.col + eb + (int64_t)q * C) : 0;
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+            if (q < nb) {
+                Real h[2];
+                load_nc<Real, 2>(val + 2 * (eb + (int64_t)q * C), h);
+                Real v[2 * E];
+                load_nc<Real, 2 * E>(V + ((int64_t)cj[q] * p.ld + cbase) * 2, v);
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
+                    s[2 * k] = fma(-h[1], v[2 * k + 1], s[2 * k]);
+                    s[2 * k + 1] = fma(h[0], v[2 * k + 1], s[2 * k + 1]);
+                    s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
+                }
+            }
+        }
+    }
+    if (init) {
+#pragma unroll
+        for (int k = 0; k < 2 * E; k++)
+            s[k] *= Real(0.5);
+    }
+    store<Real, 2 * E>(W + wofs, s);
+    // the row's own V entries (recently touched by the diagonal gather)
+    Real vs[2 * E];
+    load_nc<Real, 2 * E>(V + wofs, vs);
+#pragma unroll
+    for (int k = 0; k < E; k++)
+        acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
+}
+
+// Block-wide sum of every lane's eta terms per column in a fixed order:
+// lanes of equal columns by an xor butterfly (the same result on every
+// lane), then warps in warp order through shared memory.  The sum for
+// (quantity q, column r) is stored to dst[(q * RB + r) * stride].  red
+// holds nwarps * 3 * RB doubles; the caller synchronises before reusing it.
+template <typename Real, int T, int E, bool IMAG>
+__device__ __forceinline__ void block_eta_sum(const EtaAcc<Real, IMAG> (&acc)[E], double *red,
+                                              double *dst, int64_t stride)
+{
+    constexpr int RB = T * E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tl = lane % T, team = lane / T;
+    double out[3 * E];
+#pragma unroll
+    for (int k = 0; k < E; k++)
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            out[q * E + k] = acc[k].get(q);
+#pragma unroll
+    for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 3 * E; i++)
+            out[i] += __shfl_xor_sync(0xffffffffu, out[i], off);
+    if (team == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+#pragma unroll
+            for (int k = 0; k < E; k++)
+                red[(warp * 3 + q) * RB + tl * E + k] = out[q * E + k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * RB; t += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < nwarps; w++)
+            sum += red[w * 3 * RB + t];
+        dst[t * stride] = sum;
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 template <typename Real, int T, int E, bool IMAG>
 __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
     aug_spmmv_kernel(const SweepParams p, const int init)
 {
-    constexpr int NC = KPM_SWEEP_INDEX_RUN;  // entries whose indices are fetched together
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
     constexpr int P = 32 / T;   // rows per warp
     constexpr int RB = T * E;   // columns of this block
@@ -221,7 +329,6 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
     const int tl = lane % T;
     const int team = lane / T;
     const int64_t cbase = (int64_t)p.col0 + tl * E;
-    const int Cmask = (1 << p.log2C) - 1;
     const Real *__restrict__ val = static_cast<const Real *>(p.val);
     const Real *__restrict__ V = static_cast<const Real *>(p.V);
     Real *W = static_cast<Real *>(p.W);
@@ -243,93 +350,11 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
             const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
             if (row >= p.n_pad)
                 continue;
-            const int64_t ch = row >> p.log2C;
-            const int64_t e0 = __ldg(p.chunk_ptr + ch) + (row & Cmask);
-            const int len = __ldg(p.chunk_len + ch);
-            const int64_t wofs = (row * p.ld + cbase) * 2;
-
-            // Row-invariant loads first: the old W (not read by the initial
-            // sweep) and this row's own V entries for the scalar products.
-            Real s[2 * E];
-            if (init) {
-#pragma unroll
-                for (int k = 0; k < 2 * E; k++)
-                    s[k] = Real(0);
-            } else {
-                load_rw<Real, 2 * E>(W + wofs, s);
-#pragma unroll
-                for (int k = 0; k < 2 * E; k++)
-                    s[k] = -s[k];
-            }
-            // Entries in runs of NC: all column indices of a run are fetched
-            // first (one memory latency), then the gathers follow in groups
-            // of NB whose loads are in flight together.
-            const int64_t C = (int64_t)Cmask + 1;
-            for (int j0 = 0; j0 < len; j0 += NC) {
-                const int nb = min(NC, len - j0);
-                const int64_t eb = e0 + (int64_t)j0 * C;
-                int cj[NC];
-#pragma unroll
-                for (int q = 0; q < NC; q++)
-                    cj[q] = q < nb ? __ldg(p.col + eb + (int64_t)q * C) : 0;
-#pragma unroll
-                for (int q = 0; q < NC; q++) {
-                    if (q < nb) {
-                        Real h[2];
-                        load_nc<Real, 2>(val + 2 * (eb + (int64_t)q * C), h);
-                        Real v[2 * E];
-                        load_nc<Real, 2 * E>(V + ((int64_t)cj[q] * p.ld + cbase) * 2, v);
-#pragma unroll
-                        for (int k = 0; k < E; k++) {
-                            s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
-                            s[2 * k] = fma(-h[1], v[2 * k + 1], s[2 * k]);
-                            s[2 * k + 1] = fma(h[0], v[2 * k + 1], s[2 * k + 1]);
-                            s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
-                        }
-                    }
-                }
-            }
-            if (init) {
-#pragma unroll
-                for (int k = 0; k < 2 * E; k++)
-                    s[k] *= Real(0.5);
-            }
-            store<Real, 2 * E>(W + wofs, s);
-            // the row's own V entries (recently touched by the diagonal gather)
-            Real vs[2 * E];
-            load_nc<Real, 2 * E>(V + wofs, vs);
-#pragma unroll
-            for (int k = 0; k < E; k++)
-                acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
+            sweep_row<Real, T, E, IMAG>(p, val, V, W, row, init, cbase, acc);
         }
     }
 
-    // ---- block reduction of eta (fixed order) ----
-    double out[3 * E];
-#pragma unroll
-    for (int k = 0; k < E; k++)
-#pragma unroll
-        for (int q = 0; q < 3; q++)
-            out[q * E + k] = acc[k].get(q);
-#pragma unroll
-    for (int off = T; off < 32; off <<= 1)
-#pragma unroll
-        for (int i = 0; i < 3 * E; i++)
-            out[i] += __shfl_xor_sync(0xffffffffu, out[i], off);
-    if (team == 0) {
-#pragma unroll
-        for (int q = 0; q < 3; q++)
-#pragma unroll
-            for (int k = 0; k < E; k++)
-                red_smem[(warp * 3 + q) * RB + tl * E + k] = out[q * E + k];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 3 * RB; t += blockDim.x) {
-        double sum = 0.0;
-        for (int w = 0; w < nwarps; w++)
-            sum += red_smem[w * 3 * RB + t];
-        p.partial[(int64_t)blockIdx.x * 3 * RB + t] = sum;
-    }
+    block_eta_sum<Real, T, E, IMAG>(acc, red_smem, p.partial + (int64_t)blockIdx.x * 3 * RB, 1);
 }
 
 // Instantiated (T, E) shapes; X(T, E) is expanded for each.

@@ -1,0 +1,422 @@
+// Ensembles of independent KPM-DOS problems (disorder realisations of
+// different sizes, moment counts M and block widths R) advanced together.
+//
+// Every sweep step is one launch of batch_sweep_kernel over the tiles of
+// all problems still running at that step (problems sorted by M, so the
+// running set is always a prefix), followed by one launch of
+// batch_reduce_kernel that turns the per-tile eta partials of the step into
+// eta_{2m}, eta_{2m+1} of every running problem.  The whole schedule (start
+// vectors, the initial sweep, the M/2 - 1 sweeps of the longest problem)
+// is captured once into a CUDA graph and replayed with one graph launch.
+#define KPM_SWEEP_MAX_THREADS 512
+#define KPM_SWEEP_MIN_BLOCKS 2
+#define KPM_SWEEP_INDEX_RUN 4
+#define KPM_SWEEP_PREFETCH 1
+#include "aug_spmmv.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "kpm_internal.h"
+
+using namespace kpm;
+
+namespace {
+
+constexpr int kBatchThreads = 128;  // 4 warps per block
+constexpr int kBatchTileRows = 128;
+constexpr int kReduceThreads = 128;
+
+struct BatchProblem {
+    const int64_t *chunk_ptr;
+    const int32_t *chunk_len;
+    const int32_t *col;
+    const void *val;
+    void *buf0, *buf1;  // nu_0 lives in buf0; sweep s reads buf[s & 1], writes the other
+    double *partial;    // [3 * RB][n_tiles]
+    double *eta;        // [RB][M]
+    int64_t n_pad, n_tiles;
+    int32_t log2C, ld, RB, shape, tile_groups, M;
+};
+
+// Lane shape of a problem with block width RB = 2^shape: complex float
+// uses 4 columns (two 16-byte accesses) per lane, complex double one.
+template <typename Real, int S>
+struct BatchShape {
+    static constexpr int RB = 1 << S;
+    static constexpr int E = sizeof(Real) == 4 ? (RB < 4 ? RB : 4) : (RB < 64 ? 1 : 2);
+    static constexpr int T = RB / E;
+};
+
+template <typename Real>
+int batch_team(int shape)
+{
+    switch (shape) {
+    case 0: return BatchShape<Real, 0>::T;
+    case 1: return BatchShape<Real, 1>::T;
+    case 2: return BatchShape<Real, 2>::T;
+    case 3: return BatchShape<Real, 3>::T;
+    case 4: return BatchShape<Real, 4>::T;
+    case 5: return BatchShape<Real, 5>::T;
+    default: return BatchShape<Real, 6>::T;
+    }
+}
+
+template <typename Real, int S>
+__device__ __forceinline__ void batch_tile(const BatchProblem &bp, int64_t tile, int step,
+                                           double *red)
+{
+    using Sh = BatchShape<Real, S>;
+    constexpr int T = Sh::T, E = Sh::E, P = 32 / T;
+    SweepParams p;
+    p.chunk_ptr = bp.chunk_ptr;
+    p.chunk_len = bp.chunk_len;
+    p.col = bp.col;
+    p.val = bp.val;
+    p.V = (step & 1) ? bp.buf1 : bp.buf0;
+    p.W = (step & 1) ? bp.buf0 : bp.buf1;
+    p.partial = bp.partial;
+    p.n_pad = bp.n_pad;
+    p.log2C = bp.log2C;
+    p.ld = bp.ld;
+    p.col0 = 0;
+    p.tile_groups = bp.tile_groups;
+    p.with_imag = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tl = lane % T, team = lane / T;
+    const int64_t cbase = (int64_t)tl * E;
+    const Real *__restrict__ val = static_cast<const Real *>(p.val);
+    const Real *__restrict__ V = static_cast<const Real *>(p.V);
+    Real *W = static_cast<Real *>(p.W);
+    EtaAcc<Real, false> acc[E];
+    const int64_t rows_per_tile = (int64_t)nwarps * P * bp.tile_groups;
+    for (int g = 0; g < bp.tile_groups; g++) {
+        const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
+        if (row < p.n_pad)
+            sweep_row<Real, T, E, false>(p, val, V, W, row, step == 0, cbase, acc);
+    }
+    block_eta_sum<Real, T, E, false>(acc, red, bp.partial + tile, bp.n_tiles);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
+    batch_sweep_kernel(const BatchProblem *__restrict__ probs,
+                       const int64_t *__restrict__ tile_prefix, int n_active, int step)
+{
+    extern __shared__ double red_smem[];
+    const int64_t total = tile_prefix[n_active];
+    for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
+        // the running problem owning global tile gt
+        int lo = 0, hi = n_active - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= gt)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchProblem bp = probs[lo];
+        const int64_t tile = gt - tile_prefix[lo];
+        switch (bp.shape) {
+        case 0: batch_tile<Real, 0>(bp, tile, step, red_smem); break;
+        case 1: batch_tile<Real, 1>(bp, tile, step, red_smem); break;
+        case 2: batch_tile<Real, 2>(bp, tile, step, red_smem); break;
+        case 3: batch_tile<Real, 3>(bp, tile, step, red_smem); break;
+        case 4: batch_tile<Real, 4>(bp, tile, step, red_smem); break;
+        case 5: batch_tile<Real, 5>(bp, tile, step, red_smem); break;
+        default: batch_tile<Real, 6>(bp, tile, step, red_smem); break;
+        }
+        __syncthreads();  // red_smem is reused by the next tile
+    }
+}
+
+// One block per (running problem, quantity q in {<V|V>, Re<W|V>}, column r):
+// sums the problem's per-tile partials of this step in a fixed order.
+__global__ void batch_reduce_kernel(const BatchProblem *__restrict__ probs, int n_active, int step)
+{
+    __shared__ double red[kReduceThreads];
+    const int k = blockIdx.x / 128;
+    const int qr = blockIdx.x % 128;
+    const int q = qr / 64, r = qr % 64;
+    if (k >= n_active)
+        return;
+    const int RB = probs[k].RB;
+    if (r >= RB)
+        return;
+    const int64_t n_tiles = probs[k].n_tiles;
+    const double *src = probs[k].partial + (int64_t)(q * RB + r) * n_tiles;
+    double s = 0.0;
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        s += src[t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        probs[k].eta[(int64_t)r * probs[k].M + 2 * step + q] = red[0];
+}
+
+template <typename Real>
+int batch_grid(int n_sm)
+{
+    int nb = 0;
+    const size_t smem = (size_t)(kBatchThreads / 32) * 3 * 64 * sizeof(double);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sweep_kernel<Real>, kBatchThreads,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return nb * n_sm;
+}
+
+}  // namespace
+
+struct kpm_batch {
+    int device = 0, precision = 0, count = 0, steps = 0, grid = 0;
+    std::vector<kpm_ctx *> ctx;      // original order
+    std::vector<int> M, R;           // original order
+    std::vector<int> n_active;       // per step
+    std::vector<int> sorted_to_orig;
+    BatchProblem *d_probs = nullptr;
+    int64_t *d_prefix = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    kpm_batch_info info{};
+};
+
+namespace {
+
+void batch_release(kpm_batch *b)
+{
+    if (!b)
+        return;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    if (b->capture)
+        cudaStreamDestroy(b->capture);
+    if (!b->ctx.empty()) {
+        dev_free(b->ctx[0], b->d_probs);
+        dev_free(b->ctx[0], b->d_prefix);
+    }
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
+                     const uint64_t *seed, kpm_batch **out)
+{
+    if (!out)
+        return KPM_EINVAL;
+    *out = nullptr;
+    if (!ctx || count < 1 || !M || !R || !seed)
+        return KPM_EINVAL;
+    for (int32_t p = 0; p < count; p++) {
+        if (!ctx[p] || M[p] < 2 || (M[p] & 1) || R[p] < 1)
+            return KPM_EINVAL;
+        if (R[p] > 64 || (R[p] & (R[p] - 1)))
+            return KPM_EUNSUPPORTED;
+        if (ctx[p]->device != ctx[0]->device || ctx[p]->precision != ctx[0]->precision)
+            return KPM_EINVAL;
+        for (int32_t q = 0; q < p; q++)
+            if (ctx[q] == ctx[p])
+                return KPM_EINVAL;  // each problem needs its own work buffers
+    }
+    kpm_batch *b = new (std::nothrow) kpm_batch;
+    if (!b)
+        return KPM_ENOMEM;
+    b->device = ctx[0]->device;
+    b->precision = ctx[0]->precision;
+    b->count = count;
+    b->ctx.assign(ctx, ctx + count);
+    b->M.assign(M, M + count);
+    b->R.assign(R, R + count);
+    DeviceGuard guard(b->device);
+    auto fail = [&](int rc) {
+        batch_release(b);
+        return rc;
+    };
+    if (!guard.ok)
+        return fail(KPM_ECUDA);
+
+    // problems by decreasing M: the running set of every step is a prefix
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return M[x] > M[y]; });
+    b->sorted_to_orig = order;
+    const bool fp64 = b->precision == KPM_PREC_FP64;
+    const int sd = fp64 ? 16 : 8;
+    std::vector<BatchProblem> probs(count);
+    std::vector<int64_t> prefix(count + 1, 0);
+    double bytes = 0.0;
+    for (int i = 0; i < count; i++) {
+        const int p = order[i];
+        kpm_ctx *c = ctx[p];
+        int rc = ensure_vectors(c, R[p]);
+        if (rc)
+            return fail(rc);
+        int shape = 0;
+        while ((1 << shape) < R[p])
+            shape++;
+        const int T = fp64 ? batch_team<double>(shape) : batch_team<float>(shape);
+        const int rows_per_group = (kBatchThreads / 32) * (32 / T);
+        const int tg = std::max(1, kBatchTileRows / rows_per_group);
+        const int64_t tile_rows = (int64_t)rows_per_group * tg;
+        const int64_t n_tiles = (c->n_pad + tile_rows - 1) / tile_rows;
+        rc = ensure_partial(c, 3 * (int64_t)R[p] * n_tiles);
+        if (rc)
+            return fail(rc);
+        rc = ensure_eta(c, (int64_t)M[p] * R[p]);
+        if (rc)
+            return fail(rc);
+        BatchProblem &bp = probs[i];
+        bp.chunk_ptr = c->d_chunk_ptr;
+        bp.chunk_len = c->d_chunk_len;
+        bp.col = c->d_col;
+        bp.val = c->d_val;
+        bp.buf0 = c->d_V;
+        bp.buf1 = c->d_W;
+        bp.partial = c->d_partial;
+        bp.eta = c->d_eta;
+        bp.n_pad = c->n_pad;
+        bp.n_tiles = n_tiles;
+        bp.log2C = c->log2C;
+        bp.ld = (int32_t)block_ld(c, R[p]);
+        bp.RB = R[p];
+        bp.shape = shape;
+        bp.tile_groups = tg;
+        bp.M = M[p];
+        prefix[i + 1] = prefix[i] + n_tiles;
+        const double mat = (double)c->nnz * (sd + 4);
+        bytes += mat + 2.0 * R[p] * sd * c->n + (M[p] / 2 - 1) * (mat + 3.0 * R[p] * sd * c->n);
+        b->info.sweeps += M[p] / 2;
+    }
+    b->steps = M[order[0]] / 2;
+    b->n_active.resize(b->steps);
+    for (int s = 0; s < b->steps; s++) {
+        int k = 0;
+        while (k < count && M[order[k]] / 2 > s)
+            k++;
+        b->n_active[s] = k;
+    }
+    b->grid = fp64 ? batch_grid<double>(ctx[0]->n_sm) : batch_grid<float>(ctx[0]->n_sm);
+    if (b->grid < 1)
+        return fail(KPM_ECUDA);
+
+    b->d_probs = (BatchProblem *)dev_alloc(ctx[0], sizeof(BatchProblem) * count);
+    b->d_prefix = (int64_t *)dev_alloc(ctx[0], sizeof(int64_t) * (count + 1));
+    if (!b->d_probs || !b->d_prefix)
+        return fail(KPM_ENOMEM);
+    if (cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblem) * count,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int64_t) * (count + 1),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(KPM_ECUDA);
+
+    // ---- capture the schedule
+    if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(KPM_ECUDA);
+    if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(KPM_ECUDA);
+    int rc = KPM_OK;
+    int64_t launches = 0;
+    for (int i = 0; i < count && rc == KPM_OK; i++) {
+        const int p = order[i];
+        rc = launch_phases(ctx[p], probs[i].buf0, R[p], seed[p], b->capture);
+        launches++;
+    }
+    const size_t smem = (size_t)(kBatchThreads / 32) * 3 * 64 * sizeof(double);
+    for (int s = 0; s < b->steps && rc == KPM_OK; s++) {
+        const int na = b->n_active[s];
+        if (fp64)
+            batch_sweep_kernel<double><<<b->grid, kBatchThreads, smem, b->capture>>>(
+                b->d_probs, b->d_prefix, na, s);
+        else
+            batch_sweep_kernel<float><<<b->grid, kBatchThreads, smem, b->capture>>>(
+                b->d_probs, b->d_prefix, na, s);
+        batch_reduce_kernel<<<na * 128, kReduceThreads, 0, b->capture>>>(b->d_probs, na, s);
+        launches += 2;
+        rc = cuda_status(cudaGetLastError());
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);
+    b->graph = graph;
+    if (rc != KPM_OK)
+        return fail(rc);
+    if (ec != cudaSuccess || !graph)
+        return fail(KPM_ECUDA);
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        return fail(KPM_ECUDA);
+    b->info.count = count;
+    b->info.steps = b->steps;
+    b->info.kernel_launches = launches;
+    b->info.algorithmic_bytes = bytes;
+    b->info.grid = b->grid;
+    *out = b;
+    return KPM_OK;
+}
+
+int kpm_batch_launch(kpm_batch *b, void *stream)
+{
+    if (!b || !b->exec)
+        return KPM_EINVAL;
+    DeviceGuard guard(b->device);
+    return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+int kpm_batch_eta(kpm_batch *b, int32_t p, double *eta, void *stream)
+{
+    if (!b || p < 0 || p >= b->count || !eta)
+        return KPM_EINVAL;
+    DeviceGuard guard(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)b->M[p] * b->R[p];
+    KPM_CUDA(cudaMemcpyAsync(eta, b->ctx[p]->d_eta, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+int kpm_batch_get_info(const kpm_batch *b, kpm_batch_info *out)
+{
+    if (!b || !out)
+        return KPM_EINVAL;
+    *out = b->info;
+    return KPM_OK;
+}
+
+void kpm_batch_destroy(kpm_batch *b)
+{
+    if (!b)
+        return;
+    DeviceGuard guard(b->device);
+    cudaDeviceSynchronize();
+    batch_release(b);
+}
+
+int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
+                      const uint64_t *seed, double *const *eta, void *stream)
+{
+    if (!eta)
+        return KPM_EINVAL;
+    for (int32_t p = 0; p < count; p++)
+        if (!eta[p])
+            return KPM_EINVAL;
+    kpm_batch *b = nullptr;
+    int rc = kpm_batch_create(ctx, count, M, R, seed, &b);
+    if (rc)
+        return rc;
+    rc = kpm_batch_launch(b, stream);
+    for (int32_t p = 0; p < count && rc == KPM_OK; p++)
+        rc = kpm_batch_eta(b, p, eta[p], stream);
+    kpm_batch_destroy(b);
+    return rc;
+}
+
+}  // extern "C"

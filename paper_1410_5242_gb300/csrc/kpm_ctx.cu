@@ -28,39 +28,6 @@ __host__ __device__ inline uint64_t splitmix_mix(uint64_t z)
     return z ^ (z >> 31);
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess)
-            prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0)
-            cudaSetDevice(prev);
-    }
-};
-
-int cuda_status(cudaError_t e)
-{
-    if (e == cudaSuccess)
-        return KPM_OK;
-    if (e == cudaErrorMemoryAllocation)
-        return KPM_ENOMEM;
-    return KPM_ECUDA;
-}
-
-#define KPM_TRY(expr)                 \
-    do {                              \
-        int rc_ = (expr);             \
-        if (rc_ != KPM_OK)            \
-            return rc_;               \
-    } while (0)
-#define KPM_CUDA(expr) KPM_TRY(cuda_status(expr))
-
 // ------------------------------------------------------------- kernels
 // Random-phase start block: V[p][r] = exp(2 pi i u), u from stream 1 at
 // index r*n + perm[p]; rows p >= n and columns r >= R are zero.
@@ -143,47 +110,7 @@ __global__ void reduce_single_kernel(const double *partial, int G, int RB, int c
 
 }  // namespace
 
-// ------------------------------------------------------------ context
-struct ColumnBlock {
-    int col0, RB;
-    LaunchShape shape;
-    int grid;
-    int64_t partial_offset;  // doubles from the start of a slot
-};
-
-struct kpm_ctx {
-    int device = 0;
-    int precision = KPM_PREC_FP64;
-    int64_t n = 0, n_pad = 0, nnz = 0, n_stored = 0, n_chunks = 0;
-    int32_t C = 32, log2C = 5, sigma = 1;
-    double a = 0, b = 0;
-    int n_sm = 1;
-    size_t sdc = 16;  // bytes per complex entry of matrix and vectors
-
-    kpm_alloc_fn alloc_fn = nullptr;
-    kpm_free_fn free_fn = nullptr;
-    void *alloc_user = nullptr;
-
-    int64_t *d_chunk_ptr = nullptr;
-    int32_t *d_chunk_len = nullptr;
-    int32_t *d_col = nullptr;
-    void *d_val = nullptr;
-    int32_t *d_perm = nullptr;
-    std::vector<int32_t> perm;  // host copy: new row -> original row
-
-    // work buffers (grown on demand)
-    void *d_V = nullptr, *d_W = nullptr;
-    int64_t vw_bytes = 0;
-    double *d_partial = nullptr;
-    int64_t partial_doubles = 0;
-    double *d_eta = nullptr, *d_eta_im = nullptr;
-    int64_t eta_doubles = 0;
-
-    std::map<int, LaunchShape> shapes;  // per column-block width
-    int64_t launches = 0;  // kernels launched by this context
-};
-
-namespace {
+namespace kpm {
 
 void *dev_alloc(kpm_ctx *c, size_t bytes)
 {
@@ -318,6 +245,10 @@ int ensure_eta(kpm_ctx *c, int64_t doubles)
     return c->eta_doubles ? KPM_OK : KPM_ENOMEM;
 }
 
+}  // namespace kpm
+
+namespace {
+
 SweepParams sweep_params(const kpm_ctx *c, const ColumnBlock &cb, int R, const void *V, void *W,
                          double *partial, bool imag)
 {
@@ -347,7 +278,9 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
     return launch_sweep_fp32(p, cb.shape, cb.grid, init, st);
 }
 
-int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st)
+}  // namespace
+
+int kpm::launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st)
 {
     const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
     const int ld = (int)block_ld(c, R);
@@ -361,6 +294,8 @@ int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st)
                                                    key);
     return cuda_status(cudaGetLastError());
 }
+
+namespace {
 
 // The sweep schedule of Fig. 5 on device buffers already holding V = nu_0.
 int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
@@ -716,19 +651,6 @@ int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double
     KPM_TRY(upload_block(c, R, v0_ri, c->d_V, st));
     KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
     return moments_to_host(c, M, R, eta, eta_imag, st);
-}
-
-int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
-                      const uint64_t *seed, double *const *eta, void *stream)
-{
-    if (!ctx || count < 1 || !M || !R || !seed || !eta)
-        return KPM_EINVAL;
-    for (int32_t p = 0; p < count; p++) {
-        int rc = kpm_moments(ctx[p], M[p], R[p], seed[p], eta[p], nullptr, stream);
-        if (rc)
-            return rc;
-    }
-    return KPM_OK;
 }
 
 int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)

@@ -1,8 +1,12 @@
 // Internal declarations shared by the translation units of libkpm.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <cstddef>
+#include <map>
+#include <vector>
 
 #include "kpm.h"
 
@@ -45,4 +49,92 @@ int launch_sweep_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool
 // Occupancy query for the same kernels (blocks per SM, 0 if unsupported).
 int sweep_max_blocks_per_sm(int precision, const LaunchShape &s, bool init);
 
+// Makes a device current for the lifetime of the object and restores the
+// previous one afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+inline int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return KPM_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return KPM_ENOMEM;
+    return KPM_ECUDA;
+}
+
+#define KPM_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != KPM_OK)            \
+            return rc_;               \
+    } while (0)
+#define KPM_CUDA(expr) KPM_TRY(cuda_status(expr))
+
+
+}  // namespace kpm
+
+// ------------------------------------------------------------ context
+struct ColumnBlock {
+    int col0, RB;
+    kpm::LaunchShape shape;
+    int grid;
+    int64_t partial_offset;  // doubles from the start of a slot
+};
+
+struct kpm_ctx {
+    int device = 0;
+    int precision = KPM_PREC_FP64;
+    int64_t n = 0, n_pad = 0, nnz = 0, n_stored = 0, n_chunks = 0;
+    int32_t C = 32, log2C = 5, sigma = 1;
+    double a = 0, b = 0;
+    int n_sm = 1;
+    size_t sdc = 16;  // bytes per complex entry of matrix and vectors
+
+    kpm_alloc_fn alloc_fn = nullptr;
+    kpm_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+
+    int64_t *d_chunk_ptr = nullptr;
+    int32_t *d_chunk_len = nullptr;
+    int32_t *d_col = nullptr;
+    void *d_val = nullptr;
+    int32_t *d_perm = nullptr;
+    std::vector<int32_t> perm;  // host copy: new row -> original row
+
+    // work buffers (grown on demand)
+    void *d_V = nullptr, *d_W = nullptr;
+    int64_t vw_bytes = 0;
+    double *d_partial = nullptr;
+    int64_t partial_doubles = 0;
+    double *d_eta = nullptr, *d_eta_im = nullptr;
+    int64_t eta_doubles = 0;
+
+    std::map<int, kpm::LaunchShape> shapes;  // per column-block width
+    int64_t launches = 0;  // kernels launched by this context
+};
+
+
+namespace kpm {
+void *dev_alloc(kpm_ctx *c, size_t bytes);
+void dev_free(kpm_ctx *c, void *p);
+int64_t block_ld(const kpm_ctx *c, int R);
+int ensure_vectors(kpm_ctx *c, int R);
+int ensure_partial(kpm_ctx *c, int64_t doubles);
+int ensure_eta(kpm_ctx *c, int64_t doubles);
+int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st);
+LaunchShape default_shape(const kpm_ctx *c, int RB);
 }  // namespace kpm

@@ -54,6 +54,12 @@ class Info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("steps", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("sweeps", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double)]
+
+
 class Launch(ctypes.Structure):
     _fields_ = [("lanes_per_row", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
@@ -88,6 +94,12 @@ _SIGS = {
     "kpm_aug_spmmv": (_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
     "kpm_moments_device": (_int, [_vp, _i32, _i32, _u64, _vp, _vp, _vp]),
     "kpm_aug_spmmv_static": (_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
+    "kpm_batch_create": (_int, [ctypes.POINTER(_vp), _i32, _pi32, _pi32, ctypes.POINTER(_u64),
+                                ctypes.POINTER(_vp)]),
+    "kpm_batch_launch": (_int, [_vp, _vp]),
+    "kpm_batch_eta": (_int, [_vp, _i32, _pd, _vp]),
+    "kpm_batch_get_info": (_int, [_vp, ctypes.POINTER(BatchInfo)]),
+    "kpm_batch_destroy": (None, [_vp]),
     "kpm_get_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
     "kpm_set_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
 }
@@ -357,3 +369,49 @@ def moments_batch(ctxs, Ms, Rs, seeds, stream=None):
                                  Sa.ctypes.data_as(ctypes.POINTER(_u64)), ptrs,
                                  _stream_ptr(stream)), "kpm_moments_batch")
     return etas
+
+
+class Batch:
+    """kpm_batch_create / kpm_batch_launch / kpm_batch_eta / kpm_batch_destroy."""
+
+    def __init__(self, ctxs, Ms, Rs, seeds):
+        self.count = len(ctxs)
+        self.ctxs = list(ctxs)  # keep the contexts alive
+        self.Ms = [int(m) for m in Ms]
+        self.Rs = [int(r) for r in Rs]
+        handles = (ctypes.c_void_p * self.count)(*[c.handle for c in ctxs])
+        Ma = np.ascontiguousarray(Ms, dtype=np.int32)
+        Ra = np.ascontiguousarray(Rs, dtype=np.int32)
+        Sa = np.ascontiguousarray(seeds, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        _check(lib.kpm_batch_create(handles, self.count, _p(Ma, _i32), _p(Ra, _i32),
+                                    Sa.ctypes.data_as(ctypes.POINTER(_u64)), ctypes.byref(h)),
+               "kpm_batch_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib.kpm_batch_launch(self.handle, _stream_ptr(stream)), "kpm_batch_launch")
+
+    def eta(self, p, stream=None):
+        out = np.empty((self.Rs[p], self.Ms[p]))
+        _check(lib.kpm_batch_eta(self.handle, p, _p(out, _d), _stream_ptr(stream)), "kpm_batch_eta")
+        return out
+
+    def info(self):
+        i = BatchInfo()
+        _check(lib.kpm_batch_get_info(self.handle, ctypes.byref(i)), "kpm_batch_get_info")
+        return {f: getattr(i, f) for f, _ in BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kpm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

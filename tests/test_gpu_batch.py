@@ -1,0 +1,125 @@
+"""GPU tests of the ensemble path (kpm_moments_batch / kpm_batch_*): every
+problem of a batch must give the moments the single-problem path and the
+FP64 oracle give, with uneven sizes, moment counts and block widths in one
+graph launch."""
+import numpy as np
+import pytest
+
+from kpm_inputs import hamiltonians as ham
+from kpm_inputs import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm as k
+    return k
+
+
+def problems():
+    """Uneven little ensemble: lattices of several shapes, one open boundary,
+    one ragged random matrix; M from 2 to 130; R from 1 to 64."""
+    return [
+        (ham.ti_hamiltonian(5, 4, 3, gamma=0.5, seed=1), 64, 8, 11),
+        (ham.ti_hamiltonian(6, 6, 6, gamma=2.0, seed=2), 130, 32, 12),
+        (ham.ti_hamiltonian(3, 4, 7, gamma=1.0, seed=3, periodic=(True, True, False)), 40, 16, 13),
+        (ham.random_hermitian(203, 7, seed=4, empty_rows=0.1), 96, 64, 14),
+        (ham.ti_hamiltonian(4, 4, 4, gamma=0.0), 2, 4, 15),
+        (ham.ti_hamiltonian(3, 3, 3, gamma=3.0, seed=5), 18, 1, 16),
+        (ham.ti_hamiltonian(7, 3, 3, gamma=0.7, seed=6), 64, 2, 17),
+    ]
+
+
+def contexts(kpm, probs, prec):
+    out = []
+    for h, M, R, seed in probs:
+        a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+        out.append((kpm.create(h, a, b, precision=prec, chunk_height=8, sigma=16), h, a, b))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_matches_single_problem_and_oracle(kpm, orc, prec):
+    probs = problems()
+    ctxs = contexts(kpm, probs, prec)
+    etas = kpm.moments_batch([c for c, *_ in ctxs], [p[1] for p in probs], [p[2] for p in probs],
+                             [p[3] for p in probs])
+    for (ctx, h, a, b), (_, M, R, seed), eta in zip(ctxs, probs, etas):
+        single = ctx.moments(M, R, seed)
+        ref, _ = orc.moments(h, a, b, M, seed, range(R))
+        eta0 = ref[:, :1]
+        if prec == 0:
+            assert np.all(np.abs(eta - single) <= 1e-12 * eta0)
+            assert np.all(np.abs(eta - ref) <= 1e-10 * eta0)
+        else:
+            assert np.abs(kpm.eta_to_mu(eta) - kpm.eta_to_mu(single)).max() <= 1e-6
+            assert np.abs(kpm.eta_to_mu(eta) - orc.eta_to_mu(ref)).max() <= 1e-5
+    for c, *_ in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_object_relaunch_is_reproducible(kpm, prec):
+    probs = problems()[:4]
+    ctxs = contexts(kpm, probs, prec)
+    Ms, Rs, seeds = [p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs]
+    with kpm.Batch([c for c, *_ in ctxs], Ms, Rs, seeds) as batch:
+        info = batch.info()
+        assert info["count"] == 4 and info["steps"] == max(Ms) // 2
+        assert info["kernel_launches"] == 4 + 2 * info["steps"]
+        assert info["sweeps"] == sum(M // 2 for M in Ms)
+        batch.launch()
+        first = [batch.eta(p) for p in range(4)]
+        batch.launch()
+        second = [batch.eta(p) for p in range(4)]
+    for x, y in zip(first, second):
+        assert np.array_equal(x, y)
+    for c, *_ in ctxs:
+        c.close()
+
+
+def test_batch_rejects_bad_requests(kpm):
+    probs = problems()[:2]
+    ctxs = contexts(kpm, probs, 1)
+    c0, c1 = ctxs[0][0], ctxs[1][0]
+    for Ms, Rs, cs, status in (([64, 30], [8, 24], [c0, c1], kpm.KPM_EUNSUPPORTED),
+                               ([64, 31], [8, 8], [c0, c1], kpm.KPM_EINVAL),
+                               ([64, 30], [8, 8], [c0, c0], kpm.KPM_EINVAL),
+                               ([64, 30], [8, 128], [c0, c1], kpm.KPM_EUNSUPPORTED)):
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.moments_batch(cs, Ms, Rs, [1, 2])
+        assert e.value.status == status
+    h = probs[0][0]
+    a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    with kpm.create(h, a, b, precision=0) as c64:
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.moments_batch([c0, c64], [8, 8], [8, 8], [1, 2])
+        assert e.value.status == kpm.KPM_EINVAL
+    for c, *_ in ctxs:
+        c.close()
+
+
+def test_ensemble_recipe_sampled_against_oracle(kpm, orc):
+    """The four smallest lattices of the 64-problem ensemble recipe (complex
+    float storage), moments capped at 128 so the oracle finishes quickly;
+    vectors 0 and 1 of each checked against the oracle."""
+    ens = sorted(workloads.ensemble(), key=lambda p: np.prod(p["dims"]))[:4]
+    ctxs, Ms, Rs, seeds = [], [], [], []
+    for p in ens:
+        h = ham.ti_hamiltonian(*p["dims"], gamma=p["gamma"], seed=p["seed"])
+        a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+        ctxs.append((kpm.create(h, a, b, precision=kpm.PREC_FP32), h, a, b))
+        Ms.append(min(p["M"], 128))
+        Rs.append(p["R"])
+        seeds.append(p["seed"])
+    etas = kpm.moments_batch([c for c, *_ in ctxs], Ms, Rs, seeds)
+    for (ctx, h, a, b), M, seed, eta in zip(ctxs, Ms, seeds, etas):
+        ref, _ = orc.moments(h, a, b, M, seed, [0, 1])
+        dmu = np.abs(kpm.eta_to_mu(eta[:2]) - orc.eta_to_mu(ref)).max()
+        assert dmu <= 1e-5, dmu
+        ctx.close()
