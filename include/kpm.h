@@ -69,7 +69,8 @@ typedef struct kpm_options {
     int32_t chunk_height;     /* SELL chunk height C (rows per chunk); 0 = 32 */
     int32_t sigma;            /* SELL sorting window sigma (rows); 0 = 256, 1 = no sort */
     int32_t check_hermitian;  /* nonzero: kpm_create verifies H == H^dagger (1e-12 rel) */
-    int32_t autotune;         /* nonzero: kpm_create times the launch variants and keeps the fastest */
+    int32_t autotune;         /* nonzero: the first moment call for a block width R times the
+                                 launch variants (kpm_autotune) and keeps the fastest */
     int32_t device;           /* CUDA device ordinal */
     kpm_alloc_fn alloc_fn;    /* NULL = cudaMalloc */
     kpm_free_fn free_fn;      /* NULL = cudaFree */
@@ -304,6 +305,29 @@ typedef struct kpm_launch {
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */
 int kpm_set_launch(kpm_ctx *ctx, int32_t R, const kpm_launch *launch);
+
+/* Autotuner for block width R: times `sweeps` aug_spmmv sweeps (after two
+ * untimed ones) on the context's work blocks for every built launch shape
+ * -- lanes per row T and columns per lane E with T*E = width, 128..512
+ * threads per block, 1 or 4 row groups per tile -- and for the widest
+ * column block (64, 32 or 16 columns, R split into powers of two up to
+ * it), and keeps the fastest for later calls.  best (may be NULL) receives
+ * the shape chosen for the widest block.  Synchronises stream. */
+int kpm_autotune(kpm_ctx *ctx, int32_t R, int32_t sweeps, void *stream, kpm_launch *best);
+
+/* Widest column block the context uses (64 unless the autotuner chose
+ * less). */
+int kpm_get_max_block_width(const kpm_ctx *ctx);
+
+/* Layout autotuner: builds trial contexts with SELL chunk heights C in
+ * {8, 32, 128} and, for matrices with rows of different lengths, sorting
+ * windows sigma in {1, 256, 4096}, tunes the launch shape of each for width
+ * R (as kpm_autotune) and returns in *best the options of the fastest
+ * (base's other fields kept, autotune set) and its time per sweep in
+ * *best_ms (may be NULL).  Costs one kpm_create per trial. */
+int kpm_autotune_layout(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                        const double *val_ri, double a, double b, const kpm_options *base,
+                        int32_t R, int32_t sweeps, kpm_options *best, double *best_ms);
 
 #ifdef __cplusplus
 }

@@ -147,6 +147,73 @@ __device__ __forceinline__ void prefetch_tile(const SweepParams &p, int64_t tile
     }
 }
 
+// ------------------------------------------------------ column ownership
+// A lane owns E complex columns of its row as NP pieces of EV consecutive
+// complex numbers (EV = 2 for complex float, so a piece is one 16-byte
+// access; EV = 1 for complex double).  Piece k of team lane tl starts at
+// column k*T*EV + tl*EV, so the T lanes of a team read one contiguous
+// T*EV-column span per access: a row's 16-byte pieces are interleaved
+// across the team instead of each lane owning a contiguous E-column run,
+// which halves the cache lines one warp access touches.
+template <typename Real, int E>
+struct Pieces {
+    static constexpr int EV = (sizeof(Real) == 4 && E % 2 == 0) ? 2 : 1;
+    static constexpr int NP = E / EV;
+};
+
+// Column (within the block) of accumulator k of team lane tl.
+template <typename Real, int T, int E>
+__device__ __forceinline__ int owned_column(int tl, int k)
+{
+    constexpr int EV = Pieces<Real, E>::EV;
+    return (k / EV) * T * EV + tl * EV + (k % EV);
+}
+
+// E complex numbers of a row whose pieces start at base (complex units),
+// base + T*EV, ...; read-only and read-write variants, and the store.
+template <typename Real, int T, int E>
+__device__ __forceinline__ void load_owned_nc(const Real *__restrict__ p, int64_t base,
+                                              Real (&out)[2 * E])
+{
+    constexpr int EV = Pieces<Real, E>::EV, NP = Pieces<Real, E>::NP;
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+        Real piece[2 * EV];
+        load_nc<Real, 2 * EV>(p + (base + (int64_t)k * T * EV) * 2, piece);
+#pragma unroll
+        for (int i = 0; i < 2 * EV; i++)
+            out[k * 2 * EV + i] = piece[i];
+    }
+}
+
+template <typename Real, int T, int E>
+__device__ __forceinline__ void load_owned_rw(const Real *p, int64_t base, Real (&out)[2 * E])
+{
+    constexpr int EV = Pieces<Real, E>::EV, NP = Pieces<Real, E>::NP;
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+        Real piece[2 * EV];
+        load_rw<Real, 2 * EV>(p + (base + (int64_t)k * T * EV) * 2, piece);
+#pragma unroll
+        for (int i = 0; i < 2 * EV; i++)
+            out[k * 2 * EV + i] = piece[i];
+    }
+}
+
+template <typename Real, int T, int E>
+__device__ __forceinline__ void store_owned(Real *p, int64_t base, const Real (&in)[2 * E])
+{
+    constexpr int EV = Pieces<Real, E>::EV, NP = Pieces<Real, E>::NP;
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+        Real piece[2 * EV];
+#pragma unroll
+        for (int i = 0; i < 2 * EV; i++)
+            piece[i] = in[k * 2 * EV + i];
+        store<Real, 2 * EV>(p + (base + (int64_t)k * T * EV) * 2, piece);
+    }
+}
+
 // ------------------------------------------------------- eta accumulation
 // IMAG: also accumulate Im<W|V> (only needed for the Hermiticity check).
 template <typename Real, bool IMAG>
@@ -205,8 +272,9 @@ struct EtaAcc<float, IMAG> {
 };
 
 // ------------------------------------------------------------------ one row
-// W row <- H' V - W (or (1/2) H' V when init) for this lane's E columns
-// starting at cbase, and this row's terms of the scalar products.
+// W row <- H' V - W (or (1/2) H' V when init) for this lane's E owned
+// columns (pieces from column cbase on, see owned_column), and this row's
+// terms of the scalar products.
 template <typename Real, int T, int E, bool IMAG>
 __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__restrict__ val,
                                           const Real *__restrict__ V, Real *W, int64_t row,
@@ -217,7 +285,7 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
     const int64_t ch = row >> p.log2C;
     const int64_t e0 = __ldg(p.chunk_ptr + ch) + (row & Cmask);
     const int len = __ldg(p.chunk_len + ch);
-    const int64_t wofs = (row * p.ld + cbase) * 2;
+    const int64_t wbase = row * p.ld + cbase;
 
     // the old W first (not read by the initial sweep): it is independent of
     // the gathers and its latency overlaps theirs
@@ -227,7 +295,7 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
         for (int k = 0; k < 2 * E; k++)
             s[k] = Real(0);
     } else {
-        load_rw<Real, 2 * E>(W + wofs, s);
+        load_owned_rw<Real, T, E>(W, wbase, s);
 #pragma unroll
         for (int k = 0; k < 2 * E; k++)
             s[k] = -s[k];
@@ -249,7 +317,7 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
                 Real h[2];
                 load_nc<Real, 2>(val + 2 * (eb + (int64_t)q * C), h);
                 Real v[2 * E];
-                load_nc<Real, 2 * E>(V + ((int64_t)cj[q] * p.ld + cbase) * 2, v);
+                load_owned_nc<Real, T, E>(V, (int64_t)cj[q] * p.ld + cbase, v);
 #pragma unroll
                 for (int k = 0; k < E; k++) {
                     s[2 * k] = fma(h[0], v[2 * k], s[2 * k]);
@@ -265,10 +333,10 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
         for (int k = 0; k < 2 * E; k++)
             s[k] *= Real(0.5);
     }
-    store<Real, 2 * E>(W + wofs, s);
+    store_owned<Real, T, E>(W, wbase, s);
     // the row's own V entries (recently touched by the diagonal gather)
     Real vs[2 * E];
-    load_nc<Real, 2 * E>(V + wofs, vs);
+    load_owned_nc<Real, T, E>(V, wbase, vs);
 #pragma unroll
     for (int k = 0; k < E; k++)
         acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
@@ -302,7 +370,7 @@ __device__ __forceinline__ void block_eta_sum(const EtaAcc<Real, IMAG> (&acc)[E]
         for (int q = 0; q < 3; q++)
 #pragma unroll
             for (int k = 0; k < E; k++)
-                red[(warp * 3 + q) * RB + tl * E + k] = out[q * E + k];
+                red[(warp * 3 + q) * RB + owned_column<Real, T, E>(tl, k)] = out[q * E + k];
     }
     __syncthreads();
     for (int t = threadIdx.x; t < 3 * RB; t += blockDim.x) {
@@ -328,7 +396,7 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
     const int nwarps = blockDim.x >> 5;
     const int tl = lane % T;
     const int team = lane / T;
-    const int64_t cbase = (int64_t)p.col0 + tl * E;
+    const int64_t cbase = (int64_t)p.col0 + tl * Pieces<Real, E>::EV;
     const Real *__restrict__ val = static_cast<const Real *>(p.val);
     const Real *__restrict__ V = static_cast<const Real *>(p.V);
     Real *W = static_cast<Real *>(p.W);

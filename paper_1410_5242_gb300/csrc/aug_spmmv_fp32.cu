@@ -3,11 +3,19 @@
 // The float form is bound by memory-level parallelism: 64 registers per
 // thread (up to 16 warps of gathers in flight per SM at 512 threads),
 // index runs of 4 entries and an L2 bulk prefetch one tile ahead measured
-// best (0.385 ms per sweep at 64^3, R = 32).
+// best (0.376 ms per sweep at 64^3, R = 32).
+#ifndef KPM_SWEEP_MAX_THREADS
 #define KPM_SWEEP_MAX_THREADS 512
+#endif
+#ifndef KPM_SWEEP_MIN_BLOCKS
 #define KPM_SWEEP_MIN_BLOCKS 2
+#endif
+#ifndef KPM_SWEEP_INDEX_RUN
 #define KPM_SWEEP_INDEX_RUN 4
+#endif
+#ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1
+#endif
 #include "aug_spmmv.cuh"
 
 namespace kpm {

@@ -86,7 +86,7 @@ __device__ __forceinline__ void batch_tile(const BatchProblem &bp, int64_t tile,
     p.with_imag = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int tl = lane % T, team = lane / T;
-    const int64_t cbase = (int64_t)tl * E;
+    const int64_t cbase = (int64_t)tl * Pieces<Real, E>::EV;
     const Real *__restrict__ val = static_cast<const Real *>(p.val);
     const Real *__restrict__ V = static_cast<const Real *>(p.V);
     Real *W = static_cast<Real *>(p.W);

@@ -143,13 +143,14 @@ int64_t block_ld(const kpm_ctx *c, int R)
     return R;
 }
 
-// Column blocks: R split into powers of two <= 64, widest first, so each
-// block starts on a column that keeps its vector accesses aligned.
-std::vector<int> column_widths(int R)
+// Column blocks: R split into powers of two <= cap (64 by default), widest
+// first, so each block starts on a column that keeps its vector accesses
+// aligned.
+std::vector<int> column_widths(int R, int cap)
 {
     std::vector<int> w;
     int rest = R;
-    for (int b = 64; b >= 1; b >>= 1)
+    for (int b = cap; b >= 1; b >>= 1)
         while (rest >= b) {
             w.push_back(b);
             rest -= b;
@@ -189,7 +190,7 @@ int plan_blocks(kpm_ctx *c, int R, std::vector<ColumnBlock> &blocks, int64_t &sl
     blocks.clear();
     slot_doubles = 0;
     int col0 = 0;
-    for (int RB : column_widths(R)) {
+    for (int RB : column_widths(R, c->max_rb)) {
         ColumnBlock cb;
         cb.col0 = col0;
         cb.RB = RB;
@@ -296,6 +297,8 @@ int kpm::launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t s
 }
 
 namespace {
+
+int autotune_shapes(kpm_ctx *c, int R, int sweeps, cudaStream_t st, float *ms_per_sweep = nullptr);
 
 // The sweep schedule of Fig. 5 on device buffers already holding V = nu_0.
 int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
@@ -437,6 +440,7 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
     c->a = a;
     c->b = b;
     c->sdc = opt.precision == KPM_PREC_FP64 ? 16 : 8;
+    c->autotune = opt.autotune;
     c->alloc_fn = opt.alloc_fn;
     c->free_fn = opt.free_fn;
     c->alloc_user = opt.alloc_user;
@@ -608,6 +612,8 @@ int kpm_moments_device(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *
         return KPM_EINVAL;
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->autotune && !c->tuned.count(R))
+        KPM_TRY(autotune_shapes(c, R, 5, st));
     KPM_TRY(ensure_vectors(c, R));
     KPM_TRY(launch_phases(c, c->d_V, R, seed, st));
     return run_schedule(c, M, R, eta_dev, eta_imag_dev, st);
@@ -633,6 +639,8 @@ int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, do
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    if (c->autotune && !c->tuned.count(R))
+        KPM_TRY(autotune_shapes(c, R, 5, st));
     KPM_TRY(ensure_vectors(c, R));
     KPM_TRY(launch_phases(c, c->d_V, R, seed, st));
     KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
@@ -647,10 +655,215 @@ int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    if (c->autotune && !c->tuned.count(R))
+        KPM_TRY(autotune_shapes(c, R, 5, st));
     KPM_TRY(ensure_vectors(c, R));
     KPM_TRY(upload_block(c, R, v0_ri, c->d_V, st));
     KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
     return moments_to_host(c, M, R, eta, eta_imag, st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ autotuner
+namespace {
+
+// Candidate launch shapes for a column block of width RB.
+std::vector<LaunchShape> shape_candidates(const kpm_ctx *c, int RB)
+{
+    std::vector<LaunchShape> out;
+    const int max_threads = c->precision == KPM_PREC_FP64 ? 256 : 512;
+    for (int E = 1; E <= 4; E <<= 1) {
+        if (RB % E)
+            continue;
+        const int T = RB / E;
+        if (T < 1 || T > 32)
+            continue;
+        for (int threads = 128; threads <= max_threads; threads <<= 1)
+            for (int tg : {1, 4}) {
+                LaunchShape s{T, E, threads, 0, tg};
+                if (sweep_max_blocks_per_sm(c->precision, s, false) > 0)
+                    out.push_back(s);
+            }
+    }
+    return out;
+}
+
+// Average time of `sweeps` non-initial sweeps of one column block with
+// shape s (V, W are the context's work blocks holding a recurrence).
+int time_block(kpm_ctx *c, int R, int col0, int RB, LaunchShape s, int sweeps, cudaStream_t st,
+               cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    ColumnBlock cb;
+    cb.col0 = col0;
+    cb.RB = RB;
+    cb.shape = s;
+    cb.grid = resolve_grid(c, cb.shape);
+    if (cb.grid < 1)
+        return KPM_EUNSUPPORTED;
+    cb.partial_offset = 0;
+    KPM_TRY(ensure_partial(c, (int64_t)cb.grid * 3 * RB));
+    void *V = c->d_V, *W = c->d_W;
+    for (int k = 0; k < 2 + sweeps; k++) {
+        if (k == 2)
+            KPM_CUDA(cudaEventRecord(e0, st));
+        SweepParams p = sweep_params(c, cb, R, V, W, c->d_partial, false);
+        KPM_TRY(launch_one(c, cb, p, false, st));
+        std::swap(V, W);
+    }
+    KPM_CUDA(cudaEventRecord(e1, st));
+    KPM_CUDA(cudaEventSynchronize(e1));
+    KPM_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= sweeps;
+    return KPM_OK;
+}
+
+int autotune_shapes(kpm_ctx *c, int R, int sweeps, cudaStream_t st, float *ms_per_sweep)
+{
+    KPM_TRY(ensure_vectors(c, R));
+    // a bounded recurrence to time on: random phases in V, W = (1/2) H' V
+    KPM_TRY(launch_phases(c, c->d_V, R, 0x5EED, st));
+    {
+        std::vector<ColumnBlock> blocks;
+        int64_t slot = 0;
+        KPM_TRY(plan_blocks(c, R, blocks, slot));
+        KPM_TRY(ensure_partial(c, slot));
+        for (const ColumnBlock &cb : blocks) {
+            SweepParams p = sweep_params(c, cb, R, c->d_V, c->d_W, c->d_partial + cb.partial_offset,
+                                         false);
+            KPM_TRY(launch_one(c, cb, p, true, st));
+        }
+    }
+    cudaEvent_t e0, e1;
+    KPM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KPM_ECUDA;
+    }
+    int rc = KPM_OK;
+    std::map<int, std::pair<float, LaunchShape>> best;  // per width
+    int best_cap = 64;
+    float best_total = 1e30f;
+    for (int cap = 64; cap >= 16 && rc == KPM_OK; cap >>= 1) {
+        if (cap > 64 || (cap < 64 && R < 2 * cap))
+            continue;
+        float total = 0.f;
+        int col0 = 0;
+        for (int RB : column_widths(R, cap)) {
+            if (!best.count(RB)) {
+                float bt = 1e30f;
+                LaunchShape bs = default_shape(c, RB);
+                for (const LaunchShape &s : shape_candidates(c, RB)) {
+                    float ms = 0.f;
+                    rc = time_block(c, R, col0, RB, s, sweeps, st, e0, e1, &ms);
+                    if (rc != KPM_OK)
+                        break;
+                    if (ms < bt)
+                        bt = ms, bs = s;
+                }
+                if (rc != KPM_OK)
+                    break;
+                best[RB] = {bt, bs};
+            }
+            total += best[RB].first;
+            col0 += RB;
+        }
+        if (rc == KPM_OK && total < best_total)
+            best_total = total, best_cap = cap;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != KPM_OK)
+        return rc;
+    c->max_rb = best_cap;
+    for (auto &kv : best)
+        c->shapes[kv.first] = kv.second.second;
+    c->tuned[R] = 1;
+    if (ms_per_sweep)
+        *ms_per_sweep = best_total;
+    return KPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kpm_autotune(kpm_ctx *c, int32_t R, int32_t sweeps, void *stream,
+                            kpm_launch *best)
+{
+    if (!c || R < 1 || sweeps < 1)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    KPM_TRY(autotune_shapes(c, R, sweeps, (cudaStream_t)stream));
+    if (best) {
+        const int RB = column_widths(R, c->max_rb).front();
+        const LaunchShape &s = c->shapes[RB];
+        best->lanes_per_row = s.T;
+        best->cols_per_lane = s.E;
+        best->block_threads = s.threads;
+        best->blocks_per_sm = s.blocks_per_sm;
+        best->tile_groups = s.tile_groups;
+    }
+    return KPM_OK;
+}
+
+int kpm_autotune_layout(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                   const double *val_ri, double a, double b,
+                                   const kpm_options *base, int32_t R, int32_t sweeps,
+                                   kpm_options *best, double *best_ms)
+{
+    if (!best || R < 1 || sweeps < 1)
+        return KPM_EINVAL;
+    kpm_options opt;
+    if (base)
+        opt = *base;
+    else
+        kpm_default_options(&opt);
+    KPM_TRY(validate_csr(n, row_ptr, col, val_ri));
+    // sigma only matters when row lengths differ
+    bool uniform = true;
+    for (int64_t i = 1; i < n && uniform; i++)
+        uniform = (row_ptr[i + 1] - row_ptr[i]) == (row_ptr[1] - row_ptr[0]);
+    const int Cs[] = {8, 32, 128};
+    const int sigmas_ragged[] = {1, 256, 4096};
+    double best_t = 1e300;
+    int rc = KPM_EUNSUPPORTED;
+    for (int C : Cs) {
+        for (int si = 0; si < (uniform ? 1 : 3); si++) {
+            kpm_options o = opt;
+            o.chunk_height = C;
+            o.sigma = uniform ? 1 : sigmas_ragged[si];
+            if (o.sigma > 1 && o.sigma < C)
+                continue;
+            o.autotune = 0;
+            kpm_ctx *t = nullptr;
+            int r = kpm_create(n, row_ptr, col, val_ri, a, b, &o, &t);
+            if (r != KPM_OK)
+                return r;
+            float ms = 0.f;
+            {
+                DeviceGuard guard(t->device);
+                r = autotune_shapes(t, R, sweeps, nullptr, &ms);
+            }
+            kpm_destroy(t);
+            if (r != KPM_OK)
+                return r;
+            rc = KPM_OK;
+            if (ms < best_t) {
+                best_t = ms;
+                *best = o;
+            }
+        }
+    }
+    best->autotune = 1;
+    if (best_ms)
+        *best_ms = best_t;
+    return rc;
+}
+
+int kpm_get_max_block_width(const kpm_ctx *c)
+{
+    return c ? c->max_rb : -1;
 }
 
 int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)
@@ -747,7 +960,7 @@ extern "C" int kpm_aug_spmmv_static(kpm_ctx *c, int32_t R, const void *V, void *
     double *scratch = nullptr;
     KPM_TRY(static_scratch_address(c->device, &scratch));
 
-    // Column blocks as in kpm_aug_spmmv (powers of two <= 64, widest first),
+    // Column blocks as in kpm_aug_spmmv (powers of two <= max_rb, widest first),
     // visited twice without any container: first to size the scratch, then
     // to launch.
     auto block_shape = [&](int RB, LaunchShape &s, int &grid) {
@@ -757,7 +970,7 @@ extern "C" int kpm_aug_spmmv_static(kpm_ctx *c, int32_t R, const void *V, void *
         return grid >= 1;
     };
     int64_t need = 0;
-    for (int rest = R, RB = 64; RB >= 1; RB >>= 1) {
+    for (int rest = R, RB = c->max_rb; RB >= 1; RB >>= 1) {
         for (; rest >= RB; rest -= RB) {
             LaunchShape s;
             int grid = 0;
@@ -771,7 +984,7 @@ extern "C" int kpm_aug_spmmv_static(kpm_ctx *c, int32_t R, const void *V, void *
 
     int64_t offset = 0;
     int col0 = 0;
-    for (int rest = R, RB = 64; RB >= 1; RB >>= 1) {
+    for (int rest = R, RB = c->max_rb; RB >= 1; RB >>= 1) {
         for (; rest >= RB; rest -= RB) {
             ColumnBlock cb;
             cb.col0 = col0;

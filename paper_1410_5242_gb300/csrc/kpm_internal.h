@@ -124,6 +124,9 @@ struct kpm_ctx {
     int64_t eta_doubles = 0;
 
     std::map<int, kpm::LaunchShape> shapes;  // per column-block width
+    int max_rb = 64;        // widest column block (a power of two <= 64)
+    int autotune = 0;       // tune the launch shape on first use of each R
+    std::map<int, int> tuned;  // R -> already tuned
     int64_t launches = 0;  // kernels launched by this context
 };
 

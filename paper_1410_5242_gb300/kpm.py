@@ -100,6 +100,10 @@ _SIGS = {
     "kpm_batch_eta": (_int, [_vp, _i32, _pd, _vp]),
     "kpm_batch_get_info": (_int, [_vp, ctypes.POINTER(BatchInfo)]),
     "kpm_batch_destroy": (None, [_vp]),
+    "kpm_autotune": (_int, [_vp, _i32, _i32, _vp, ctypes.POINTER(Launch)]),
+    "kpm_get_max_block_width": (_int, [_vp]),
+    "kpm_autotune_layout": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options), _i32,
+                                   _i32, ctypes.POINTER(Options), _pd]),
     "kpm_get_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
     "kpm_set_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
 }
@@ -238,7 +242,7 @@ class Context:
     """kpm_create / kpm_destroy around a Hermitian CSR matrix and (a, b)."""
 
     def __init__(self, csr, a, b, precision=PREC_FP64, chunk_height=32, sigma=256,
-                 check_hermitian=False, device=0, torch_allocator=True):
+                 check_hermitian=False, device=0, torch_allocator=True, autotune=False):
         n, rp, col, val = _csr(csr)
         opt = default_options()
         opt.precision = precision
@@ -246,6 +250,7 @@ class Context:
         opt.sigma = sigma
         opt.check_hermitian = 1 if check_hermitian else 0
         opt.device = device
+        opt.autotune = 1 if autotune else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(device)
@@ -291,6 +296,15 @@ class Context:
                    tile_groups=0):
         l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups)
         _check(lib.kpm_set_launch(self.handle, R, ctypes.byref(l)), "kpm_set_launch")
+
+    def autotune(self, R, sweeps=5, stream=None):
+        """kpm_autotune: returns the launch shape chosen for the widest block."""
+        l = Launch()
+        _check(lib.kpm_autotune(self.handle, R, sweeps, _stream_ptr(stream), ctypes.byref(l)),
+               "kpm_autotune")
+        out = {f: getattr(l, f) for f, _ in Launch._fields_}
+        out["max_block_width"] = lib.kpm_get_max_block_width(self.handle)
+        return out
 
     # -- host-buffer calls
     def moments(self, M, R, seed, imag=False, stream=None):
@@ -350,6 +364,21 @@ class Context:
             self.handle, M, R, seed, ctypes.c_void_p(eta_dev.data_ptr()),
             ctypes.c_void_p(eta_imag_dev.data_ptr()) if eta_imag_dev is not None else None,
             _stream_ptr(stream)), "kpm_moments_device")
+
+
+def autotune_layout(csr, a, b, R, precision=PREC_FP64, sweeps=5, device=0):
+    """kpm_autotune_layout: the fastest SELL (C, sigma) for width R, as
+    {"chunk_height", "sigma", "ms_per_sweep"}."""
+    n, rp, col, val = _csr(csr)
+    base = default_options()
+    base.precision = precision
+    base.device = device
+    best = Options()
+    ms = _d()
+    _check(lib.kpm_autotune_layout(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b,
+                                   ctypes.byref(base), R, sweeps, ctypes.byref(best),
+                                   ctypes.byref(ms)), "kpm_autotune_layout")
+    return {"chunk_height": best.chunk_height, "sigma": best.sigma, "ms_per_sweep": ms.value}
 
 
 def create(csr, a, b, **kw):
