@@ -289,6 +289,22 @@ def bench_ours(args, world, rank, local):
     if rank == 0 and not args.skip_accuracy:
         fp32_err = fp32_accuracy(kpm, h4, a4, b4, c4, ctx32, dev, args)
 
+    # ---------------- R sweep on the 64^3 lattice (code-balance drop, Eqs. 5-7)
+    r_sweep = []
+    if not args.skip_r_sweep:
+        for Rs in workloads.R_SWEEP:
+            t64 = kernel_only(ctx, Rs, max(3, args.kernel_launches // 10), stream)
+            t32s = kernel_only(ctx32, Rs, max(10, args.kernel_launches // 2), stream)
+            b64 = model.sweep_bytes(n, nnz, Rs, 16)
+            b32 = model.sweep_bytes(h4["n"], nnz4, Rs, 8)
+            r_sweep.append({
+                "R": Rs, "B_min_fp64_bytes_per_flop": round(model.code_balance(nnz / n, Rs), 3),
+                "fp64_ms": round(t64 * 1e3, 4), "fp64_GBs": round(b64 / t64 / 1e9, 1),
+                "fp64_TFLOPs": round(model.fused_fp64_flops(nnz, n, Rs) / t64 / 1e12, 4),
+                "fp32_ms": round(t32s * 1e3, 4), "fp32_GBs": round(b32 / t32s / 1e9, 1),
+                "fp32_frac_hbm": round(b32 / t32s / 1e9 / hbm_peak, 4),
+                "launch_fp64": ctx.get_launch(Rs), "launch_fp32": ctx32.get_launch(Rs)})
+
     # ---------------- the 64-problem ensemble in one graph launch
     ens = None
     if not args.skip_ensemble:
@@ -356,6 +372,7 @@ def bench_ours(args, world, rank, local):
                          "algorithmic_bytes": k32_bytes},
             "accuracy": fp32_err,
         },
+        "r_sweep": r_sweep,
         "ensemble": ens,
         "e2e": e2e,
         "gpu_launches": launches * world,
@@ -536,6 +553,7 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-oracle-accuracy", action="store_true")
     ap.add_argument("--skip-ensemble", action="store_true")
+    ap.add_argument("--skip-r-sweep", action="store_true")
     ap.add_argument("--ensemble-runs", type=int, default=1)
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")

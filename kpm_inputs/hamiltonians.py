@@ -67,12 +67,13 @@ def disorder_potential(nx, ny, nz, gamma, seed):
 
 
 def ti_hamiltonian(nx, ny, nz, gamma=0.0, seed=0, t=1.0, periodic=(True, True, True),
-                   potential=None):
+                   potential=None, chunk_sites=1 << 20):
     """Topological-insulator Hamiltonian of Eq. 1 as CSR.
 
     ``periodic`` gives the boundary condition per axis; a periodic axis needs
     at least 3 sites so that the +e_j and -e_j neighbours are distinct.
-    ``potential`` (float64[sites]) overrides the seeded disorder.
+    ``potential`` (float64[sites]) overrides the seeded disorder.  Sites are
+    processed in chunks of ``chunk_sites`` to bound temporary memory.
     """
     dims = (nx, ny, nz)
     for L, p in zip(dims, periodic):
@@ -83,60 +84,68 @@ def ti_hamiltonian(nx, ny, nz, gamma=0.0, seed=0, t=1.0, periodic=(True, True, T
     if potential is None:
         potential = disorder_potential(nx, ny, nz, gamma, seed)
     potential = np.asarray(potential, dtype=np.float64)
-    s = np.arange(sites, dtype=np.int64)
-    x = s % nx
-    y = (s // nx) % ny
-    z = s // (nx * ny)
-    coords = (x, y, z)
     g1 = dirac_matrices()[1]
     blocks = ti_blocks(t)
-
     max_per_row = 1 + sum(int(np.count_nonzero(np.abs(b[0]) > 0)) for b in blocks.values())
-    cols = np.full((sites, 4, max_per_row), -1, dtype=np.int64)
-    vals = np.zeros((sites, 4, max_per_row), dtype=np.complex128)
-    slot = np.zeros(4, dtype=np.int64)
-    # on-site diagonal (Gamma^1 is diagonal in this representation)
-    for a in range(4):
-        cols[:, a, 0] = 4 * s + a
-        vals[:, a, 0] = potential + 2.0 * g1[a, a].real
-        slot[a] = 1
-    for d, blk in blocks.items():
-        nb = []
-        valid = np.ones(sites, dtype=bool)
-        for axis in range(3):
-            c = coords[axis] + d[axis]
-            L = dims[axis]
-            if periodic[axis]:
-                c = c % L
-            else:
-                valid &= (c >= 0) & (c < L)
-                c = np.clip(c, 0, L - 1)
-            nb.append(c)
-        nsite = nb[0] + nx * (nb[1] + ny * nb[2])
+
+    counts = np.empty(n, dtype=np.int64)
+    col_parts, val_parts = [], []
+    for s0 in range(0, sites, chunk_sites):
+        s = np.arange(s0, min(sites, s0 + chunk_sites), dtype=np.int64)
+        ns = s.size
+        coords = (s % nx, (s // nx) % ny, s // (nx * ny))
+        cols = np.full((ns, 4, max_per_row), -1, dtype=np.int64)
+        vals = np.zeros((ns, 4, max_per_row), dtype=np.complex128)
+        slot = np.zeros(4, dtype=np.int64)
+        # on-site diagonal (Gamma^1 is diagonal in this representation)
         for a in range(4):
-            for b in range(4):
-                h = blk[a, b]
-                if h == 0:
-                    continue
-                k = slot[a]
-                cols[:, a, k] = np.where(valid, 4 * nsite + b, -1)
-                vals[:, a, k] = np.where(valid, h, 0.0)
-                slot[a] += 1
-    cols = cols.reshape(n, max_per_row)
-    vals = vals.reshape(n, max_per_row)
-    key = np.where(cols < 0, np.iinfo(np.int64).max, cols)
-    order = np.argsort(key, axis=1, kind="stable")
-    cols = np.take_along_axis(cols, order, axis=1)
-    vals = np.take_along_axis(vals, order, axis=1)
-    keep = cols >= 0
-    counts = keep.sum(axis=1)
+            cols[:, a, 0] = 4 * s + a
+            vals[:, a, 0] = potential[s] + 2.0 * g1[a, a].real
+            slot[a] = 1
+        for d, blk in blocks.items():
+            nb = []
+            valid = np.ones(ns, dtype=bool)
+            for axis in range(3):
+                c = coords[axis] + d[axis]
+                L = dims[axis]
+                if periodic[axis]:
+                    c = c % L
+                else:
+                    valid &= (c >= 0) & (c < L)
+                    c = np.clip(c, 0, L - 1)
+                nb.append(c)
+            nsite = nb[0] + nx * (nb[1] + ny * nb[2])
+            for a in range(4):
+                for b in range(4):
+                    h = blk[a, b]
+                    if h == 0:
+                        continue
+                    k = slot[a]
+                    cols[:, a, k] = np.where(valid, 4 * nsite + b, -1)
+                    vals[:, a, k] = np.where(valid, h, 0.0)
+                    slot[a] += 1
+        cols = cols.reshape(4 * ns, max_per_row)
+        vals = vals.reshape(4 * ns, max_per_row)
+        key = np.where(cols < 0, np.iinfo(np.int64).max, cols)
+        order = np.argsort(key, axis=1, kind="stable")
+        cols = np.take_along_axis(cols, order, axis=1)
+        vals = np.take_along_axis(vals, order, axis=1)
+        keep = cols >= 0
+        counts[4 * s0:4 * s0 + 4 * ns] = keep.sum(axis=1)
+        col_parts.append(cols[keep].astype(np.int32))
+        val_parts.append(vals[keep])
+        del cols, vals, key, order, keep
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
+    col = col_parts[0] if len(col_parts) == 1 else np.concatenate(col_parts)
+    del col_parts
+    val = val_parts[0] if len(val_parts) == 1 else np.concatenate(val_parts)
+    del val_parts
     return {
         "n": n,
         "row_ptr": row_ptr,
-        "col": cols[keep].astype(np.int32),
-        "val": vals[keep],
+        "col": col,
+        "val": val,
         "potential": potential,
         "dims": dims,
         "periodic": tuple(bool(p) for p in periodic),

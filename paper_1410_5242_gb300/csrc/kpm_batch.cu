@@ -3,9 +3,11 @@
 //
 // Every sweep step is one launch of batch_sweep_kernel over the tiles of
 // all problems still running at that step (problems sorted by M, so the
-// running set is always a prefix), followed by one launch of
-// batch_reduce_kernel that turns the per-tile eta partials of the step into
-// eta_{2m}, eta_{2m+1} of every running problem.  The whole schedule (start
+// running set is always a prefix; blocks stride over the concatenated tile
+// list and keep their eta terms in registers for as long as they stay in
+// one problem), followed by one launch of batch_reduce_kernel that turns
+// the per-block eta partials of the step into eta_{2m}, eta_{2m+1} of every
+// running problem.  The whole schedule (start
 // vectors, the initial sweep, the M/2 - 1 sweeps of the longest problem)
 // is captured once into a CUDA graph and replayed with one graph launch.
 #define KPM_SWEEP_MAX_THREADS 512
@@ -26,7 +28,9 @@ using namespace kpm;
 namespace {
 
 constexpr int kBatchThreads = 128;  // 4 warps per block
-constexpr int kBatchTileRows = 128;
+// block tile: one row group per warp (complex float), four (complex double),
+// as measured best for the single-problem sweep
+constexpr int kBatchTileGroups[2] = {4, 1};  // [precision]
 constexpr int kReduceThreads = 128;
 
 struct BatchProblem {
@@ -37,9 +41,27 @@ struct BatchProblem {
     void *buf0, *buf1;  // nu_0 lives in buf0; sweep s reads buf[s & 1], writes the other
     double *partial;    // [3 * RB][n_tiles]
     double *eta;        // [RB][M]
-    int64_t n_pad, n_tiles;
+    int64_t n_pad, n_tiles, tile_rows;
+    int64_t slots;  // min(grid, n_tiles): blocks that touch the problem in a step
     int32_t log2C, ld, RB, shape, tile_groups, M;
 };
+
+// L2 prefetch of a run's first tile (the later ones are prefetched one tile
+// ahead inside the run).
+template <typename Real>
+__device__ __forceinline__ void prefetch_first(const BatchProblem &bp, int64_t t0, int step)
+{
+    SweepParams p;
+    p.chunk_ptr = bp.chunk_ptr;
+    p.val = bp.val;
+    p.col = bp.col;
+    p.V = (step & 1) ? bp.buf1 : bp.buf0;
+    p.W = (step & 1) ? bp.buf0 : bp.buf1;
+    p.n_pad = bp.n_pad;
+    p.log2C = bp.log2C;
+    p.ld = bp.ld;
+    prefetch_tile<Real>(p, t0, bp.tile_rows, step != 0);
+}
 
 // Lane shape of a problem with block width RB = 2^shape: complex float
 // uses 4 columns (two 16-byte accesses) per lane, complex double one.
@@ -64,9 +86,12 @@ int batch_team(int shape)
     }
 }
 
+// One block's run of tiles within one problem: local tiles t0, t0 + G, ...
+// (G = gridDim.x), accumulated in registers and written once, as the
+// block's partial in slot t0 of the problem's [3*RB][slots] array.
 template <typename Real, int S>
-__device__ __forceinline__ void batch_tile(const BatchProblem &bp, int64_t tile, int step,
-                                           double *red)
+__device__ __forceinline__ void batch_run(const BatchProblem &bp, int64_t t0, int step,
+                                          double *red)
 {
     using Sh = BatchShape<Real, S>;
     constexpr int T = Sh::T, E = Sh::E, P = 32 / T;
@@ -92,12 +117,16 @@ __device__ __forceinline__ void batch_tile(const BatchProblem &bp, int64_t tile,
     Real *W = static_cast<Real *>(p.W);
     EtaAcc<Real, false> acc[E];
     const int64_t rows_per_tile = (int64_t)nwarps * P * bp.tile_groups;
-    for (int g = 0; g < bp.tile_groups; g++) {
-        const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
-        if (row < p.n_pad)
-            sweep_row<Real, T, E, false>(p, val, V, W, row, step == 0, cbase, acc);
+    for (int64_t tile = t0; tile < bp.n_tiles; tile += gridDim.x) {
+        if (threadIdx.x == 0)
+            prefetch_tile<Real>(p, tile + gridDim.x, rows_per_tile, step != 0);
+        for (int g = 0; g < bp.tile_groups; g++) {
+            const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
+            if (row < p.n_pad)
+                sweep_row<Real, T, E, false>(p, val, V, W, row, step == 0, cbase, acc);
+        }
     }
-    block_eta_sum<Real, T, E, false>(acc, red, bp.partial + tile, bp.n_tiles);
+    block_eta_sum<Real, T, E, false>(acc, red, bp.partial + t0, bp.slots);
 }
 
 template <typename Real>
@@ -107,7 +136,8 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
 {
     extern __shared__ double red_smem[];
     const int64_t total = tile_prefix[n_active];
-    for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
+    int64_t gt = blockIdx.x;
+    while (gt < total) {
         // the running problem owning global tile gt
         int lo = 0, hi = n_active - 1;
         while (lo < hi) {
@@ -118,22 +148,27 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
                 hi = mid - 1;
         }
         const BatchProblem bp = probs[lo];
-        const int64_t tile = gt - tile_prefix[lo];
+        const int64_t t0 = gt - tile_prefix[lo];  // < gridDim.x: first tile of this block's run
+        if (threadIdx.x == 0)
+            prefetch_first<Real>(bp, t0, step);
         switch (bp.shape) {
-        case 0: batch_tile<Real, 0>(bp, tile, step, red_smem); break;
-        case 1: batch_tile<Real, 1>(bp, tile, step, red_smem); break;
-        case 2: batch_tile<Real, 2>(bp, tile, step, red_smem); break;
-        case 3: batch_tile<Real, 3>(bp, tile, step, red_smem); break;
-        case 4: batch_tile<Real, 4>(bp, tile, step, red_smem); break;
-        case 5: batch_tile<Real, 5>(bp, tile, step, red_smem); break;
-        default: batch_tile<Real, 6>(bp, tile, step, red_smem); break;
+        case 0: batch_run<Real, 0>(bp, t0, step, red_smem); break;
+        case 1: batch_run<Real, 1>(bp, t0, step, red_smem); break;
+        case 2: batch_run<Real, 2>(bp, t0, step, red_smem); break;
+        case 3: batch_run<Real, 3>(bp, t0, step, red_smem); break;
+        case 4: batch_run<Real, 4>(bp, t0, step, red_smem); break;
+        case 5: batch_run<Real, 5>(bp, t0, step, red_smem); break;
+        default: batch_run<Real, 6>(bp, t0, step, red_smem); break;
         }
-        __syncthreads();  // red_smem is reused by the next tile
+        __syncthreads();  // red_smem is reused by the next run
+        // next tile of this block after the run
+        const int64_t run = (bp.n_tiles - t0 + gridDim.x - 1) / gridDim.x;
+        gt += run * (int64_t)gridDim.x;
     }
 }
 
 // One block per (running problem, quantity q in {<V|V>, Re<W|V>}, column r):
-// sums the problem's per-tile partials of this step in a fixed order.
+// sums the problem's per-block partials of this step in slot order.
 __global__ void batch_reduce_kernel(const BatchProblem *__restrict__ probs, int n_active, int step)
 {
     __shared__ double red[kReduceThreads];
@@ -145,10 +180,10 @@ __global__ void batch_reduce_kernel(const BatchProblem *__restrict__ probs, int 
     const int RB = probs[k].RB;
     if (r >= RB)
         return;
-    const int64_t n_tiles = probs[k].n_tiles;
-    const double *src = probs[k].partial + (int64_t)(q * RB + r) * n_tiles;
+    const int64_t slots = probs[k].slots;
+    const double *src = probs[k].partial + (int64_t)(q * RB + r) * slots;
     double s = 0.0;
-    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+    for (int64_t t = threadIdx.x; t < slots; t += blockDim.x)
         s += src[t];
     red[threadIdx.x] = s;
     __syncthreads();
@@ -254,6 +289,9 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     b->sorted_to_orig = order;
     const bool fp64 = b->precision == KPM_PREC_FP64;
     const int sd = fp64 ? 16 : 8;
+    b->grid = fp64 ? batch_grid<double>(ctx[0]->n_sm) : batch_grid<float>(ctx[0]->n_sm);
+    if (b->grid < 1)
+        return fail(KPM_ECUDA);
     std::vector<BatchProblem> probs(count);
     std::vector<int64_t> prefix(count + 1, 0);
     double bytes = 0.0;
@@ -268,10 +306,11 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             shape++;
         const int T = fp64 ? batch_team<double>(shape) : batch_team<float>(shape);
         const int rows_per_group = (kBatchThreads / 32) * (32 / T);
-        const int tg = std::max(1, kBatchTileRows / rows_per_group);
+        const int tg = kBatchTileGroups[fp64 ? 0 : 1];
         const int64_t tile_rows = (int64_t)rows_per_group * tg;
         const int64_t n_tiles = (c->n_pad + tile_rows - 1) / tile_rows;
-        rc = ensure_partial(c, 3 * (int64_t)R[p] * n_tiles);
+        const int64_t slots = std::min<int64_t>(b->grid, n_tiles);
+        rc = ensure_partial(c, 3 * (int64_t)R[p] * slots);
         if (rc)
             return fail(rc);
         rc = ensure_eta(c, (int64_t)M[p] * R[p]);
@@ -288,6 +327,8 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         bp.eta = c->d_eta;
         bp.n_pad = c->n_pad;
         bp.n_tiles = n_tiles;
+        bp.tile_rows = tile_rows;
+        bp.slots = slots;
         bp.log2C = c->log2C;
         bp.ld = (int32_t)block_ld(c, R[p]);
         bp.RB = R[p];
@@ -307,9 +348,6 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             k++;
         b->n_active[s] = k;
     }
-    b->grid = fp64 ? batch_grid<double>(ctx[0]->n_sm) : batch_grid<float>(ctx[0]->n_sm);
-    if (b->grid < 1)
-        return fail(KPM_ECUDA);
 
     b->d_probs = (BatchProblem *)dev_alloc(ctx[0], sizeof(BatchProblem) * count);
     b->d_prefix = (int64_t *)dev_alloc(ctx[0], sizeof(int64_t) * (count + 1));

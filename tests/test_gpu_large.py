@@ -1,0 +1,48 @@
+"""Parity at the large lattice: 240 x 240 x 120 sites (N = 27,648,000 rows,
+359,424,000 non-zeros, complex double; 7.2 GB matrix and 28 GB of vector
+blocks at R = 32).  The oracle computes sampled outputs one by one: the
+first 8 moments of vectors 0 and 31; the full M = 1024 run is checked
+against the short run (same kernels, so its first moments must be
+identical) and against invariants that hold at any size."""
+import numpy as np
+import pytest
+
+from kpm_inputs import hamiltonians as ham
+from kpm_inputs import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm as k
+    return k
+
+
+def test_large_lattice_fp64(kpm, orc):
+    cfg = workloads.TI_LARGE
+    h = ham.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+    n, R, M, seed = h["n"], cfg["R"], cfg["M"], cfg["seed"]
+    assert n == 27_648_000 and len(h["col"]) == 13 * n
+    a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    with kpm.create(h, a, b) as ctx:
+        short = ctx.moments(8, R, seed)
+        full = ctx.moments(M, R, seed)
+    ref, _ = orc.moments(h, a, b, 8, seed, [0, R - 1])
+    got = short[[0, R - 1]]
+    assert np.all(np.abs(got - ref) <= 1e-10 * ref[:, :1])
+    assert np.array_equal(full[:, :8], short)
+    # invariants of the whole run: unit-modulus start vectors, norms, bounds
+    np.testing.assert_allclose(full[:, 0], n, rtol=1e-13)
+    assert np.all(full[:, 0::2] >= 0)
+    c = 2 * full - full[:, [0, 1] * (M // 2)]
+    c[:, :2] = full[:, :2]
+    assert np.max(np.abs(c)) <= n * (1 + 1e-10)
+    mu = kpm.eta_to_mu(full)
+    assert mu[0] == pytest.approx(1.0, abs=1e-15)
+    _, rho = kpm.dos(mu, 4096, a, b)
+    assert rho.min() > -1e-6 * rho.max()
