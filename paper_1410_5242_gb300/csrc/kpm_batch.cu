@@ -12,7 +12,7 @@
 // is captured once into a CUDA graph and replayed with one graph launch.
 #define KPM_SWEEP_MAX_THREADS 512
 #define KPM_SWEEP_MIN_BLOCKS 2
-#define KPM_SWEEP_INDEX_RUN 4
+#define KPM_SWEEP_INDEX_RUN 2
 #define KPM_SWEEP_PREFETCH 1
 #include "aug_spmmv.cuh"
 
