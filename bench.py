@@ -305,6 +305,11 @@ def bench_ours(args, world, rank, local):
                 "fp32_frac_hbm": round(b32 / t32s / 1e9 / hbm_peak, 4),
                 "launch_fp64": ctx.get_launch(Rs), "launch_fp32": ctx32.get_launch(Rs)})
 
+    # ---------------- optimisation stages of the paper on this GPU
+    ablation = None
+    if not args.skip_ablation:
+        ablation = ablation_stages(kpm, h, a, b, ctx, ctx32, n, nnz, h4["n"], nnz4, stream)
+
     # ---------------- the 64-problem ensemble in one graph launch
     ens = None
     if not args.skip_ensemble:
@@ -373,6 +378,7 @@ def bench_ours(args, world, rank, local):
             "accuracy": fp32_err,
         },
         "r_sweep": r_sweep,
+        "ablation": ablation,
         "ensemble": ens,
         "e2e": e2e,
         "gpu_launches": launches * world,
@@ -383,6 +389,52 @@ def bench_ours(args, world, rank, local):
     ctx32.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def ablation_stages(kpm, h, a, b, ctx, ctx32, n, nnz, n4, nnz4, stream):
+    """The paper's optimisation stages (Figs. 3-5, Table III, Fig. 10) on the
+    64^3 lattice, R = 32, M = 400, timed with CUDA events: the naive
+    library-call algorithm, fused aug_spmv in throughput mode (R runs of one
+    vector), blocked aug_spmmv with a reduction after every sweep and with
+    batched reductions, and the sweep kernel without dots / plain SpMMV."""
+    import torch
+    M, R, seed = 400, 32, 9
+    eta = torch.empty((R, M), dtype=torch.float64, device="cuda")
+    eta1 = torch.empty((1, M), dtype=torch.float64, device="cuda")
+    out = {"M": M, "R": R, "unit": "ms per KPM-DOS run"}
+
+    def timed(fn):
+        fn()
+        return time_steps(fn, 1, stream) * 1e3
+
+    with kpm.Naive(h, a, b) as nv:
+        out["fp64_naive_library_calls"] = round(timed(lambda: nv.moments_device(M, R, seed, eta,
+                                                                                 stream=stream)), 2)
+    for name, c in (("fp64", ctx), ("fp32", ctx32)):
+        t1 = timed(lambda: c.moments_device(M, 1, seed, eta1, stream=stream))
+        out[name + "_aug_spmv_throughput_mode"] = round(R * t1, 2)
+        c.set_reduce_interval(1)
+        out[name + "_aug_spmmv_reduce_every_sweep"] = round(
+            timed(lambda: c.moments_device(M, R, seed, eta, stream=stream)), 2)
+        c.set_reduce_interval(0)
+        out[name + "_aug_spmmv"] = round(timed(lambda: c.moments_device(M, R, seed, eta,
+                                                                         stream=stream)), 2)
+        V, W = c.new_block(R), c.new_block(R)
+        c.aug_spmmv(R, V, W, None, init=True, with_imag=False, stream=stream)
+        for variant, label in ((2, "plain_spmmv"), (1, "aug_spmmv_no_dots"), (0, "aug_spmmv")):
+            def sweeps():
+                for _ in range(10):
+                    c.sweep_variant(R, V, W, variant, stream=stream)
+            out["%s_sweep_ms_%s" % (name, label)] = round(timed(sweeps) / 10, 4)
+    naive = out["fp64_naive_library_calls"]
+    out["fp64_speedup_vs_naive"] = {k: round(naive / out[k], 2) for k in (
+        "fp64_aug_spmv_throughput_mode", "fp64_aug_spmmv_reduce_every_sweep", "fp64_aug_spmmv",
+        "fp32_aug_spmmv")}
+    sd_bytes = {"naive": model.kpm_traffic(M, n, nnz, R, 16, "naive"),
+                "aug_spmv": model.kpm_traffic(M, n, nnz, R, 16, "aug_spmv"),
+                "aug_spmmv": model.kpm_traffic(M, n, nnz, R, 16, "aug_spmmv")}
+    out["fp64_eq4_bytes"] = sd_bytes
+    return out
 
 
 def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
@@ -554,6 +606,7 @@ def main():
     ap.add_argument("--skip-oracle-accuracy", action="store_true")
     ap.add_argument("--skip-ensemble", action="store_true")
     ap.add_argument("--skip-r-sweep", action="store_true")
+    ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--ensemble-runs", type=int, default=1)
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")

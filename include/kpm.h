@@ -294,6 +294,38 @@ int kpm_aug_spmmv_static(kpm_ctx *ctx, int32_t R, const void *V, void *W, double
 int kpm_moments_device(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
                        double *eta_imag_dev, void *stream);
 
+/* ------------------------------------------------------- ablation calls
+ * The optimisation stages of the paper on this GPU (Secs. "Algorithm
+ * Analysis and Optimization" and "GPU Performance Model"). */
+
+/* One sweep of a reduced kernel (Fig. 10's three kernels), on device blocks
+ * as in kpm_aug_spmmv:
+ *   variant 0: fully augmented sweep (kpm_aug_spmmv with eta_dev = NULL),
+ *   variant 1: augmented SpMMV without the scalar products, W <- H'V - W,
+ *   variant 2: plain SpMMV, W <- (1/2) H'V (W not read).
+ * KPM_EINVAL for another variant. */
+int kpm_sweep_variant(kpm_ctx *ctx, int32_t R, const void *V, void *W, int32_t variant,
+                      void *stream);
+
+/* Sweeps whose per-block eta partials one reduction launch sums in the
+ * moment calls: 0 (default) = as many as fit 64 MB; 1 = a reduction after
+ * every sweep, the single-GPU form of the paper's aug_spmmv* (a global
+ * reduction in every iteration, Table III). */
+int kpm_set_reduce_interval(kpm_ctx *ctx, int32_t sweeps);
+
+/* The naive KPM-DOS of Fig. 3 from library calls: for each start vector in
+ * turn, per step one cuSPARSE CSR SpMV (u = H v) and the cuBLAS level-1 calls
+ * axpy (u -= b v), scal (w = -w), axpy (w += 2a u), nrm2 (eta_2m) and dotc
+ * (eta_2m+1), in complex double on the original CSR matrix.  A baseline for
+ * the ablation, not the production path. */
+typedef struct kpm_naive kpm_naive;
+int kpm_naive_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
+                     double a, double b, int32_t device, kpm_naive **out);
+/* eta_dev: device double[R][M]; random-phase start vectors as kpm_moments. */
+int kpm_naive_moments(kpm_naive *nv, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
+                      void *stream);
+void kpm_naive_destroy(kpm_naive *nv);
+
 /* Launch variant the context uses for block width R: lanes per row (T),
  * complex columns per lane (E, T*E = R), threads per block, blocks per SM
  * (0 = occupancy maximum) and row groups per warp in one block tile (a

@@ -18,7 +18,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libkpm.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["kpm_host.cpp", "kpm_ctx.cu", "kpm_batch.cu", "aug_spmmv_fp64.cu", "aug_spmmv_fp32.cu"]
+SOURCES = ["kpm_host.cpp", "kpm_ctx.cu", "kpm_batch.cu", "kpm_naive.cu", "aug_spmmv_fp64.cu",
+           "aug_spmmv_fp32.cu"]
 HEADERS = ["kpm_internal.h", "aug_spmmv.cuh", os.path.join(INCLUDE, "kpm.h")]
 
 
@@ -65,7 +66,9 @@ def build(force=False, verbose=False, extra_nvcc=()):
             if err:
                 sys.stderr.write(err)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [_nvcc(), ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "lib64")
+    cmd = [_nvcc(), ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results] + \
+        ["-L" + cuda_lib, "-lcusparse", "-lcublas", "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("linking libkpm.so failed:\n%s" % r.stderr)

@@ -277,8 +277,10 @@ struct EtaAcc<float, IMAG> {
 // ------------------------------------------------------------------ one row
 // W row <- H' V - W (or (1/2) H' V when init) for this lane's E owned
 // columns (pieces from column cbase on, see owned_column), and this row's
-// terms of the scalar products.
-template <typename Real, int T, int E, bool IMAG>
+// terms of the scalar products (DOTS = false leaves them out: the ablation
+// variants of the paper's GPU model, augmented SpMMV without dot products
+// and plain SpMMV).
+template <typename Real, int T, int E, bool IMAG, bool DOTS = true>
 __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__restrict__ val,
                                           const Real *__restrict__ V, Real *W, int64_t row,
                                           int init, int64_t cbase, EtaAcc<Real, IMAG> (&acc)[E])
@@ -353,12 +355,14 @@ __device__ __forceinline__ void sweep_row(const SweepParams &p, const Real *__re
             s[k] *= Real(0.5);
     }
     store_owned<Real, T, E>(W, wbase, s);
-    // the row's own V entries (recently touched by the diagonal gather)
-    Real vs[2 * E];
-    load_owned_nc<Real, T, E>(V, wbase, vs);
+    if constexpr (DOTS) {
+        // the row's own V entries (recently touched by the diagonal gather)
+        Real vs[2 * E];
+        load_owned_nc<Real, T, E>(V, wbase, vs);
 #pragma unroll
-    for (int k = 0; k < E; k++)
-        acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
+        for (int k = 0; k < E; k++)
+            acc[k].add(s[2 * k], s[2 * k + 1], vs[2 * k], vs[2 * k + 1]);
+    }
 }
 
 // Block-wide sum of every lane's eta terms per column in a fixed order:
@@ -442,6 +446,43 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
     }
 
     block_eta_sum<Real, T, E, IMAG>(acc, red_smem, p.partial + (int64_t)blockIdx.x * 3 * RB, 1);
+}
+
+// The sweep without the scalar products (ablation variants): the same
+// loop and prefetching as aug_spmmv_kernel, no eta accumulation or
+// reduction.  init = 1 gives plain SpMMV (W <- (1/2) H' V, W not read),
+// init = 0 the augmented SpMMV without dots (W <- H' V - W).
+template <typename Real, int T, int E>
+__global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
+    spmmv_nodot_kernel(const SweepParams p, const int init)
+{
+    constexpr int P = 32 / T;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int tl = lane % T;
+    const int team = lane / T;
+    const int64_t cbase = (int64_t)p.col0 + tl * Pieces<Real, E>::EV;
+    const Real *__restrict__ val = static_cast<const Real *>(p.val);
+    const Real *__restrict__ V = static_cast<const Real *>(p.V);
+    Real *W = static_cast<Real *>(p.W);
+    EtaAcc<Real, false> acc[E];
+    const int64_t rows_per_tile = (int64_t)nwarps * P * p.tile_groups;
+    const int64_t n_tiles = (p.n_pad + rows_per_tile - 1) / rows_per_tile;
+    constexpr int D = KPM_SWEEP_PREFETCH;
+    if (D > 0 && threadIdx.x == 0)
+        for (int k = 0; k < D; k++)
+            prefetch_tile<Real>(p, blockIdx.x + (int64_t)k * gridDim.x, rows_per_tile, !init);
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (D > 0 && threadIdx.x == 0)
+            prefetch_tile<Real>(p, tile + (int64_t)D * gridDim.x, rows_per_tile, !init);
+        for (int g = 0; g < p.tile_groups; g++) {
+            const int64_t row = tile * rows_per_tile + ((int64_t)g * nwarps + warp) * P + team;
+            if (row >= p.n_pad)
+                continue;
+            sweep_row<Real, T, E, false, false>(p, val, V, W, row, init, cbase, acc);
+        }
+    }
 }
 
 // Instantiated (T, E) shapes; X(T, E) is expanded for each.

@@ -40,6 +40,21 @@ int launch_sweep_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool
     return KPM_EUNSUPPORTED;
 }
 
+int launch_nodot_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool init, void *stream)
+{
+    if (s.threads < 32 || s.threads > KPM_SWEEP_MAX_THREADS || (s.threads % 32) || grid < 1)
+        return KPM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+#define KPM_CASE(T_, E_)                                                                       \
+    if (s.T == T_ && s.E == E_) {                                                              \
+        spmmv_nodot_kernel<float, T_, E_><<<grid, s.threads, 0, st>>>(p, init ? 1 : 0);           \
+        return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;                         \
+    }
+    KPM_SHAPES_FP32(KPM_CASE)
+#undef KPM_CASE
+    return KPM_EUNSUPPORTED;
+}
+
 int sweep_max_blocks_per_sm_fp32(const LaunchShape &s)
 {
     int nb = 0;

@@ -42,7 +42,7 @@ __global__ void phases_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n
         const int r = (int)(idx - p * ld);
         Real re = 0, im = 0;
         if (p < n && r < R) {
-            const uint64_t i = (uint64_t)perm[p];
+            const uint64_t i = perm ? (uint64_t)perm[p] : (uint64_t)p;
             const uint64_t x = splitmix_mix(key + ((uint64_t)r * (uint64_t)n + i + 1) * kGolden);
             const double u = (double)(x >> 11) * 0x1.0p-53;
             if constexpr (sizeof(Real) == 8) {
@@ -281,6 +281,18 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
 
 }  // namespace
 
+int kpm::launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, int64_t n_pad,
+                           int R, int ld, uint64_t seed, int n_sm, cudaStream_t st)
+{
+    const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
+    const int grid = n_sm * 8;
+    if (fp64)
+        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, perm, n, n_pad, R, ld, key);
+    else
+        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, perm, n, n_pad, R, ld, key);
+    return cuda_status(cudaGetLastError());
+}
+
 int kpm::launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st)
 {
     const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
@@ -309,6 +321,8 @@ int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStre
     const int sweeps = M / 2;
     // as many sweeps of partials as fit in ~64 MB (at least one)
     int slots = (int)std::max<int64_t>(1, std::min<int64_t>(sweeps, (64LL << 20) / 8 / slot_doubles));
+    if (c->reduce_interval > 0)
+        slots = std::min(slots, c->reduce_interval);
     KPM_TRY(ensure_partial(c, slots * slot_doubles));
     const bool imag = eta_im != nullptr;
     void *V = c->d_V, *W = c->d_W;
@@ -602,6 +616,36 @@ int kpm_aug_spmmv(kpm_ctx *c, int32_t R, const void *V, void *W, double *eta_dev
             c->d_partial + cb.partial_offset, cb.grid, cb.RB, cb.col0, R, eta_dev);
         KPM_CUDA(cudaGetLastError());
     }
+    return KPM_OK;
+}
+
+int kpm_sweep_variant(kpm_ctx *c, int32_t R, const void *V, void *W, int32_t variant,
+                      void *stream)
+{
+    if (!c || R < 1 || !V || !W || V == W || variant < 0 || variant > 2)
+        return KPM_EINVAL;
+    if (variant == 0)
+        return kpm_aug_spmmv(c, R, V, W, nullptr, 0, 0, stream);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ColumnBlock> blocks;
+    int64_t slot_doubles = 0;
+    KPM_TRY(plan_blocks(c, R, blocks, slot_doubles));
+    for (const ColumnBlock &cb : blocks) {
+        SweepParams p = sweep_params(c, cb, R, V, W, nullptr, false);
+        c->launches++;
+        KPM_TRY(c->precision == KPM_PREC_FP64
+                    ? launch_nodot_fp64(p, cb.shape, cb.grid, variant == 2, st)
+                    : launch_nodot_fp32(p, cb.shape, cb.grid, variant == 2, st));
+    }
+    return KPM_OK;
+}
+
+int kpm_set_reduce_interval(kpm_ctx *c, int32_t sweeps)
+{
+    if (!c || sweeps < 0)
+        return KPM_EINVAL;
+    c->reduce_interval = sweeps;
     return KPM_OK;
 }
 

@@ -46,6 +46,9 @@ int launch_sweep_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool
                       void *stream);
 int launch_sweep_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool init,
                       void *stream);
+// The same sweep without scalar products (ablation variants).
+int launch_nodot_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool init, void *stream);
+int launch_nodot_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool init, void *stream);
 // Occupancy query for the same kernels (blocks per SM, 0 if unsupported).
 int sweep_max_blocks_per_sm(int precision, const LaunchShape &s, bool init);
 
@@ -126,6 +129,7 @@ struct kpm_ctx {
     std::map<int, kpm::LaunchShape> shapes;  // per column-block width
     int max_rb = 64;        // widest column block (a power of two <= 64)
     int autotune = 0;       // tune the launch shape on first use of each R
+    int reduce_interval = 0;  // sweeps per eta reduction launch (0 = as many as fit 64 MB)
     std::map<int, int> tuned;  // R -> already tuned
     int64_t launches = 0;  // kernels launched by this context
 };
@@ -139,5 +143,8 @@ int ensure_vectors(kpm_ctx *c, int R);
 int ensure_partial(kpm_ctx *c, int64_t doubles);
 int ensure_eta(kpm_ctx *c, int64_t doubles);
 int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st);
+// Random-phase block without a context: perm may be NULL (identity).
+int launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, int64_t n_pad, int R,
+                      int ld, uint64_t seed, int n_sm, cudaStream_t st);
 LaunchShape default_shape(const kpm_ctx *c, int RB);
 }  // namespace kpm

@@ -104,6 +104,11 @@ _SIGS = {
     "kpm_get_max_block_width": (_int, [_vp]),
     "kpm_autotune_layout": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options), _i32,
                                    _i32, ctypes.POINTER(Options), _pd]),
+    "kpm_sweep_variant": (_int, [_vp, _i32, _vp, _vp, _i32, _vp]),
+    "kpm_set_reduce_interval": (_int, [_vp, _i32]),
+    "kpm_naive_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, ctypes.POINTER(_vp)]),
+    "kpm_naive_moments": (_int, [_vp, _i32, _i32, _u64, _vp, _vp]),
+    "kpm_naive_destroy": (None, [_vp]),
     "kpm_get_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
     "kpm_set_launch": (_int, [_vp, _i32, ctypes.POINTER(Launch)]),
 }
@@ -359,6 +364,15 @@ class Context:
                                         1 if with_imag else 0, _stream_ptr(stream)),
                "kpm_aug_spmmv_static")
 
+    def sweep_variant(self, R, V, W, variant, stream=None):
+        """kpm_sweep_variant: 0 fully augmented, 1 without dots, 2 plain SpMMV."""
+        _check(lib.kpm_sweep_variant(self.handle, R, ctypes.c_void_p(V.data_ptr()),
+                                     ctypes.c_void_p(W.data_ptr()), variant, _stream_ptr(stream)),
+               "kpm_sweep_variant")
+
+    def set_reduce_interval(self, sweeps):
+        _check(lib.kpm_set_reduce_interval(self.handle, sweeps), "kpm_set_reduce_interval")
+
     def moments_device(self, M, R, seed, eta_dev, eta_imag_dev=None, stream=None):
         _check(lib.kpm_moments_device(
             self.handle, M, R, seed, ctypes.c_void_p(eta_dev.data_ptr()),
@@ -379,6 +393,43 @@ def autotune_layout(csr, a, b, R, precision=PREC_FP64, sweeps=5, device=0):
                                    ctypes.byref(base), R, sweeps, ctypes.byref(best),
                                    ctypes.byref(ms)), "kpm_autotune_layout")
     return {"chunk_height": best.chunk_height, "sigma": best.sigma, "ms_per_sweep": ms.value}
+
+
+class Naive:
+    """kpm_naive_create / kpm_naive_moments / kpm_naive_destroy: the library-call
+    KPM-DOS of Fig. 3 (ablation baseline)."""
+
+    def __init__(self, csr, a, b, device=0):
+        n, rp, col, val = _csr(csr)
+        h = ctypes.c_void_p()
+        _check(lib.kpm_naive_create(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, device,
+                                    ctypes.byref(h)), "kpm_naive_create")
+        self.handle = h
+
+    def moments_device(self, M, R, seed, eta_dev, stream=None):
+        _check(lib.kpm_naive_moments(self.handle, M, R, seed, ctypes.c_void_p(eta_dev.data_ptr()),
+                                     _stream_ptr(stream)), "kpm_naive_moments")
+
+    def moments(self, M, R, seed):
+        torch = _torch()
+        eta = torch.empty((R, M), dtype=torch.float64, device="cuda")
+        self.moments_device(M, R, seed, eta)
+        torch.cuda.synchronize()
+        return eta.cpu().numpy()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.kpm_naive_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def create(csr, a, b, **kw):
