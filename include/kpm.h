@@ -75,6 +75,10 @@ typedef struct kpm_options {
     kpm_alloc_fn alloc_fn;    /* NULL = cudaMalloc */
     kpm_free_fn free_fn;      /* NULL = cudaFree */
     void *alloc_user;
+    const int32_t *row_order; /* NULL, or int32[n]: a permutation of the rows (new position ->
+                                 original row) applied before the sigma sort, e.g. to place
+                                 rows that share neighbours together for cache reuse; moments
+                                 do not depend on it beyond rounding.  Read during kpm_create. */
 } kpm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -145,12 +149,15 @@ typedef struct kpm_sell {
 } kpm_sell;
 
 /* Builds the SELL-C-sigma form of H' = 2a(H - b 1) from CSR (host only).
- * Rows are sorted by descending length inside windows of sigma rows
- * (stable), grouped into chunks of C rows, and the permutation is applied
+ * Rows are taken in the order row_order (NULL = 0..n-1; otherwise a
+ * permutation of 0..n-1, new position -> original row, else KPM_EINVAL),
+ * sorted by descending length inside windows of sigma rows (stable),
+ * grouped into chunks of C rows, and the permutation is applied
  * symmetrically (rows and columns).  C in [1, 1024], sigma >= 1.
  * Free with kpm_sell_release.  KPM_EINVAL on a malformed CSR. */
 int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
-                   double a, double b, int32_t C, int32_t sigma, kpm_sell *out);
+                   double a, double b, int32_t C, int32_t sigma, const int32_t *row_order,
+                   kpm_sell *out);
 void kpm_sell_release(kpm_sell *s);
 
 /* ============================================================ GPU calls */

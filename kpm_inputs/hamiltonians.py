@@ -152,6 +152,23 @@ def ti_hamiltonian(nx, ny, nz, gamma=0.0, seed=0, t=1.0, periodic=(True, True, T
     }
 
 
+def cube_row_order(dims, block=(4, 4, 4)):
+    """A row ordering (new position -> row) that lists the lattice sites
+    block by block (bx x by x bz sites, blocks in x, then y, then z order;
+    sites inside a block x-fastest) with the four orbitals of a site kept
+    together, so that rows sharing neighbours sit next to each other."""
+    nx, ny, nz = dims
+    bx, by, bz = block
+    s = np.arange(nx * ny * nz, dtype=np.int64)
+    x, y, z = s % nx, (s // nx) % ny, s // (nx * ny)
+    bxn, byn = -(-nx // bx), -(-ny // by)
+    blk = (x // bx) + bxn * ((y // by) + byn * (z // bz))
+    inner = (x % bx) + bx * ((y % by) + by * (z % bz))
+    sites = np.lexsort((inner, blk))
+    rows = (4 * sites[:, None] + np.arange(4)[None, :]).ravel()
+    return rows.astype(np.int32)
+
+
 def diagonal_matrix(diag):
     """CSR of a diagonal matrix with the given real diagonal."""
     diag = np.asarray(diag, dtype=np.float64)

@@ -1,20 +1,24 @@
 // Instantiations and launcher of the aug_spmmv sweep for complex float
 // storage (one translation unit per precision so they compile in parallel).
 // The float form is bound by memory-level parallelism: 64 registers per
-// thread (8 blocks of 4 warps per SM), pipelined index runs of 2 entries
-// and an L2 bulk prefetch one tile ahead measured best (0.35 ms per sweep
-// at 64^3, R = 32).
+// thread (launched as 8 blocks of 4 warps per SM; blocks of up to 1024
+// threads are allowed for the autotuner), pipelined index runs of 2
+// entries and an L2 bulk prefetch one tile ahead measured best (0.32 ms
+// per sweep at 64^3, R = 32).
 #ifndef KPM_SWEEP_MAX_THREADS
-#define KPM_SWEEP_MAX_THREADS 512
+#define KPM_SWEEP_MAX_THREADS 1024
 #endif
 #ifndef KPM_SWEEP_MIN_BLOCKS
-#define KPM_SWEEP_MIN_BLOCKS 2
+#define KPM_SWEEP_MIN_BLOCKS 1
 #endif
 #ifndef KPM_SWEEP_INDEX_RUN
 #define KPM_SWEEP_INDEX_RUN 2
 #endif
 #ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1
+#endif
+#ifndef KPM_SWEEP_MAX_L1
+#define KPM_SWEEP_MAX_L1 0
 #endif
 #include "aug_spmmv.cuh"
 
@@ -29,6 +33,15 @@ int launch_sweep_fp32(const SweepParams &p, const LaunchShape &s, int grid, bool
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
     if (s.T == T_ && s.E == E_) {                                                              \
+        if (KPM_SWEEP_MAX_L1) {                                                                \
+            static bool carved = false;                                                        \
+            if (!carved) {                                                                     \
+                cudaFuncSetAttribute(aug_spmmv_kernel<float, T_, E_, false>,                       \
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,           \
+                                     cudaSharedmemCarveoutMaxL1);                              \
+                carved = true;                                                                 \
+            }                                                                                  \
+        }                                                                                      \
         if (p.with_imag)                                                                       \
             aug_spmmv_kernel<float, T_, E_, true><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0);  \
         else                                                                                   \

@@ -17,6 +17,9 @@
 #ifndef KPM_SWEEP_PREFETCH
 #define KPM_SWEEP_PREFETCH 1
 #endif
+#ifndef KPM_SWEEP_MAX_L1
+#define KPM_SWEEP_MAX_L1 0
+#endif
 #include "aug_spmmv.cuh"
 
 namespace kpm {
@@ -30,6 +33,15 @@ int launch_sweep_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
     if (s.T == T_ && s.E == E_) {                                                              \
+        if (KPM_SWEEP_MAX_L1) {                                                                \
+            static bool carved = false;                                                        \
+            if (!carved) {                                                                     \
+                cudaFuncSetAttribute(aug_spmmv_kernel<double, T_, E_, false>,                       \
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,           \
+                                     cudaSharedmemCarveoutMaxL1);                              \
+                carved = true;                                                                 \
+            }                                                                                  \
+        }                                                                                      \
         if (p.with_imag)                                                                       \
             aug_spmmv_kernel<double, T_, E_, true><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0);  \
         else                                                                                   \

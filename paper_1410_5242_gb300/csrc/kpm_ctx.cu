@@ -161,7 +161,7 @@ std::vector<int> column_widths(int R, int cap)
 LaunchShape default_shape(const kpm_ctx *c, int RB)
 {
     LaunchShape s;
-    s.threads = 128;
+    s.threads = c->precision == KPM_PREC_FP64 ? 256 : 128;
     if (c->precision == KPM_PREC_FP64) {
         s.E = RB >= 64 ? 2 : 1;
         s.T = RB / s.E;
@@ -170,7 +170,7 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
         s.T = RB / s.E;
     }
     s.blocks_per_sm = 0;  // 0 = occupancy maximum
-    s.tile_groups = c->precision == KPM_PREC_FP64 ? 4 : 1;
+    s.tile_groups = c->precision == KPM_PREC_FP64 ? 8 : 1;
     return s;
 }
 
@@ -430,7 +430,8 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         return ndev == 0 ? KPM_ECUDA : KPM_EINVAL;
     }
     kpm_sell sell;
-    rc = kpm_sell_build(n, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma, &sell);
+    rc = kpm_sell_build(n, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma, opt.row_order,
+                        &sell);
     if (rc)
         return rc;
 

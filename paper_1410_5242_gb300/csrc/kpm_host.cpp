@@ -191,7 +191,8 @@ int kpm_dos(const double *mu, int32_t M, int32_t K, double a, double b, double *
 }
 
 int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
-                   double a, double b, int32_t C, int32_t sigma, kpm_sell *out)
+                   double a, double b, int32_t C, int32_t sigma, const int32_t *row_order,
+                   kpm_sell *out)
 {
     if (!out)
         return KPM_EINVAL;
@@ -218,6 +219,17 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
     // sigma-window sort by descending row length (stable)
     std::vector<int32_t> perm(n_pad);
     std::iota(perm.begin(), perm.end(), 0);
+    if (row_order) {
+        // caller's ordering first (must be a permutation of 0..n-1)
+        std::vector<uint8_t> seen(n, 0);
+        for (int64_t p = 0; p < n; p++) {
+            const int32_t i = row_order[p];
+            if (i < 0 || i >= n || seen[i])
+                return KPM_EINVAL;
+            seen[i] = 1;
+            perm[p] = i;
+        }
+    }
     if (sigma > 1) {
         for (int64_t w = 0; w < n; w += sigma) {
             const int64_t e = std::min<int64_t>(n, w + sigma);

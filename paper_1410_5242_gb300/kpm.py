@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("chunk_height", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("check_hermitian", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+                ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p),
+                ("row_order", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Sell(ctypes.Structure):
@@ -78,7 +79,8 @@ _SIGS = {
     "kpm_scale_from_bounds": (_int, [_d, _d, _d, _pd, _pd]),
     "kpm_eta_to_mu": (_int, [_pd, _i32, _i32, _pd]),
     "kpm_dos": (_int, [_pd, _i32, _i32, _d, _d, _pd, _pd]),
-    "kpm_sell_build": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, _i32, ctypes.POINTER(Sell)]),
+    "kpm_sell_build": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, _i32, _pi32,
+                              ctypes.POINTER(Sell)]),
     "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
     "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
                           ctypes.POINTER(_vp)]),
@@ -186,12 +188,14 @@ def dos(mu, K, a, b):
     return e, rho
 
 
-def sell_build(csr, a, b, C=32, sigma=256):
+def sell_build(csr, a, b, C=32, sigma=256, row_order=None):
     """The SELL-C-sigma layout kpm_create would upload, as numpy arrays."""
     n, rp, col, val = _csr(csr)
     s = Sell()
+    order = None if row_order is None else np.ascontiguousarray(row_order, dtype=np.int32)
     _check(lib.kpm_sell_build(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, C, sigma,
-                              ctypes.byref(s)), "kpm_sell_build")
+                              _p(order, _i32) if order is not None else None, ctypes.byref(s)),
+           "kpm_sell_build")
     try:
         out = {
             "n": s.n, "n_pad": s.n_pad, "C": s.C, "sigma": s.sigma, "n_chunks": s.n_chunks,
@@ -247,7 +251,8 @@ class Context:
     """kpm_create / kpm_destroy around a Hermitian CSR matrix and (a, b)."""
 
     def __init__(self, csr, a, b, precision=PREC_FP64, chunk_height=32, sigma=256,
-                 check_hermitian=False, device=0, torch_allocator=True, autotune=False):
+                 check_hermitian=False, device=0, torch_allocator=True, autotune=False,
+                 row_order=None):
         n, rp, col, val = _csr(csr)
         opt = default_options()
         opt.precision = precision
@@ -256,6 +261,9 @@ class Context:
         opt.check_hermitian = 1 if check_hermitian else 0
         opt.device = device
         opt.autotune = 1 if autotune else 0
+        if row_order is not None:
+            self._row_order = np.ascontiguousarray(row_order, dtype=np.int32)
+            opt.row_order = _p(self._row_order, _i32)
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator(device)
