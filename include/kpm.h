@@ -101,6 +101,20 @@ const char *kpm_status_string(int status);
 int kpm_gershgorin(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
                    double *emin, double *emax);
 
+/* Spectral bounds from a few Lanczos steps (Sec. "Problem Description": the
+ * alternative to Gershgorin).  steps Lanczos iterations in double from a
+ * random-phase start vector (SplitMix64 stream 3 of seed), no
+ * reorthogonalisation; the Ritz values theta_i of the tridiagonal matrix,
+ * each within r_i = |beta_k s_{k,i}| of an eigenvalue of H, give
+ * [min(theta_i - r_i), max(theta_i + r_i)], intersected with the
+ * Gershgorin interval.  The interval is tighter than Gershgorin's but, like
+ * any Krylov estimate, covers the spectrum only to the accuracy the
+ * residuals state: widen it (kpm_scale_from_bounds' eps) before use.
+ * Host only.  KPM_EINVAL for steps < 2 or a malformed CSR. */
+int kpm_lanczos_bounds(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                       const double *val_ri, int32_t steps, uint64_t seed, double *emin,
+                       double *emax);
+
 /* Rescaling of Sec. "Problem Description": b = (emax + emin)/2 and
  * a = (1 - eps) * 2/(emax - emin), mapping [emin, emax] onto
  * [-(1-eps), 1-eps].  KPM_EINVAL unless emax > emin and 0 <= eps < 1. */

@@ -190,6 +190,139 @@ int kpm_dos(const double *mu, int32_t M, int32_t K, double a, double b, double *
     return KPM_OK;
 }
 
+// Eigenvalues and the last components of the eigenvectors of the symmetric
+// tridiagonal matrix (alpha on the diagonal, beta off it), by Jacobi
+// rotations (k is small: a few dozen Lanczos steps).
+static void tridiag_eig(const std::vector<double> &alpha, const std::vector<double> &beta,
+                        std::vector<double> &theta, std::vector<double> &last)
+{
+    const int k = (int)alpha.size();
+    std::vector<double> A((size_t)k * k, 0.0), Q((size_t)k * k, 0.0);
+    for (int i = 0; i < k; i++) {
+        A[(size_t)i * k + i] = alpha[i];
+        Q[(size_t)i * k + i] = 1.0;
+        if (i + 1 < k)
+            A[(size_t)i * k + i + 1] = A[(size_t)(i + 1) * k + i] = beta[i];
+    }
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < k; p++)
+            for (int q = p + 1; q < k; q++)
+                off += A[(size_t)p * k + q] * A[(size_t)p * k + q];
+        if (off < 1e-30)
+            break;
+        for (int p = 0; p < k; p++)
+            for (int q = p + 1; q < k; q++) {
+                const double apq = A[(size_t)p * k + q];
+                if (std::fabs(apq) < 1e-300)
+                    continue;
+                const double tau = (A[(size_t)q * k + q] - A[(size_t)p * k + p]) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                for (int r = 0; r < k; r++) {  // A <- J^T A J, Q <- Q J
+                    const double arp = A[(size_t)r * k + p], arq = A[(size_t)r * k + q];
+                    A[(size_t)r * k + p] = c * arp - s * arq;
+                    A[(size_t)r * k + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < k; r++) {
+                    const double apr = A[(size_t)p * k + r], aqr = A[(size_t)q * k + r];
+                    A[(size_t)p * k + r] = c * apr - s * aqr;
+                    A[(size_t)q * k + r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < k; r++) {
+                    const double qrp = Q[(size_t)r * k + p], qrq = Q[(size_t)r * k + q];
+                    Q[(size_t)r * k + p] = c * qrp - s * qrq;
+                    Q[(size_t)r * k + q] = s * qrp + c * qrq;
+                }
+            }
+    }
+    theta.resize(k);
+    last.resize(k);
+    for (int i = 0; i < k; i++) {
+        theta[i] = A[(size_t)i * k + i];
+        last[i] = Q[(size_t)(k - 1) * k + i];
+    }
+}
+
+int kpm_lanczos_bounds(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                       const double *val_ri, int32_t steps, uint64_t seed, double *emin,
+                       double *emax)
+{
+    if (!emin || !emax || steps < 2)
+        return KPM_EINVAL;
+    int rc = validate_csr(n, row_ptr, col, val_ri);
+    if (rc)
+        return rc;
+    double glo, ghi;
+    rc = kpm_gershgorin(n, row_ptr, col, val_ri, &glo, &ghi);
+    if (rc)
+        return rc;
+    const int k = (int)std::min<int64_t>(steps, n);
+    // complex vectors as interleaved doubles; q1 = random phases / sqrt(n)
+    std::vector<double> qprev(2 * n, 0.0), q(2 * n), w(2 * n);
+    const uint64_t G = 0x9E3779B97F4A7C15ULL;
+    auto mix = [](uint64_t z) {
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    };
+    const uint64_t key = mix(seed + 4 * G);  // stream 3
+    const double inv = 1.0 / std::sqrt((double)n);
+    for (int64_t i = 0; i < n; i++) {
+        const double u = (double)(mix(key + ((uint64_t)i + 1) * G) >> 11) * 0x1.0p-53;
+        q[2 * i] = std::cos(6.283185307179586 * u) * inv;
+        q[2 * i + 1] = std::sin(6.283185307179586 * u) * inv;
+    }
+    std::vector<double> alpha, beta;
+    double b_prev = 0.0;
+    for (int j = 0; j < k; j++) {
+        // w = H q - b_prev q_prev
+        for (int64_t i = 0; i < n; i++) {
+            double re = 0.0, im = 0.0;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+                const double hr = val_ri[2 * e], hi = val_ri[2 * e + 1];
+                const double xr = q[2 * (int64_t)col[e]], xi = q[2 * (int64_t)col[e] + 1];
+                re += hr * xr - hi * xi;
+                im += hr * xi + hi * xr;
+            }
+            w[2 * i] = re - b_prev * qprev[2 * i];
+            w[2 * i + 1] = im - b_prev * qprev[2 * i + 1];
+        }
+        double a = 0.0;  // Re <q|w> (real for Hermitian H)
+        for (int64_t i = 0; i < 2 * n; i++)
+            a += q[i] * w[i];
+        for (int64_t i = 0; i < 2 * n; i++)
+            w[i] -= a * q[i];
+        double bn = 0.0;
+        for (int64_t i = 0; i < 2 * n; i++)
+            bn += w[i] * w[i];
+        bn = std::sqrt(bn);
+        alpha.push_back(a);
+        beta.push_back(bn);
+        if (bn < 1e-12 * (std::fabs(ghi) + std::fabs(glo)) || j == k - 1)
+            break;
+        for (int64_t i = 0; i < 2 * n; i++) {
+            qprev[i] = q[i];
+            q[i] = w[i] / bn;
+        }
+        b_prev = bn;
+    }
+    std::vector<double> theta, last;
+    tridiag_eig(alpha, std::vector<double>(beta.begin(), beta.end() - 1), theta, last);
+    // Each Ritz value theta_i is within |beta_k s_{k,i}| of an eigenvalue; the
+    // extreme ones widened by that residual, and never wider than Gershgorin.
+    const double bk = beta.back();
+    double lo = INFINITY, hi = -INFINITY;
+    for (size_t i = 0; i < theta.size(); i++) {
+        const double r = std::fabs(bk * last[i]);
+        lo = std::min(lo, theta[i] - r);
+        hi = std::max(hi, theta[i] + r);
+    }
+    *emin = std::max(lo, glo);
+    *emax = std::min(hi, ghi);
+    return KPM_OK;
+}
+
 int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
                    double a, double b, int32_t C, int32_t sigma, const int32_t *row_order,
                    kpm_sell *out)

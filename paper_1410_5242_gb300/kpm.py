@@ -77,6 +77,7 @@ _SIGS = {
     "kpm_status_string": (ctypes.c_char_p, [_int]),
     "kpm_gershgorin": (_int, [_i64, _pi64, _pi32, _pd, _pd, _pd]),
     "kpm_scale_from_bounds": (_int, [_d, _d, _d, _pd, _pd]),
+    "kpm_lanczos_bounds": (_int, [_i64, _pi64, _pi32, _pd, _i32, _u64, _pd, _pd]),
     "kpm_eta_to_mu": (_int, [_pd, _i32, _i32, _pd]),
     "kpm_dos": (_int, [_pd, _i32, _i32, _d, _d, _pd, _pd]),
     "kpm_sell_build": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, _i32, _pi32,
@@ -163,6 +164,14 @@ def gershgorin(csr):
     lo, hi = _d(), _d()
     _check(lib.kpm_gershgorin(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), ctypes.byref(lo),
                               ctypes.byref(hi)), "kpm_gershgorin")
+    return lo.value, hi.value
+
+
+def lanczos_bounds(csr, steps=30, seed=0):
+    n, rp, col, val = _csr(csr)
+    lo, hi = _d(), _d()
+    _check(lib.kpm_lanczos_bounds(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), steps, seed,
+                                  ctypes.byref(lo), ctypes.byref(hi)), "kpm_lanczos_bounds")
     return lo.value, hi.value
 
 

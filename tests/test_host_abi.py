@@ -238,3 +238,39 @@ def test_model_reproduces_paper_numbers():
     args = (2000, 10 ** 6, 13 * 10 ** 6, 32, 16)
     assert (model.kpm_traffic(*args, variant="aug_spmmv") < model.kpm_traffic(*args, variant="aug_spmv")
             < model.kpm_traffic(*args, variant="naive"))
+
+
+@pytest.mark.parametrize("which", ["ti", "ragged", "diag"])
+def test_lanczos_bounds_contain_spectrum_and_beat_gershgorin(kpm, which):
+    h = {"ti": lambda: ham.ti_hamiltonian(5, 6, 6, gamma=1.0, seed=1),
+         "ragged": lambda: ham.random_hermitian(300, 6, seed=3, empty_rows=0.05),
+         "diag": lambda: ham.diagonal_matrix(np.linspace(-2.0, 5.0, 400))}[which]()
+    lam = np.linalg.eigvalsh(ham.to_dense(h))
+    glo, ghi = kpm.gershgorin(h)
+    lo, hi = kpm.lanczos_bounds(h, steps=40, seed=2)
+    assert lo <= lam.min() + 1e-9 * abs(lam.min()) and hi >= lam.max() - 1e-9 * abs(lam.max())
+    assert glo <= lo and hi <= ghi
+    if which != "diag":   # Gershgorin is exact for a diagonal matrix
+        assert (hi - lo) < 0.8 * (ghi - glo)
+    # more steps close in on the extreme eigenvalues while still containing them
+    lo, hi = kpm.lanczos_bounds(h, steps=120, seed=2)
+    assert lo <= lam.min() + 1e-9 * abs(lam.min()) and hi >= lam.max() - 1e-9 * abs(lam.max())
+    assert abs(lo - lam.min()) < 1e-3 and abs(hi - lam.max()) < 1e-3
+
+
+def test_lanczos_bounds_keep_the_recurrence_bounded(kpm, orc):
+    h = ham.ti_hamiltonian(6, 6, 6, gamma=1.5, seed=5)
+    a, b = kpm.scale_from_bounds(*kpm.lanczos_bounds(h, steps=40, seed=1), 0.01)
+    ag, bg = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    assert a > 1.4 * ag                          # finer energy resolution per moment
+    er, _ = orc.moments(h, a, b, 512, 3, range(4))
+    n = h["n"]
+    c = 2 * er - er[:, [0, 1] * 256]
+    c[:, :2] = er[:, :2]
+    assert np.max(np.abs(c)) <= n * (1 + 1e-9)  # spectrum of a(H - b) inside [-1, 1]
+
+
+def test_lanczos_bounds_reject_bad_arguments(kpm):
+    h = ham.ti_hamiltonian(3, 3, 3)
+    with pytest.raises(kpm.KPMError):
+        kpm.lanczos_bounds(h, steps=1)
