@@ -104,10 +104,11 @@ int kpm_gershgorin(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
 /* Spectral bounds from a few Lanczos steps (Sec. "Problem Description": the
  * alternative to Gershgorin).  steps Lanczos iterations in double from a
  * random-phase start vector (SplitMix64 stream 3 of seed), no
- * reorthogonalisation; the Ritz values theta_i of the tridiagonal matrix,
- * each within r_i = |beta_k s_{k,i}| of an eigenvalue of H, give
- * [min(theta_i - r_i), max(theta_i + r_i)], intersected with the
- * Gershgorin interval.  The interval is tighter than Gershgorin's but, like
+ * reorthogonalisation; the smallest and largest Ritz values of the
+ * tridiagonal matrix, each within r = |beta_k s_k| of an eigenvalue of H
+ * (s_k the last component of its eigenvector), give
+ * [theta_min - r_min, theta_max + r_max], intersected with the Gershgorin
+ * interval.  The interval is tighter than Gershgorin's but, like
  * any Krylov estimate, covers the spectrum only to the accuracy the
  * residuals state: widen it (kpm_scale_from_bounds' eps) before use.
  * Host only.  KPM_EINVAL for steps < 2 or a malformed CSR. */

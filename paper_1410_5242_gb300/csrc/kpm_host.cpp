@@ -309,17 +309,21 @@ int kpm_lanczos_bounds(int64_t n, const int64_t *row_ptr, const int32_t *col,
     }
     std::vector<double> theta, last;
     tridiag_eig(alpha, std::vector<double>(beta.begin(), beta.end() - 1), theta, last);
-    // Each Ritz value theta_i is within |beta_k s_{k,i}| of an eigenvalue; the
-    // extreme ones widened by that residual, and never wider than Gershgorin.
+    // Ritz values lie inside [lambda_min, lambda_max] and each theta_i is
+    // within |beta_k s_{k,i}| of an eigenvalue; the extreme ones converge to
+    // the extreme eigenvalues first, so they are widened by their own
+    // residuals (interior values, ghosts included, play no part), and the
+    // result is never wider than Gershgorin.
     const double bk = beta.back();
-    double lo = INFINITY, hi = -INFINITY;
-    for (size_t i = 0; i < theta.size(); i++) {
-        const double r = std::fabs(bk * last[i]);
-        lo = std::min(lo, theta[i] - r);
-        hi = std::max(hi, theta[i] + r);
+    size_t imin = 0, imax = 0;
+    for (size_t i = 1; i < theta.size(); i++) {
+        if (theta[i] < theta[imin])
+            imin = i;
+        if (theta[i] > theta[imax])
+            imax = i;
     }
-    *emin = std::max(lo, glo);
-    *emax = std::min(hi, ghi);
+    *emin = std::max(theta[imin] - std::fabs(bk * last[imin]), glo);
+    *emax = std::min(theta[imax] + std::fabs(bk * last[imax]), ghi);
     return KPM_OK;
 }
 
