@@ -610,9 +610,18 @@ def main():
     ap.add_argument("--ensemble-runs", type=int, default=1)
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="only the 64-problem ensemble (one warm-up and --ensemble-runs timed runs)")
     args = ap.parse_args()
     if args.profile_sweeps:
         profile_sweeps(args)
+        return
+    if args.ensemble_only:
+        import torch
+        from paper_1410_5242_gb300 import build
+        build.build()
+        from paper_1410_5242_gb300 import kpm
+        print(json.dumps(ensemble_rate(kpm, 0, args, torch.cuda.current_stream(), 1, peaks()[0])))
         return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -214,10 +214,11 @@ int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, doub
  * same device and of the same precision), problem p with M[p] moments
  * (even, >= 2), R[p] random-phase vectors from seed[p] (R[p] a power of two
  * <= 64, else KPM_EUNSUPPORTED); eta[p] is host double[R[p]][M[p]].
- * All problems advance together: every sweep step is one batched launch
- * covering every problem still running plus one batched eta reduction, and
- * the whole schedule is captured into a CUDA graph and run as one graph
- * launch.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
+ * All problems advance together.  Problems whose R[p] round to the same
+ * lane shape (the same power of two) form a class; every sweep step is, per
+ * class, one batched launch covering the class's problems still running
+ * plus one batched eta reduction, and the whole schedule is captured into a
+ * CUDA graph and run as one graph launch.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
  * + kpm_batch_eta for every problem + kpm_batch_destroy. */
 int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
                       const uint64_t *seed, double *const *eta, void *stream);

@@ -1,13 +1,14 @@
 // Ensembles of independent KPM-DOS problems (disorder realisations of
 // different sizes, moment counts M and block widths R) advanced together.
 //
-// Every sweep step is one launch of batch_sweep_kernel over the tiles of
-// all problems still running at that step (problems sorted by M, so the
+// Problems are grouped into classes of equal block width R.  Every sweep
+// step is, per class, one launch of batch_sweep_kernel over the tiles of
+// the class's problems still running at that step (sorted by M, so the
 // running set is always a prefix; blocks stride over the concatenated tile
 // list and keep their eta terms in registers for as long as they stay in
 // one problem), followed by one launch of batch_reduce_kernel that turns
 // the per-block eta partials of the step into eta_{2m}, eta_{2m+1} of every
-// running problem.  The whole schedule (start
+// running problem of the class.  The whole schedule (start
 // vectors, the initial sweep, the M/2 - 1 sweeps of the longest problem)
 // is captured once into a CUDA graph and replayed with one graph launch.
 #define KPM_SWEEP_MAX_THREADS 512
@@ -213,7 +214,9 @@ struct kpm_batch {
     int device = 0, precision = 0, count = 0, steps = 0, grid = 0;
     std::vector<kpm_ctx *> ctx;      // original order
     std::vector<int> M, R;           // original order
-    std::vector<int> n_active;       // per step
+    std::vector<int> n_active;       // [step][class]: running problems of each class
+    std::vector<int> class_first;    // first sorted problem of each class (+ count)
+    std::vector<int> class_prefix;   // offset of each class's tile prefix array
     std::vector<int> sorted_to_orig;
     BatchProblem *d_probs = nullptr;
     int64_t *d_prefix = nullptr;
@@ -282,10 +285,24 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     if (!guard.ok)
         return fail(KPM_ECUDA);
 
-    // problems by decreasing M: the running set of every step is a prefix
+    // Problems grouped by lane shape (one batched launch per shape class and
+    // step: a launch whose blocks all run the same (T, E) loop keeps the SMs
+    // evenly loaded; mixing widths in one launch ran 12% slower on the
+    // 64-lattice ensemble), each class by decreasing M, so that the running
+    // set of a class is a prefix of it.
+    auto shape_of = [&](int p) {
+        int s = 0;
+        while ((1 << s) < R[p])
+            s++;
+        return s;
+    };
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return M[x] > M[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (shape_of(x) != shape_of(y))
+            return shape_of(x) < shape_of(y);
+        return M[x] > M[y];
+    });
     b->sorted_to_orig = order;
     const bool fp64 = b->precision == KPM_PREC_FP64;
     const int sd = fp64 ? 16 : 8;
@@ -293,9 +310,14 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     if (b->grid < 1)
         return fail(KPM_ECUDA);
     std::vector<BatchProblem> probs(count);
-    std::vector<int64_t> prefix(count + 1, 0);
+    std::vector<int64_t> prefix;  // per class: tile prefix over its problems (count_c + 1)
     double bytes = 0.0;
     for (int i = 0; i < count; i++) {
+        if (i == 0 || shape_of(order[i]) != shape_of(order[i - 1])) {
+            b->class_first.push_back(i);
+            b->class_prefix.push_back((int)prefix.size());
+            prefix.push_back(0);
+        }
         const int p = order[i];
         kpm_ctx *c = ctx[p];
         int rc = ensure_vectors(c, R[p]);
@@ -335,27 +357,32 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         bp.shape = shape;
         bp.tile_groups = tg;
         bp.M = M[p];
-        prefix[i + 1] = prefix[i] + n_tiles;
+        prefix.push_back(prefix.back() + n_tiles);
         const double mat = (double)c->nnz * (sd + 4);
         bytes += mat + 2.0 * R[p] * sd * c->n + (M[p] / 2 - 1) * (mat + 3.0 * R[p] * sd * c->n);
         b->info.sweeps += M[p] / 2;
     }
-    b->steps = M[order[0]] / 2;
-    b->n_active.resize(b->steps);
-    for (int s = 0; s < b->steps; s++) {
-        int k = 0;
-        while (k < count && M[order[k]] / 2 > s)
-            k++;
-        b->n_active[s] = k;
-    }
+    b->class_first.push_back(count);
+    b->steps = 0;
+    for (int i = 0; i < count; i++)
+        b->steps = std::max(b->steps, M[order[i]] / 2);
+    const int n_classes = (int)b->class_first.size() - 1;
+    b->n_active.assign((size_t)b->steps * n_classes, 0);
+    for (int cl = 0; cl < n_classes; cl++)
+        for (int s = 0; s < b->steps; s++) {
+            int k = b->class_first[cl];
+            while (k < b->class_first[cl + 1] && M[order[k]] / 2 > s)
+                k++;
+            b->n_active[(size_t)s * n_classes + cl] = k - b->class_first[cl];
+        }
 
     b->d_probs = (BatchProblem *)dev_alloc(ctx[0], sizeof(BatchProblem) * count);
-    b->d_prefix = (int64_t *)dev_alloc(ctx[0], sizeof(int64_t) * (count + 1));
+    b->d_prefix = (int64_t *)dev_alloc(ctx[0], sizeof(int64_t) * prefix.size());
     if (!b->d_probs || !b->d_prefix)
         return fail(KPM_ENOMEM);
     if (cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblem) * count,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int64_t) * (count + 1),
+        cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int64_t) * prefix.size(),
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(KPM_ECUDA);
 
@@ -372,17 +399,25 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         launches++;
     }
     const size_t smem = (size_t)(kBatchThreads / 32) * 3 * 64 * sizeof(double);
+    // The classes of a step run one after the other (as concurrent graph
+    // branches they ran 3% slower on the 64-lattice ensemble).
     for (int s = 0; s < b->steps && rc == KPM_OK; s++) {
-        const int na = b->n_active[s];
-        if (fp64)
-            batch_sweep_kernel<double><<<b->grid, kBatchThreads, smem, b->capture>>>(
-                b->d_probs, b->d_prefix, na, s);
-        else
-            batch_sweep_kernel<float><<<b->grid, kBatchThreads, smem, b->capture>>>(
-                b->d_probs, b->d_prefix, na, s);
-        batch_reduce_kernel<<<na * 128, kReduceThreads, 0, b->capture>>>(b->d_probs, na, s);
-        launches += 2;
-        rc = cuda_status(cudaGetLastError());
+        for (int cl = 0; cl < n_classes && rc == KPM_OK; cl++) {
+            const int na = b->n_active[(size_t)s * n_classes + cl];
+            if (na == 0)
+                continue;
+            const BatchProblem *cp = b->d_probs + b->class_first[cl];
+            const int64_t *cpre = b->d_prefix + b->class_prefix[cl];
+            if (fp64)
+                batch_sweep_kernel<double><<<b->grid, kBatchThreads, smem, b->capture>>>(
+                    cp, cpre, na, s);
+            else
+                batch_sweep_kernel<float><<<b->grid, kBatchThreads, smem, b->capture>>>(
+                    cp, cpre, na, s);
+            batch_reduce_kernel<<<na * 128, kReduceThreads, 0, b->capture>>>(cp, na, s);
+            launches += 2;
+            rc = cuda_status(cudaGetLastError());
+        }
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);

@@ -71,7 +71,12 @@ def test_batch_object_relaunch_is_reproducible(kpm, prec):
     with kpm.Batch([c for c, *_ in ctxs], Ms, Rs, seeds) as batch:
         info = batch.info()
         assert info["count"] == 4 and info["steps"] == max(Ms) // 2
-        assert info["kernel_launches"] == 4 + 2 * info["steps"]
+        # one phase launch per problem; per step, a sweep and a reduction for
+        # each lane-shape class (problems of equal R) that is still running
+        class_steps = {}
+        for M, R in zip(Ms, Rs):
+            class_steps[R] = max(class_steps.get(R, 0), M // 2)
+        assert info["kernel_launches"] == 4 + 2 * sum(class_steps.values())
         assert info["sweeps"] == sum(M // 2 for M in Ms)
         batch.launch()
         first = [batch.eta(p) for p in range(4)]
