@@ -175,6 +175,31 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
                    kpm_sell *out);
 void kpm_sell_release(kpm_sell *s);
 
+/* Gather lists of the staged sweep (host view, for inspection and tests).
+ * The staged aug_spmmv kernel copies, for each chunk, every V row the
+ * chunk's entries read into shared memory once, however many entries read
+ * it.  For chunk c of a kpm_sell (rows r0 = c*C .. r0+C-1) that list holds
+ * the chunk's own C rows first (local positions 0..C-1), then every other
+ * row its stored entries reference, in increasing order.  It is stored as
+ * runs of consecutive rows: runs[2q] = first row, runs[2q+1] = row count,
+ * for q in [run_ptr[c], run_ptr[c+1]); local positions count through the
+ * runs in order (adjacent runs are merged).  lidx[e] is the local position
+ * of the row that stored entry e reads (indexed like kpm_sell.col), so
+ * col[e] is the row at position lidx[e] of its chunk's list.  u_max is the
+ * longest list in rows, l_max the largest chunk_len.
+ * KPM_EINVAL for C < 8 (16-byte multiples of 16-bit indices per chunk
+ * column); KPM_EUNSUPPORTED if a list exceeds 65535 rows.  Host only; free
+ * with kpm_gather_release. */
+typedef struct kpm_gather {
+    int64_t n_chunks, n_runs;
+    int32_t u_max, l_max;
+    uint16_t *lidx;    /* [n_stored] */
+    int64_t *run_ptr;  /* [n_chunks + 1] */
+    int32_t *runs;     /* [2 * n_runs] */
+} kpm_gather;
+int kpm_gather_build(const kpm_sell *s, kpm_gather *out);
+void kpm_gather_release(kpm_gather *g);
+
 /* ============================================================ GPU calls */
 
 /* Creates a context on opt->device: validates the CSR (and, if asked,
@@ -264,6 +289,13 @@ typedef struct kpm_info {
 
 int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);
 
+/* Reads and clears the context's device error word: KPM_OK, or
+ * KPM_ETIMEOUT if a bounded device-side wait of the staged kernel gave up
+ * since the last check (its results are then invalid).  The moment calls
+ * check it themselves before returning; the device-resident calls leave it
+ * to the caller.  Synchronous. */
+int kpm_check_device_error(kpm_ctx *ctx);
+
 /* Bytes of one device vector block of width R in the context's layout:
  * n_pad rows of ld(R) complex numbers (complex double for FP64, complex
  * float for FP32), ld(R) = R, rounded up to even for FP32 when R > 1,
@@ -351,11 +383,21 @@ void kpm_naive_destroy(kpm_naive *nv);
 
 /* Launch variant the context uses for block width R: lanes per row (T),
  * complex columns per lane (E, T*E = R), threads per block, blocks per SM
- * (0 = occupancy maximum) and row groups per warp in one block tile (a
- * tile is threads/32 * (32/T) * tile_groups consecutive rows; 0 = 4), as
- * chosen by the defaults or the autotuner. */
+ * (0 = occupancy maximum), row groups per warp in one block tile (a
+ * tile is threads/32 * (32/T) * tile_groups consecutive rows; 0 = 4) and
+ * the kernel (stages), as chosen by the defaults or the autotuner.  The
+ * complex float default is the staged kernel with two stages wherever the
+ * context has gather lists (C >= 8), the width is 8..64 and two stages fit
+ * in shared memory; everything else runs the register-path kernel. */
 typedef struct kpm_launch {
     int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
+    int32_t stages;  /* 0: register-path kernel (block_threads per block, tile_groups);
+                        1..8: complex float only, the staged kernel -- per SELL chunk
+                        one producer warp copies the matrix entries, the old W rows and
+                        each V row the chunk reads (once, kpm_gather_build) into one of
+                        `stages` shared-memory stages with bulk copies, and C*T/32
+                        consumer warps compute from there; block_threads = 32 + C*T,
+                        cols_per_lane = 4, width 8..64 */
 } kpm_launch;
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */

@@ -1,0 +1,504 @@
+// The aug_spmmv sweep of Fig. 5 with the gathered V rows staged in shared
+// memory by the bulk-copy (TMA) engine, for complex float storage.
+//
+// Why: in the register-path kernel every entry's gather of R complex values
+// is a load into registers, so the bytes a streaming multiprocessor can
+// have in flight are capped by its register file, and each V row is read
+// from L2 once per entry that uses it (13 times at 13 entries per row).
+// Here one producer warp per block copies, per SELL chunk, the matrix
+// values, the 16-bit local column indices, the old W rows and every V row
+// the chunk reads -- once, however many of its entries read it (the chunk's
+// gather list, kpm_gather_build) -- into a ring of shared-memory stages with
+// cp.async.bulk, which completes on an mbarrier and occupies no registers.
+// The consumer warps compute the chunk's rows from shared memory.
+//
+// Per stage s: full[s] (the producer's arrive + the copies' byte count)
+// and empty[s] (one arrive per consumer warp once it has read the stage).
+// A chunk is one tile; blocks stride over chunks, so all blocks sweep the
+// matrix together and the V rows one chunk gathers are recent in L2.
+//
+// Arithmetic per row and column is that of aug_spmmv.cuh (same lane/column
+// ownership, same entry order, same eta accumulation and block sum): W
+// equals the register path's bit for bit; eta differs from it only in the
+// order in which rows are summed (and is itself reproducible run to run).
+//
+// Every wait is bounded (about two seconds of SM clock): on expiry the
+// thread records KPM_DEVERR_TIMEOUT in *err, raises the block's abort flag
+// (which every other wait polls), and the block stops; before exiting the
+// producer waits (bounded again) for the copies it issued.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "aug_spmmv.cuh"
+#include "kpm_internal.h"
+
+namespace kpm {
+namespace {
+
+constexpr long long kWaitLimitCycles = 4LL << 30;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Global -> shared bulk copy completing on mbarrier bar.  dst, src and
+// bytes are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Wait for the phase of parity `parity` of bar to complete.  Gives up when
+// the block's abort flag is raised (returns false) or after
+// kWaitLimitCycles (records the timeout, raises the flag, returns false).
+// honour_abort = false waits for the copies themselves even after an abort.
+__device__ __forceinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
+                                            volatile int *abort_flag, int *err, bool honour_abort)
+{
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; it++) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((it & 31) == 0) {
+            if (honour_abort && *abort_flag)
+                return false;
+            if (clock64() - t0 > kWaitLimitCycles) {
+                *abort_flag = 1;
+                if (err)
+                    atomicExch(err, KPM_DEVERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  volatile int *abort_flag, int *err,
+                                                  bool honour_abort)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    return mbar_wait_slow(bar, parity, abort_flag, err, honour_abort);
+}
+
+// The producer's record ring: the 256-byte records of the next kMetaDepth
+// tiles are fetched with cp.async (8 bytes per lane) into shared memory, so
+// the per-tile metadata never waits on a memory round trip.
+constexpr int kMetaDepth = 8;
+constexpr uint32_t kRingOffset = 256;  // after the barriers and the abort flag
+constexpr uint32_t kBarBytes = kRingOffset + kMetaDepth * KPM_REC_WORDS * 8;
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies rows [row0, row0 + nrows) of a vector block (columns col0 ..
+// col0 + RB - 1) to consecutive RB-wide rows at dst: one copy when the
+// block's rows are exactly RB wide, else one per row.
+__device__ __forceinline__ void copy_rows(uint32_t dst, const char *block, int64_t row0, int nrows,
+                                          const StagedParams &p, uint32_t row_bytes, uint32_t bar)
+{
+    const int64_t ld_bytes = (int64_t)p.ld * 8;
+    const char *src = block + row0 * ld_bytes + (int64_t)p.col0 * 8;
+    if (ld_bytes == (int64_t)row_bytes) {
+        bulk_g2s(dst, src, (uint32_t)nrows * row_bytes, bar);
+    } else {
+        for (int i = 0; i < nrows; i++)
+            bulk_g2s(dst + (uint32_t)i * row_bytes, src + i * ld_bytes, row_bytes, bar);
+    }
+}
+
+// Inclusive prefix sum over the warp's lanes.
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off)
+            v += t;
+    }
+    return v;
+}
+
+// The producer warp: for each tile of this block, wait until its stage is
+// free, announce the bytes on full[s], and issue the copies.  Lane l holds
+// word l of the tile's record, i.e. inline run l - 3; runs past the inline
+// ones are read from the overflow array 32 at a time.  Returns the number
+// of tiles armed.
+template <int RB>
+__device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem, int init,
+                                           volatile int *abort_flag)
+{
+    constexpr uint32_t row_bytes = RB * 8;
+    const int lane = threadIdx.x & 31;
+    const int NS = p.stages;
+    const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
+    const uint32_t ring0 = smem_u32(smem + kRingOffset);
+    const int2 *ring = reinterpret_cast<const int2 *>(smem + kRingOffset);
+    const uint32_t stage0 = smem_u32(smem + p.bar_bytes);
+    const char *Vb = static_cast<const char *>(p.V);
+    const char *Wb = static_cast<const char *>(p.W);
+    const char *valb = static_cast<const char *>(p.val);
+    const char *lidxb = reinterpret_cast<const char *>(p.lidx);
+    const int64_t G = gridDim.x;
+
+    for (int i = 0; i < kMetaDepth; i++) {
+        const int64_t t = blockIdx.x + i * G;
+        if (t < p.n_chunks)
+            cp_async8(ring0 + (uint32_t)(i * KPM_REC_WORDS + lane) * 8,
+                      p.rec + t * KPM_REC_WORDS + lane);
+        cp_async_commit();
+    }
+    int64_t k = 0;
+    for (int64_t tile = blockIdx.x; tile < p.n_chunks; tile += G, k++) {
+        const int slot = (int)(k % kMetaDepth);
+        cp_async_wait<kMetaDepth - 1>();
+        __syncwarp();
+        const int2 word = ring[slot * KPM_REC_WORDS + lane];
+        __syncwarp();
+        {
+            const int64_t tn = tile + kMetaDepth * G;
+            if (tn < p.n_chunks)
+                cp_async8(ring0 + (uint32_t)(slot * KPM_REC_WORDS + lane) * 8,
+                          p.rec + tn * KPM_REC_WORDS + lane);
+            cp_async_commit();
+        }
+        const int64_t e0 = (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, 0) |
+                           ((int64_t)__shfl_sync(0xffffffffu, word.y, 0) << 32);
+        const int len = __shfl_sync(0xffffffffu, word.x, 1);
+        const int nruns = __shfl_sync(0xffffffffu, word.y, 1);
+        const int64_t ovf0 = (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, 2) |
+                             ((int64_t)__shfl_sync(0xffffffffu, word.y, 2) << 32);
+        const int n_inline = min(nruns, KPM_REC_INLINE_RUNS);
+        const bool has_run = lane >= 3 && lane - 3 < n_inline;
+        const int count = has_run ? word.y : 0;
+        const int incl = warp_incl_scan(count, lane);
+        uint32_t total_rows = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+        for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
+            const int2 r = g + lane < nruns ? __ldg(p.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                                            : make_int2(0, 0);
+            total_rows += (uint32_t)__shfl_sync(0xffffffffu, warp_incl_scan(r.y, lane), 31);
+        }
+
+        const int s = (int)(k % NS);
+        const uint32_t ph = (uint32_t)((k / NS) & 1);
+        const uint32_t full = full0 + 8 * s, empty = empty0 + 8 * s;
+        if (k >= NS) {
+            // every lane waits (and acquires); the warp leaves together
+            const bool ok = mbar_wait_bounded(empty, ph ^ 1u, abort_flag, p.err, true);
+            if (!__all_sync(0xffffffffu, ok))
+                break;
+        }
+        const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
+        const uint32_t mat_entries = (uint32_t)len * (uint32_t)p.C;
+        const uint32_t bytes = total_rows * row_bytes + mat_entries * 10u +
+                               (init ? 0u : (uint32_t)p.C * row_bytes);
+        if (lane == 0) {
+            reinterpret_cast<volatile int *>(smem + p.bar_bytes + (size_t)s * p.stage_bytes +
+                                             p.off_meta)[0] = len;
+            mbar_arrive_expect_tx(full, bytes);
+        }
+        __syncwarp();
+        if (mat_entries > 0) {
+            if (lane == 0)
+                bulk_g2s(st + p.off_val, valb + e0 * 8, mat_entries * 8u, full);
+            if (lane == 1)
+                bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, mat_entries * 2u, full);
+        }
+        if (!init && lane == 2)
+            copy_rows(st + p.off_w, Wb, tile * (int64_t)p.C, p.C, p, row_bytes, full);
+        if (has_run && count > 0)
+            copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, p, row_bytes,
+                      full);
+        uint32_t base = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+        for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
+            const int2 r = g + lane < nruns ? __ldg(p.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                                            : make_int2(0, 0);
+            const int ri = warp_incl_scan(r.y, lane);
+            if (r.y > 0)
+                copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, p,
+                          row_bytes, full);
+            base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
+        }
+    }
+    cp_async_wait<0>();
+    return k;
+}
+
+// Up to 32 + C*T = 544 threads (C = 32, T = 16); the register budget that
+// leaves (112 per thread) holds a consumer's accumulators without spills.
+#define KPM_STAGED_MAX_THREADS 576
+
+template <int T, int E, bool IMAG>
+__global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
+    aug_spmmv_staged_kernel(const StagedParams p, const int init)
+{
+    static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
+    constexpr int P = 32 / T;
+    constexpr int RB = T * E;
+    constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
+    // [full[NS], empty[NS] | abort flag at byte 128 | record ring at 256 |
+    //  stages from bar_bytes on]
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = p.stages;
+    const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
+    const int n_cw = (blockDim.x >> 5) - 1;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < NS; s++) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, (uint32_t)n_cw);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    EtaAcc<float, IMAG> acc[E];
+    if (warp == 0) {
+        const int64_t armed = produce<RB>(p, smem, init, abort_flag);
+        // the copies of the last armed stages must land before the block's
+        // shared memory is reused or released
+        if (lane == 0)
+            for (int64_t k = armed > NS ? armed - NS : 0; k < armed; k++)
+                mbar_wait_bounded(full0 + 8 * (uint32_t)(k % NS), (uint32_t)((k / NS) & 1),
+                                  abort_flag, p.err, false);
+        __syncwarp();
+    } else {
+        const int cw = warp - 1;
+        const int tl = lane % T, team = lane / T;
+        const int rit = cw * P + team;  // row within the chunk
+        const int C = p.C;
+        float *W = static_cast<float *>(p.W);
+        int64_t k = 0;
+        for (int64_t tile = blockIdx.x; tile < p.n_chunks; tile += gridDim.x, k++) {
+            const int s = (int)(k % NS);
+            const uint32_t ph = (uint32_t)((k / NS) & 1);
+            const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
+            if (!__all_sync(0xffffffffu, ok))
+                break;
+            const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
+            const int len = reinterpret_cast<const volatile int *>(st + p.off_meta)[0];
+            const float *vb = reinterpret_cast<const float *>(st);
+            const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
+            const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
+
+            float acc_s[2 * E];
+            if (init) {
+#pragma unroll
+                for (int q = 0; q < 2 * E; q++)
+                    acc_s[q] = 0.f;
+            } else {
+                const float *wr = reinterpret_cast<const float *>(st + p.off_w) + rit * 2 * RB;
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    const float4 w4 =
+                        *reinterpret_cast<const float4 *>(wr + 2 * (q * T * EV + tl * EV));
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int i = 0; i < 2 * EV; i++)
+                        acc_s[q * 2 * EV + i] = -wv[i];
+                }
+            }
+#pragma unroll 4
+            for (int j = 0; j < len; j++) {
+                const int u = lid[j * C + rit];
+                const float2 h = vals[j * C + rit];
+                const float *vr = vb + (size_t)u * 2 * RB;
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    const float4 v4 =
+                        *reinterpret_cast<const float4 *>(vr + 2 * (q * T * EV + tl * EV));
+                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int e = 0; e < EV; e++) {
+                        float &sr = acc_s[q * 2 * EV + 2 * e];
+                        float &si = acc_s[q * 2 * EV + 2 * e + 1];
+                        sr = fmaf(h.x, v[2 * e], sr);
+                        sr = fmaf(-h.y, v[2 * e + 1], sr);
+                        si = fmaf(h.x, v[2 * e + 1], si);
+                        si = fmaf(h.y, v[2 * e], si);
+                    }
+                }
+            }
+            if (init) {
+#pragma unroll
+                for (int q = 0; q < 2 * E; q++)
+                    acc_s[q] *= 0.5f;
+            }
+            const int64_t row = tile * (int64_t)C + rit;
+            store_owned<float, T, E>(W, row * p.ld + p.col0 + tl * EV, acc_s);
+            // the row's own V entries: local position rit of the list
+            const float *ov = vb + (size_t)rit * 2 * RB;
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const float4 v4 =
+                    *reinterpret_cast<const float4 *>(ov + 2 * (q * T * EV + tl * EV));
+                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int e = 0; e < EV; e++)
+                    acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e], acc_s[q * 2 * EV + 2 * e + 1],
+                                        v[2 * e], v[2 * e + 1]);
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(empty0 + 8 * s);
+        }
+    }
+    __syncthreads();
+    // the stages are idle now: reuse them for the block's eta sum
+    block_eta_sum<float, T, E, IMAG>(acc, reinterpret_cast<double *>(smem + p.bar_bytes),
+                                     p.partial + (int64_t)blockIdx.x * 3 * RB, 1);
+}
+
+}  // namespace
+
+// (T, E) shapes of the staged kernel: 4 complex columns per lane as two
+// 16-byte pieces, widths 8..64.
+#define KPM_STAGED_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(16, 4)
+
+bool staged_shape_supported(int T, int E)
+{
+#define KPM_CASE(T_, E_) \
+    if (T == T_ && E == E_) \
+        return true;
+    KPM_STAGED_SHAPES(KPM_CASE)
+#undef KPM_CASE
+    return false;
+}
+
+bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, size_t max_smem,
+                   StagedLayout &o)
+{
+    auto up = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
+    if (C < 8 || T < 1 || RB < 1 || u_max < C || l_max < 0 || stages < 1 || stages > 8 ||
+        (C * T) % 32 != 0 || 32 + C * T > KPM_STAGED_MAX_THREADS)
+        return false;
+    const uint64_t row_bytes = (uint64_t)RB * 8;
+    uint64_t off = up((uint64_t)u_max * row_bytes, 128);
+    o.off_w = (uint32_t)off;
+    off = up(off + (uint64_t)C * row_bytes, 128);
+    o.off_val = (uint32_t)off;
+    off = up(off + (uint64_t)C * l_max * 8, 128);
+    o.off_lidx = (uint32_t)off;
+    off = up(off + (uint64_t)C * l_max * 2, 128);
+    o.off_meta = (uint32_t)off;
+    off = up(off + 16, 128);
+    o.stage_bytes = (uint32_t)off;
+    o.bar_bytes = kBarBytes;
+    o.stages = stages;
+    o.smem = o.bar_bytes + (uint64_t)stages * o.stage_bytes;
+    // the block's eta sum reuses the stages: one [3][RB] double row per warp
+    const uint64_t red = (uint64_t)(1 + C * T / 32) * 3 * RB * 8;
+    return o.smem <= max_smem && (uint64_t)stages * o.stage_bytes >= red &&
+           o.stage_bytes < (1u << 20);
+}
+
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem)
+{
+    const int threads = 32 + C * T;
+    int nb = 0;
+#define KPM_CASE(T_, E_)                                                                       \
+    if (T == T_ && E == E_) {                                                                  \
+        if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, false>,                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=    \
+                cudaSuccess ||                                                                 \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                     \
+                &nb, aug_spmmv_staged_kernel<T_, E_, false>, threads, smem) != cudaSuccess) {  \
+            cudaGetLastError();                                                                \
+            return 0;                                                                          \
+        }                                                                                      \
+        return nb;                                                                             \
+    }
+    KPM_STAGED_SHAPES(KPM_CASE)
+#undef KPM_CASE
+    return 0;
+}
+
+int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, bool init,
+                        void *stream)
+{
+    const int threads = 32 + p.C * T;
+    if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8)
+        return KPM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+#define KPM_CASE(T_, E_)                                                                       \
+    if (T == T_ && E == E_) {                                                                  \
+        static size_t set_t = 0, set_f = 0;                                                    \
+        if (p.with_imag) {                                                                     \
+            if (set_t < smem) {                                                                \
+                if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, true>,                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                         (int)smem) != cudaSuccess)                            \
+                    return KPM_ECUDA;                                                          \
+                set_t = smem;                                                                  \
+            }                                                                                  \
+            aug_spmmv_staged_kernel<T_, E_, true><<<grid, threads, smem, st>>>(p, init ? 1 : 0); \
+        } else {                                                                               \
+            if (set_f < smem) {                                                                \
+                if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, false>,               \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                         (int)smem) != cudaSuccess)                            \
+                    return KPM_ECUDA;                                                          \
+                set_f = smem;                                                                  \
+            }                                                                                  \
+            aug_spmmv_staged_kernel<T_, E_, false><<<grid, threads, smem, st>>>(p, init ? 1 : 0); \
+        }                                                                                      \
+        return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;                         \
+    }
+    KPM_STAGED_SHAPES(KPM_CASE)
+#undef KPM_CASE
+    return KPM_EUNSUPPORTED;
+}
+
+}  // namespace kpm

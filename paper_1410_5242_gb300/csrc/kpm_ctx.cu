@@ -171,13 +171,45 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
     }
     s.blocks_per_sm = 0;  // 0 = occupancy maximum
     s.tile_groups = c->precision == KPM_PREC_FP64 ? 8 : 1;
+    s.stages = 0;
+    if (c->precision == KPM_PREC_FP32 && c->gather_ok && s.E == 4 &&
+        staged_shape_supported(s.T, s.E)) {
+        // two stages: the copies of one chunk fly while the consumers work
+        // on the other, and two blocks fit per SM at width 32 (measured
+        // best at widths 16..64 on the 64^3 lattice; a third stage costs
+        // the second block)
+        for (int ns = 2; ns >= 2; ns--) {
+            StagedLayout L;
+            if (staged_layout(c->C, s.T, RB, c->u_max, c->l_max, ns, c->max_smem, L)) {
+                s.stages = ns;
+                break;
+            }
+        }
+    }
     return s;
+}
+
+// Shared-memory layout of a staged shape on this context (false if it does
+// not fit or the context has no gather lists).
+bool shape_layout(const kpm_ctx *c, const LaunchShape &s, StagedLayout &L)
+{
+    if (s.stages < 1 || c->precision != KPM_PREC_FP32 || !c->gather_ok ||
+        !staged_shape_supported(s.T, s.E))
+        return false;
+    return staged_layout(c->C, s.T, s.T * s.E, c->u_max, c->l_max, s.stages, c->max_smem, L);
 }
 
 int resolve_grid(kpm_ctx *c, LaunchShape &s)
 {
     int occ = 0;
-    occ = sweep_max_blocks_per_sm(c->precision, s, false);
+    if (s.stages > 0) {
+        StagedLayout L;
+        if (!shape_layout(c, s, L))
+            return -1;
+        occ = staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem);
+    } else {
+        occ = sweep_max_blocks_per_sm(c->precision, s, false);
+    }
     if (occ < 1)
         return -1;
     if (s.blocks_per_sm < 1 || s.blocks_per_sm > occ)
@@ -274,6 +306,33 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
                cudaStream_t st)
 {
     c->launches++;
+    if (cb.shape.stages > 0) {
+        StagedLayout L;
+        if (!shape_layout(c, cb.shape, L))
+            return KPM_EUNSUPPORTED;
+        StagedParams q;
+        q.rec = c->d_rec;
+        q.ovf = c->d_ovf;
+        q.lidx = c->d_lidx;
+        q.val = c->d_val;
+        q.V = p.V;
+        q.W = p.W;
+        q.partial = p.partial;
+        q.err = c->d_err;
+        q.n_chunks = c->n_chunks;
+        q.C = c->C;
+        q.ld = p.ld;
+        q.col0 = p.col0;
+        q.stages = L.stages;
+        q.with_imag = p.with_imag;
+        q.bar_bytes = L.bar_bytes;
+        q.stage_bytes = L.stage_bytes;
+        q.off_w = L.off_w;
+        q.off_val = L.off_val;
+        q.off_lidx = L.off_lidx;
+        q.off_meta = L.off_meta;
+        return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, init, st);
+    }
     if (c->precision == KPM_PREC_FP64)
         return launch_sweep_fp64(p, cb.shape, cb.grid, init, st);
     return launch_sweep_fp32(p, cb.shape, cb.grid, init, st);
@@ -471,6 +530,18 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         return fail(KPM_ECUDA);
     if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return fail(KPM_ECUDA);
+    {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) !=
+            cudaSuccess)
+            return fail(KPM_ECUDA);
+        c->max_smem = (size_t)optin;
+    }
+    c->d_err = (int *)dev_alloc(c, sizeof(int));
+    if (!c->d_err)
+        return fail(KPM_ENOMEM);
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+        return fail(KPM_ECUDA);
 
     c->d_chunk_ptr = (int64_t *)dev_alloc(c, sizeof(int64_t) * (sell.n_chunks + 1));
     c->d_chunk_len = (int32_t *)dev_alloc(c, sizeof(int32_t) * sell.n_chunks);
@@ -505,6 +576,58 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             cudaSuccess)
             return fail(KPM_ECUDA);
     }
+    if (c->precision == KPM_PREC_FP32 && sell.C >= 8) {
+        // gather lists for the staged kernel; a matrix whose lists do not fit
+        // the 16-bit local indices keeps the register-path kernel only
+        kpm_gather g;
+        const int grc = kpm_gather_build(&sell, &g);
+        if (grc == KPM_ENOMEM)
+            return fail(KPM_ENOMEM);
+        if (grc == KPM_OK) {
+            // producer records: fixed 256-byte entries, runs past the inline
+            // ones in the overflow array
+            std::vector<int2> rec, ovf;
+            try {
+                rec.assign((size_t)g.n_chunks * KPM_REC_WORDS, make_int2(0, 0));
+                for (int64_t ch = 0; ch < g.n_chunks; ch++) {
+                    int2 *r = &rec[(size_t)ch * KPM_REC_WORDS];
+                    const int64_t e0 = sell.chunk_ptr[ch];
+                    const int64_t q0 = g.run_ptr[ch], nr = g.run_ptr[ch + 1] - q0;
+                    const int64_t of = (int64_t)ovf.size();
+                    r[0] = make_int2((int)(uint32_t)e0, (int)(e0 >> 32));
+                    r[1] = make_int2(sell.chunk_len[ch], (int)nr);
+                    r[2] = make_int2((int)(uint32_t)of, (int)(of >> 32));
+                    for (int64_t q = 0; q < nr; q++) {
+                        const int2 run = make_int2(g.runs[2 * (q0 + q)], g.runs[2 * (q0 + q) + 1]);
+                        if (q < KPM_REC_INLINE_RUNS)
+                            r[3 + q] = run;
+                        else
+                            ovf.push_back(run);
+                    }
+                }
+            } catch (const std::bad_alloc &) {
+                kpm_gather_release(&g);
+                return fail(KPM_ENOMEM);
+            }
+            c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sell.n_stored);
+            c->d_rec = (int2 *)dev_alloc(c, sizeof(int2) * rec.size());
+            c->d_ovf = (int2 *)dev_alloc(c, sizeof(int2) * (ovf.empty() ? 1 : ovf.size()));
+            const bool ok =
+                c->d_lidx && c->d_rec && c->d_ovf &&
+                cudaMemcpy(c->d_lidx, g.lidx, sizeof(uint16_t) * sell.n_stored,
+                           cudaMemcpyHostToDevice) == cudaSuccess &&
+                cudaMemcpy(c->d_rec, rec.data(), sizeof(int2) * rec.size(),
+                           cudaMemcpyHostToDevice) == cudaSuccess &&
+                (ovf.empty() || cudaMemcpy(c->d_ovf, ovf.data(), sizeof(int2) * ovf.size(),
+                                           cudaMemcpyHostToDevice) == cudaSuccess);
+            c->u_max = g.u_max;
+            c->l_max = g.l_max;
+            kpm_gather_release(&g);
+            if (!ok)
+                return fail(c->d_lidx && c->d_rec && c->d_ovf ? KPM_ECUDA : KPM_ENOMEM);
+            c->gather_ok = true;
+        }
+    }
     kpm_sell_release(&sell);
     *out = c;
     return KPM_OK;
@@ -526,7 +649,24 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_partial);
     dev_free(c, c->d_eta);
     dev_free(c, c->d_eta_im);
+    dev_free(c, c->d_lidx);
+    dev_free(c, c->d_rec);
+    dev_free(c, c->d_ovf);
+    dev_free(c, c->d_err);
     delete c;
+}
+
+int kpm_check_device_error(kpm_ctx *c)
+{
+    if (!c)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    int word = 0;
+    KPM_CUDA(cudaMemcpy(&word, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (word == 0)
+        return KPM_OK;
+    KPM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    return KPM_ETIMEOUT;
 }
 
 int kpm_get_info(const kpm_ctx *c, kpm_info *out)
@@ -673,7 +813,7 @@ static int moments_to_host(kpm_ctx *c, int32_t M, int32_t R, double *eta, double
         KPM_CUDA(cudaMemcpyAsync(eta_imag, c->d_eta_im, count * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));
     KPM_CUDA(cudaStreamSynchronize(st));
-    return KPM_OK;
+    return kpm_check_device_error(c);
 }
 
 int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, double *eta_imag,
@@ -919,13 +1059,20 @@ int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)
     LaunchShape s = it != c->shapes.end() ? it->second : default_shape(c, R);
     if (s.blocks_per_sm < 1) {
         DeviceGuard guard(c->device);
-        s.blocks_per_sm = sweep_max_blocks_per_sm(c->precision, s, false);
+        StagedLayout L;
+        if (s.stages > 0)
+            s.blocks_per_sm = shape_layout(c, s, L)
+                                  ? staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem)
+                                  : 0;
+        else
+            s.blocks_per_sm = sweep_max_blocks_per_sm(c->precision, s, false);
     }
     out->lanes_per_row = s.T;
     out->cols_per_lane = s.E;
-    out->block_threads = s.threads;
+    out->block_threads = s.stages > 0 ? 32 + c->C * s.T : s.threads;
     out->blocks_per_sm = s.blocks_per_sm;
     out->tile_groups = s.tile_groups;
+    out->stages = s.stages;
     return KPM_OK;
 }
 
@@ -937,10 +1084,20 @@ int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
         l->block_threads > 1024 || (l->block_threads % 32) ||
         l->blocks_per_sm < 0 || l->tile_groups < 0 || l->tile_groups > 1024)
         return KPM_EINVAL;
+    if (l->stages < 0 || l->stages > 8)
+        return KPM_EINVAL;
     LaunchShape s{l->lanes_per_row, l->cols_per_lane, l->block_threads, l->blocks_per_sm,
                   l->tile_groups > 0 ? l->tile_groups : 4};
+    s.stages = l->stages;
     DeviceGuard guard(c->device);
-    if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)
+    if (s.stages > 0) {
+        StagedLayout L;
+        if (!shape_layout(c, s, L) || staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem) < 1)
+            return KPM_EUNSUPPORTED;
+        // the register-path fields stay valid for the ablation variants
+        if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)
+            s.threads = 128;
+    } else if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)
         return KPM_EUNSUPPORTED;
     c->shapes[R] = s;
     return KPM_OK;

@@ -475,3 +475,101 @@ void kpm_sell_release(kpm_sell *s)
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int kpm_gather_build(const kpm_sell *s, kpm_gather *out)
+{
+    if (!out)
+        return KPM_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (!s || !s->chunk_ptr || !s->chunk_len || (s->n_stored > 0 && !s->col))
+        return KPM_EINVAL;
+    if (s->C < 8)
+        return KPM_EINVAL;
+    const int64_t C = s->C;
+    const int64_t n_chunks = s->n_chunks;
+    uint16_t *lidx = (uint16_t *)std::malloc(sizeof(uint16_t) * (s->n_stored ? s->n_stored : 1));
+    int64_t *run_ptr = (int64_t *)std::malloc(sizeof(int64_t) * (n_chunks + 1));
+    if (!lidx || !run_ptr) {
+        std::free(lidx);
+        std::free(run_ptr);
+        return KPM_ENOMEM;
+    }
+    std::vector<int32_t> runs;
+    std::vector<int32_t> others;
+    int32_t u_max = 0, l_max = 0;
+    run_ptr[0] = 0;
+    for (int64_t c = 0; c < n_chunks; c++) {
+        const int64_t r0 = c * C;
+        const int64_t e0 = s->chunk_ptr[c];
+        const int64_t cnt = (int64_t)s->chunk_len[c] * C;
+        l_max = std::max(l_max, s->chunk_len[c]);
+        others.clear();
+        for (int64_t e = e0; e < e0 + cnt; e++) {
+            const int64_t j = s->col[e];
+            if (j < r0 || j >= r0 + C)
+                others.push_back((int32_t)j);
+        }
+        std::sort(others.begin(), others.end());
+        others.erase(std::unique(others.begin(), others.end()), others.end());
+        const int64_t u = C + (int64_t)others.size();
+        if (u > 65535) {
+            std::free(lidx);
+            std::free(run_ptr);
+            return KPM_EUNSUPPORTED;
+        }
+        u_max = std::max<int32_t>(u_max, (int32_t)u);
+        // own rows, then the others; a row that continues the last run joins it
+        runs.push_back((int32_t)r0);
+        runs.push_back((int32_t)C);
+        for (int32_t j : others) {
+            const size_t last = runs.size() - 2;
+            if ((int64_t)runs[last] + runs[last + 1] == j)
+                runs[last + 1]++;
+            else {
+                runs.push_back(j);
+                runs.push_back(1);
+            }
+        }
+        for (int64_t e = e0; e < e0 + cnt; e++) {
+            const int64_t j = s->col[e];
+            int64_t pos;
+            if (j >= r0 && j < r0 + C)
+                pos = j - r0;
+            else
+                pos = C + (std::lower_bound(others.begin(), others.end(), (int32_t)j) -
+                           others.begin());
+            lidx[e] = (uint16_t)pos;
+        }
+        run_ptr[c + 1] = (int64_t)runs.size() / 2;
+    }
+    int32_t *runs_out = (int32_t *)std::malloc(sizeof(int32_t) * (runs.empty() ? 1 : runs.size()));
+    if (!runs_out) {
+        std::free(lidx);
+        std::free(run_ptr);
+        return KPM_ENOMEM;
+    }
+    if (!runs.empty())
+        std::memcpy(runs_out, runs.data(), sizeof(int32_t) * runs.size());
+    out->n_chunks = n_chunks;
+    out->n_runs = (int64_t)runs.size() / 2;
+    out->u_max = u_max;
+    out->l_max = l_max;
+    out->lidx = lidx;
+    out->run_ptr = run_ptr;
+    out->runs = runs_out;
+    return KPM_OK;
+}
+
+void kpm_gather_release(kpm_gather *g)
+{
+    if (!g)
+        return;
+    std::free(g->lidx);
+    std::free(g->run_ptr);
+    std::free(g->runs);
+    std::memset(g, 0, sizeof(*g));
+}
+
+}  // extern "C"

@@ -36,8 +36,56 @@ struct SweepParams {
     int32_t with_imag;
 };
 
+// Device-side error codes a kernel records in the context's error word.
+#define KPM_DEVERR_TIMEOUT 1
+
+// Arguments of one staged sweep (aug_spmmv_staged.cu): the SELL arrays
+// plus the gather lists of kpm_gather_build, and the shared-memory layout
+// of one stage: V rows [u_max][RB] at 0, old W rows [C][RB] at off_w,
+// values [l_max*C] at off_val, local indices at off_lidx, the chunk's
+// length at off_meta.  Stages start at bar_bytes (barriers and the abort
+// flag before them).
+// Per-chunk producer record of the staged kernel: 32 int2 (256 bytes),
+// [0] = first stored entry (int64 as lo, hi), [1] = (chunk_len, run count),
+// [2] = index of run kRecInlineRuns in the overflow array (int64 as lo, hi),
+// [3 + q] = run q (first row, row count) for q < kRecInlineRuns.
+#define KPM_REC_WORDS 32
+#define KPM_REC_INLINE_RUNS 29
+
+struct StagedParams {
+    const int2 *rec;   // [n_chunks][KPM_REC_WORDS]
+    const int2 *ovf;   // runs beyond the inline ones
+    const uint16_t *lidx;
+    const void *val;
+    const void *V;
+    void *W;
+    double *partial;  // [grid][3][RB]
+    int *err;         // device error word (KPM_DEVERR_*)
+    int64_t n_chunks;
+    int32_t C, ld, col0, stages, with_imag;
+    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx, off_meta;
+};
+
+// The shared-memory layout of a staged launch; false if fewer than
+// min_stages stages fit in max_smem bytes.
+struct StagedLayout {
+    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx, off_meta;
+    int stages;
+    size_t smem;
+};
+bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, size_t max_smem,
+                   StagedLayout &out);
+bool staged_shape_supported(int T, int E);
+int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, bool init,
+                        void *stream);
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem);
+
+// stages = 0: the register-path kernel of aug_spmmv.cuh with `threads` per
+// block; stages >= 2: the staged kernel (complex float) with that many
+// shared-memory stages and 32 + C*T threads per block.
 struct LaunchShape {
     int T, E, threads, blocks_per_sm, tile_groups;
+    int stages = 0;
 };
 
 // Launch one sweep of the given shape; grid = blocks_per_sm * n_sm.
@@ -117,6 +165,15 @@ struct kpm_ctx {
     void *d_val = nullptr;
     int32_t *d_perm = nullptr;
     std::vector<int32_t> perm;  // host copy: new row -> original row
+
+    // gather lists of the staged kernel (complex float contexts)
+    bool gather_ok = false;
+    uint16_t *d_lidx = nullptr;
+    int2 *d_rec = nullptr;  // [n_chunks][KPM_REC_WORDS]
+    int2 *d_ovf = nullptr;
+    int32_t u_max = 0, l_max = 0;
+    int *d_err = nullptr;  // device error word, KPM_DEVERR_*
+    size_t max_smem = 0;   // opt-in shared memory per block
 
     // work buffers (grown on demand)
     void *d_V = nullptr, *d_W = nullptr;

@@ -64,7 +64,14 @@ class BatchInfo(ctypes.Structure):
 class Launch(ctypes.Structure):
     _fields_ = [("lanes_per_row", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("tile_groups", ctypes.c_int32)]
+                ("tile_groups", ctypes.c_int32), ("stages", ctypes.c_int32)]
+
+
+class Gather(ctypes.Structure):
+    _fields_ = [("n_chunks", ctypes.c_int64), ("n_runs", ctypes.c_int64),
+                ("u_max", ctypes.c_int32), ("l_max", ctypes.c_int32),
+                ("lidx", ctypes.POINTER(ctypes.c_uint16)), ("run_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("runs", ctypes.POINTER(ctypes.c_int32))]
 
 
 _i32, _i64, _u64, _d = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -83,6 +90,9 @@ _SIGS = {
     "kpm_sell_build": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, _i32, _pi32,
                               ctypes.POINTER(Sell)]),
     "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
+    "kpm_gather_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather)]),
+    "kpm_gather_release": (None, [ctypes.POINTER(Gather)]),
+    "kpm_check_device_error": (_int, [_vp]),
     "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
                           ctypes.POINTER(_vp)]),
     "kpm_destroy": (None, [_vp]),
@@ -206,7 +216,42 @@ def sell_build(csr, a, b, C=32, sigma=256, row_order=None):
                               _p(order, _i32) if order is not None else None, ctypes.byref(s)),
            "kpm_sell_build")
     try:
-        out = {
+        out = _sell_dict(s)
+    finally:
+        lib.kpm_sell_release(ctypes.byref(s))
+    return out
+
+
+def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
+    """The SELL layout (as sell_build) and the staged kernel's gather lists of
+    kpm_gather_build: (sell dict, {"u_max", "l_max", "lidx", "run_ptr", "runs"})."""
+    n, rp, col, val = _csr(csr)
+    s = Sell()
+    order = None if row_order is None else np.ascontiguousarray(row_order, dtype=np.int32)
+    _check(lib.kpm_sell_build(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, C, sigma,
+                              _p(order, _i32) if order is not None else None, ctypes.byref(s)),
+           "kpm_sell_build")
+    g = Gather()
+    try:
+        sell = _sell_dict(s)
+        _check(lib.kpm_gather_build(ctypes.byref(s), ctypes.byref(g)), "kpm_gather_build")
+        try:
+            gat = {
+                "u_max": g.u_max, "l_max": g.l_max,
+                "lidx": np.ctypeslib.as_array(g.lidx, (max(s.n_stored, 1),))[:s.n_stored].copy(),
+                "run_ptr": np.ctypeslib.as_array(g.run_ptr, (g.n_chunks + 1,)).copy(),
+                "runs": np.ctypeslib.as_array(g.runs, (max(2 * g.n_runs, 1),))[:2 * g.n_runs]
+                .copy().reshape(-1, 2),
+            }
+        finally:
+            lib.kpm_gather_release(ctypes.byref(g))
+    finally:
+        lib.kpm_sell_release(ctypes.byref(s))
+    return sell, gat
+
+
+def _sell_dict(s):
+    return {
             "n": s.n, "n_pad": s.n_pad, "C": s.C, "sigma": s.sigma, "n_chunks": s.n_chunks,
             "nnz": s.nnz, "n_stored": s.n_stored,
             "chunk_ptr": np.ctypeslib.as_array(s.chunk_ptr, (s.n_chunks + 1,)).copy(),
@@ -215,10 +260,7 @@ def sell_build(csr, a, b, C=32, sigma=256, row_order=None):
             "val": np.ctypeslib.as_array(s.val_ri, (max(2 * s.n_stored, 2),))[:2 * s.n_stored]
             .copy().view(np.complex128),
             "perm": np.ctypeslib.as_array(s.perm, (s.n_pad,)).copy(),
-        }
-    finally:
-        lib.kpm_sell_release(ctypes.byref(s))
-    return out
+    }
 
 
 # ------------------------------------------------------------------- GPU
@@ -315,9 +357,12 @@ class Context:
         return {f: getattr(l, f) for f, _ in Launch._fields_}
 
     def set_launch(self, R, lanes_per_row, cols_per_lane, block_threads=256, blocks_per_sm=0,
-                   tile_groups=0):
-        l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups)
+                   tile_groups=0, stages=0):
+        l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups, stages)
         _check(lib.kpm_set_launch(self.handle, R, ctypes.byref(l)), "kpm_set_launch")
+
+    def check_device_error(self):
+        _check(lib.kpm_check_device_error(self.handle), "kpm_check_device_error")
 
     def autotune(self, R, sweeps=5, stream=None):
         """kpm_autotune: returns the launch shape chosen for the widest block."""

@@ -1,0 +1,141 @@
+"""GPU tests of the staged sweep kernel (complex float storage; the V rows
+each SELL chunk gathers are copied once into shared memory by bulk copies,
+see include/kpm.h, kpm_launch.stages): the updated W must equal the
+register-path kernel's bit for bit (same products, same order per row), eta
+must agree with it to rounding of the summation order, and the moments must
+match the FP64 oracle within the FP32-form tolerance, for every stage count,
+block width, column-block split and row ordering."""
+import numpy as np
+import pytest
+
+from kpm_inputs import hamiltonians as ham
+from kpm_inputs import vectors
+
+pytestmark = pytest.mark.gpu
+
+FP32_MU_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm as k
+    return k
+
+
+def scaled(h, k):
+    return k.scale_from_bounds(*k.gershgorin(h), 0.01)
+
+
+def sweep(ctx, R, V, W, init):
+    import torch
+    dV, dW = ctx.new_block(R), ctx.new_block(R)
+    ctx.block_upload(R, V, dV)
+    ctx.block_upload(R, W, dW)
+    eta = torch.zeros(3 * R, dtype=torch.float64, device="cuda")
+    ctx.aug_spmmv(R, dV, dW, eta, init=init)
+    torch.cuda.synchronize()
+    ctx.check_device_error()
+    return ctx.block_download(R, dW), eta.cpu().numpy().reshape(3, R)
+
+
+def test_staged_is_the_complex_float_default(kpm):
+    h = ham.ti_hamiltonian(8, 8, 8, gamma=0.5, seed=0)
+    a, b = scaled(h, kpm)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        for R in (8, 16, 32, 64):
+            l = ctx.get_launch(R)
+            assert l["stages"] >= 2 and l["cols_per_lane"] == 4, (R, l)
+            assert l["block_threads"] == 32 + 32 * (R // 4)
+    with kpm.create(h, a, b) as ctx:
+        assert ctx.get_launch(32)["stages"] == 0  # complex double: register path
+
+
+@pytest.mark.parametrize("R", [8, 16, 24, 32, 64, 100])
+@pytest.mark.parametrize("order", ["lattice", "cube"])
+def test_staged_sweep_equals_register_path(kpm, R, order):
+    dims = (8, 6, 5)
+    h = ham.ti_hamiltonian(*dims, gamma=0.8, seed=2)
+    a, b = scaled(h, kpm)
+    row_order = ham.cube_row_order(dims, block=(2, 2, 2)) if order == "cube" else None
+    g = np.random.default_rng(R)
+    V = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+    W = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32, row_order=row_order) as ctx:
+        widths = [w for w in (64, 32, 16, 8, 4, 2, 1) if R & w]
+        for init in (False, True):
+            ref = None
+            for stages in (0, 2, 3, 4):
+                try:
+                    for w in widths:
+                        if w >= 8:
+                            ctx.set_launch(w, w // 4, 4, 128, stages=stages)
+                        else:  # narrow blocks always run the register path
+                            ctx.set_launch(w, 1, w, 128)
+                except kpm.KPMError as e:
+                    # more stages of 64-wide rows than shared memory holds
+                    assert e.status == kpm.KPM_EUNSUPPORTED and stages > 2
+                    continue
+                Wg, eg = sweep(ctx, R, V, W, init)
+                if ref is None:
+                    ref = (Wg, eg)
+                    continue
+                assert np.array_equal(Wg, ref[0]), (stages, init)
+                np.testing.assert_allclose(eg, ref[1], rtol=0, atol=1e-12 * ref[1][0].max())
+
+
+@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("R", [8, 32, 64])
+def test_staged_moments_match_oracle(kpm, orc, stages, R):
+    h = ham.ti_hamiltonian(6, 7, 5, gamma=1.5, seed=4)
+    a, b = scaled(h, kpm)
+    M = 64
+    cols = [0, R - 1]
+    ref, _ = orc.moments(h, a, b, M, 9, cols)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        try:
+            ctx.set_launch(R, R // 4, 4, 128, stages=stages)
+        except kpm.KPMError as e:
+            assert e.status == kpm.KPM_EUNSUPPORTED and stages > 2
+            pytest.skip("%d stages of %d-wide rows do not fit in shared memory" % (stages, R))
+        eta = ctx.moments(M, R, 9)
+    dmu = np.abs(kpm.eta_to_mu(eta[cols]) - orc.eta_to_mu(ref)).max()
+    assert dmu <= FP32_MU_TOL, dmu
+
+
+def test_staged_ragged_matrix(kpm, orc):
+    # rows of different lengths, empty rows, padding rows, C = 16 and 64
+    h = ham.random_hermitian(517, 9, seed=13, empty_rows=0.08)
+    a, b = scaled(h, kpm)
+    M, R = 40, 16
+    ref, _ = orc.moments(h, a, b, M, 5, range(R))
+    for C in (16, 64):
+        for sigma in (1, 64):
+            with kpm.create(h, a, b, precision=kpm.PREC_FP32, chunk_height=C, sigma=sigma) as ctx:
+                assert ctx.get_launch(R)["stages"] >= 2
+                eta = ctx.moments(M, R, 5)
+            dmu = np.abs(kpm.eta_to_mu(eta) - orc.eta_to_mu(ref)).max()
+            assert dmu <= FP32_MU_TOL, (C, sigma, dmu)
+
+
+def test_staged_full_size_sweep_equals_register_path(kpm):
+    """64^3 lattice (N = 1,048,576), R = 32 in the bench's launch: W of one
+    sweep bit for bit and eta against the register path."""
+    import torch
+    h = ham.ti_hamiltonian(64, 64, 64, gamma=1.0, seed=2)
+    a, b = scaled(h, kpm)
+    R = 32
+    V = vectors.random_phase_block(2, h["n"], range(R))
+    g = np.random.default_rng(1)
+    W = (g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))).astype(np.complex64)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        assert ctx.get_launch(R)["stages"] >= 2
+        Ws, es = sweep(ctx, R, V, W, False)
+        ctx.set_launch(R, 8, 4, 128, stages=0)
+        Wr, er = sweep(ctx, R, V, W, False)
+    assert np.array_equal(Ws, Wr)
+    np.testing.assert_allclose(es, er, rtol=0, atol=1e-12 * er[0].max())
+    torch.cuda.synchronize()

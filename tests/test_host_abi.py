@@ -274,3 +274,61 @@ def test_lanczos_bounds_reject_bad_arguments(kpm):
     h = ham.ti_hamiltonian(3, 3, 3)
     with pytest.raises(kpm.KPMError):
         kpm.lanczos_bounds(h, steps=1)
+
+
+def _expand_runs(gat, c):
+    """The gather list of chunk c as row numbers, position by position."""
+    rows = []
+    for start, count in gat["runs"][gat["run_ptr"][c]:gat["run_ptr"][c + 1]]:
+        rows.extend(range(start, start + count))
+    return np.array(rows, dtype=np.int64)
+
+
+@pytest.mark.parametrize("C,order", [(32, None), (8, None), (32, "cube"), (64, None)])
+def test_gather_lists_reproduce_the_column_indices(kpm, C, order):
+    # every stored entry reads, through its chunk's list, exactly the V row
+    # its SELL column index names; each list holds the chunk's own rows
+    # first and every other row once, in increasing order
+    h = ham.ti_hamiltonian(6, 5, 4, gamma=0.7, seed=3)
+    row_order = ham.cube_row_order((6, 5, 4), block=(2, 2, 2)) if order else None
+    for m in (h, ham.random_hermitian(203, 5, seed=4, empty_rows=0.05)):
+        ro = row_order if m is h else None
+        sell, gat = kpm.gather_build(m, 0.1, 0.3, C=C, sigma=1, row_order=ro)
+        assert gat["l_max"] == sell["chunk_len"].max()
+        u_max = 0
+        for c in range(sell["n_chunks"]):
+            rows = _expand_runs(gat, c)
+            r0 = c * C
+            np.testing.assert_array_equal(rows[:C], np.arange(r0, r0 + C))
+            rest = rows[C:]
+            assert np.all(np.diff(rest) > 0)
+            assert not np.any((rest >= r0) & (rest < r0 + C))
+            e0, e1 = sell["chunk_ptr"][c], sell["chunk_ptr"][c + 1]
+            cols = sell["col"][e0:e1]
+            np.testing.assert_array_equal(rows[gat["lidx"][e0:e1]], cols)
+            # nothing listed that no entry reads (own rows excepted)
+            assert set(rest.tolist()) == set(cols.tolist()) - set(range(r0, r0 + C))
+            # adjacent runs are merged
+            runs = gat["runs"][gat["run_ptr"][c]:gat["run_ptr"][c + 1]]
+            assert np.all(runs[:-1, 0] + runs[:-1, 1] != runs[1:, 0])
+            u_max = max(u_max, rows.size)
+        assert gat["u_max"] == u_max
+
+
+def test_gather_lists_of_the_lattice_are_few_runs(kpm):
+    # in lattice order a chunk of 8 sites along x reads its own 8 sites, the
+    # two x neighbours and 8 sites in each of +-y, +-z: 42 sites in at most
+    # 7 runs (fewer where an x neighbour continues the own rows)
+    h = ham.ti_hamiltonian(16, 8, 8, gamma=0.5, seed=1)
+    sell, gat = kpm.gather_build(h, 0.1, 0.0, C=32, sigma=1)
+    nruns = np.diff(gat["run_ptr"])
+    assert gat["u_max"] == 42 * 4
+    assert np.all(np.diff(gat["run_ptr"]) <= 7)
+    assert nruns.min() >= 5
+
+
+def test_gather_build_rejects_small_chunks(kpm):
+    h = ham.ti_hamiltonian(3, 3, 3)
+    with pytest.raises(kpm.KPMError) as e:
+        kpm.gather_build(h, 0.1, 0.0, C=4, sigma=1)
+    assert e.value.status == kpm.KPM_EINVAL
