@@ -243,7 +243,10 @@ int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, doub
  * lane shape (the same power of two) form a class; every sweep step is, per
  * class, one batched launch covering the class's problems still running
  * plus one batched eta reduction, and the whole schedule is captured into a
- * CUDA graph and run as one graph launch.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
+ * CUDA graph and run as one graph launch.  Complex float classes of width
+ * 8..64 whose contexts all have gather lists with one chunk height run the
+ * staged kernel (kpm_launch.stages) over the class's chunks, the others the
+ * register-path kernel.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
  * + kpm_batch_eta for every problem + kpm_batch_destroy. */
 int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
                       const uint64_t *seed, double *const *eta, void *stream);
@@ -270,7 +273,8 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
  * stream.  Each run redraws the start vectors from the seeds. */
 int kpm_batch_launch(kpm_batch *batch, void *stream);
 /* Copies problem p's eta (host double[R[p]][M[p]]) after the launch on
- * stream; synchronises the stream. */
+ * stream; synchronises the stream.  KPM_ETIMEOUT if a bounded device-side
+ * wait of the last launch gave up (the moments are then invalid). */
 int kpm_batch_eta(kpm_batch *batch, int32_t p, double *eta, void *stream);
 int kpm_batch_get_info(const kpm_batch *batch, kpm_batch_info *out);
 void kpm_batch_destroy(kpm_batch *batch);

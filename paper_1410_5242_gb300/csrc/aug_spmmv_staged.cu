@@ -17,6 +17,13 @@
 // A chunk is one tile; blocks stride over chunks, so all blocks sweep the
 // matrix together and the V rows one chunk gathers are recent in L2.
 //
+// One launch may cover several independent problems (an ensemble: one
+// batched launch per step, kpm_batch.cu): their chunks form one global tile
+// sequence, a table in shared memory gives each problem's arrays, and the
+// consumer warps flush their eta sums to a problem's partial slot when the
+// tile sequence moves on to the next problem.  A single problem is a table
+// of one.
+//
 // Arithmetic per row and column is that of aug_spmmv.cuh (same lane/column
 // ownership, same entry order, same eta accumulation and block sum): W
 // equals the register path's bit for bit; eta differs from it only in the
@@ -122,7 +129,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // the per-tile metadata never waits on a memory round trip.
 constexpr int kMetaDepth = 8;
 constexpr uint32_t kRingOffset = 256;  // after the barriers and the abort flag
-constexpr uint32_t kBarBytes = kRingOffset + kMetaDepth * KPM_REC_WORDS * 8;
+constexpr uint32_t kRedOffset = kRingOffset + kMetaDepth * KPM_REC_WORDS * 8;
+constexpr uint32_t kTableOffset = kRedOffset + 3 * 64 * 8;  // eta sum of up to 64 columns
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
 {
@@ -140,14 +148,14 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Copies rows [row0, row0 + nrows) of a vector block (columns col0 ..
-// col0 + RB - 1) to consecutive RB-wide rows at dst: one copy when the
-// block's rows are exactly RB wide, else one per row.
+// Copies rows [row0, row0 + nrows) of a vector block (rows of ld complex
+// floats; columns col0 .. col0 + RB - 1) to consecutive RB-wide rows at
+// dst: one copy when the block's rows are exactly RB wide, else one per row.
 __device__ __forceinline__ void copy_rows(uint32_t dst, const char *block, int64_t row0, int nrows,
-                                          const StagedParams &p, uint32_t row_bytes, uint32_t bar)
+                                          int ld, int col0, uint32_t row_bytes, uint32_t bar)
 {
-    const int64_t ld_bytes = (int64_t)p.ld * 8;
-    const char *src = block + row0 * ld_bytes + (int64_t)p.col0 * 8;
+    const int64_t ld_bytes = (int64_t)ld * 8;
+    const char *src = block + row0 * ld_bytes + (int64_t)col0 * 8;
     if (ld_bytes == (int64_t)row_bytes) {
         bulk_g2s(dst, src, (uint32_t)nrows * row_bytes, bar);
     } else {
@@ -168,13 +176,24 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
     return v;
 }
 
+// The problem table in shared memory and the problem owning a global tile
+// (cursor moves forward only: a block's tiles increase).
+__device__ __forceinline__ int advance_problem(const StagedProblem *tab, int n_probs, int pi,
+                                               int64_t gt)
+{
+    while (pi + 1 < n_probs && gt >= tab[pi].tile0 + tab[pi].n_tiles)
+        pi++;
+    return pi;
+}
+
 // The producer warp: for each tile of this block, wait until its stage is
 // free, announce the bytes on full[s], and issue the copies.  Lane l holds
 // word l of the tile's record, i.e. inline run l - 3; runs past the inline
 // ones are read from the overflow array 32 at a time.  Returns the number
 // of tiles armed.
 template <int RB>
-__device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem, int init,
+__device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem,
+                                           const StagedProblem *tab, int64_t total,
                                            volatile int *abort_flag)
 {
     constexpr uint32_t row_bytes = RB * 8;
@@ -184,33 +203,36 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
     const uint32_t ring0 = smem_u32(smem + kRingOffset);
     const int2 *ring = reinterpret_cast<const int2 *>(smem + kRingOffset);
     const uint32_t stage0 = smem_u32(smem + p.bar_bytes);
-    const char *Vb = static_cast<const char *>(p.V);
-    const char *Wb = static_cast<const char *>(p.W);
-    const char *valb = static_cast<const char *>(p.val);
-    const char *lidxb = reinterpret_cast<const char *>(p.lidx);
     const int64_t G = gridDim.x;
+    const int par = p.parity;
 
-    for (int i = 0; i < kMetaDepth; i++) {
-        const int64_t t = blockIdx.x + i * G;
-        if (t < p.n_chunks)
-            cp_async8(ring0 + (uint32_t)(i * KPM_REC_WORDS + lane) * 8,
-                      p.rec + t * KPM_REC_WORDS + lane);
+    // the record stream runs kMetaDepth tiles ahead of the issue stream
+    int pj = 0;
+    auto fetch_record = [&](int64_t t, uint32_t slot) {
+        if (t < total) {
+            pj = advance_problem(tab, p.n_probs, pj, t);
+            cp_async8(ring0 + (slot * KPM_REC_WORDS + lane) * 8,
+                      tab[pj].rec + (t - tab[pj].tile0) * KPM_REC_WORDS + lane);
+        }
         cp_async_commit();
-    }
+    };
+    for (int i = 0; i < kMetaDepth; i++)
+        fetch_record(blockIdx.x + i * G, (uint32_t)i);
+    int pi = 0;
     int64_t k = 0;
-    for (int64_t tile = blockIdx.x; tile < p.n_chunks; tile += G, k++) {
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         const int slot = (int)(k % kMetaDepth);
         cp_async_wait<kMetaDepth - 1>();
         __syncwarp();
         const int2 word = ring[slot * KPM_REC_WORDS + lane];
         __syncwarp();
-        {
-            const int64_t tn = tile + kMetaDepth * G;
-            if (tn < p.n_chunks)
-                cp_async8(ring0 + (uint32_t)(slot * KPM_REC_WORDS + lane) * 8,
-                          p.rec + tn * KPM_REC_WORDS + lane);
-            cp_async_commit();
-        }
+        fetch_record(gt + kMetaDepth * G, (uint32_t)slot);
+        pi = advance_problem(tab, p.n_probs, pi, gt);
+        const StagedProblem &P = tab[pi];
+        const int64_t lt = gt - P.tile0;  // chunk within the problem
+        const char *Vb = static_cast<const char *>(P.buf[par]);
+        const char *Wb = static_cast<const char *>(P.buf[par ^ 1]);
+
         const int64_t e0 = (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, 0) |
                            ((int64_t)__shfl_sync(0xffffffffu, word.y, 0) << 32);
         const int len = __shfl_sync(0xffffffffu, word.x, 1);
@@ -223,8 +245,9 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const int incl = warp_incl_scan(count, lane);
         uint32_t total_rows = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
         for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
-            const int2 r = g + lane < nruns ? __ldg(p.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
-                                            : make_int2(0, 0);
+            const int2 r = g + lane < nruns
+                               ? __ldg(P.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                               : make_int2(0, 0);
             total_rows += (uint32_t)__shfl_sync(0xffffffffu, warp_incl_scan(r.y, lane), 31);
         }
 
@@ -240,37 +263,89 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
         const uint32_t mat_entries = (uint32_t)len * (uint32_t)p.C;
         const uint32_t bytes = total_rows * row_bytes + mat_entries * 10u +
-                               (init ? 0u : (uint32_t)p.C * row_bytes);
+                               (p.init ? 0u : (uint32_t)p.C * row_bytes);
         if (lane == 0) {
-            reinterpret_cast<volatile int *>(smem + p.bar_bytes + (size_t)s * p.stage_bytes +
-                                             p.off_meta)[0] = len;
+            volatile int *meta = reinterpret_cast<volatile int *>(
+                smem + p.bar_bytes + (size_t)s * p.stage_bytes + p.off_meta);
+            meta[0] = len;
+            meta[1] = pi;
+            meta[2] = (int)lt;
             mbar_arrive_expect_tx(full, bytes);
         }
         __syncwarp();
         if (mat_entries > 0) {
             if (lane == 0)
-                bulk_g2s(st + p.off_val, valb + e0 * 8, mat_entries * 8u, full);
+                bulk_g2s(st + p.off_val, static_cast<const char *>(P.val) + e0 * 8,
+                         mat_entries * 8u, full);
             if (lane == 1)
-                bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, mat_entries * 2u, full);
+                bulk_g2s(st + p.off_lidx, reinterpret_cast<const char *>(P.lidx) + e0 * 2,
+                         mat_entries * 2u, full);
         }
-        if (!init && lane == 2)
-            copy_rows(st + p.off_w, Wb, tile * (int64_t)p.C, p.C, p, row_bytes, full);
+        if (!p.init && lane == 2)
+            copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, P.ld, P.col0, row_bytes, full);
         if (has_run && count > 0)
-            copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, p, row_bytes,
-                      full);
+            copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, P.ld, P.col0,
+                      row_bytes, full);
         uint32_t base = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
         for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
-            const int2 r = g + lane < nruns ? __ldg(p.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
-                                            : make_int2(0, 0);
+            const int2 r = g + lane < nruns
+                               ? __ldg(P.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                               : make_int2(0, 0);
             const int ri = warp_incl_scan(r.y, lane);
             if (r.y > 0)
-                copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, p,
-                          row_bytes, full);
+                copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, P.ld,
+                          P.col0, row_bytes, full);
             base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
         }
     }
     cp_async_wait<0>();
     return k;
+}
+
+__device__ __forceinline__ void consumer_bar(int n_cw)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(n_cw * 32) : "memory");
+}
+
+// The consumer warps' eta sums for one problem, in a fixed order: lanes of
+// equal columns by an xor butterfly, then warp after warp into red (3*RB
+// doubles), then red to the problem's partial slot.  Resets acc.
+template <int T, int E, bool IMAG>
+__device__ __forceinline__ void flush_eta(EtaAcc<float, IMAG> (&acc)[E], double *red,
+                                          const StagedProblem &P, int64_t slot, int cw, int n_cw)
+{
+    constexpr int RB = T * E;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane % T, team = lane / T;
+    double out[3 * E];
+#pragma unroll
+    for (int k = 0; k < E; k++)
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            out[q * E + k] = acc[k].get(q);
+#pragma unroll
+    for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 3 * E; i++)
+            out[i] += __shfl_xor_sync(0xffffffffu, out[i], off);
+    for (int w = 0; w < n_cw; w++) {
+        if (cw == w && team == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    double &d = red[q * RB + owned_column<float, T, E>(tl, k)];
+                    d = w == 0 ? out[q * E + k] : d + out[q * E + k];
+                }
+        }
+        consumer_bar(n_cw);
+    }
+    for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
+        P.partial[slot * P.ps + t * P.qs] = red[t];
+    consumer_bar(n_cw);
+#pragma unroll
+    for (int k = 0; k < E; k++)
+        acc[k] = EtaAcc<float, IMAG>();
 }
 
 // Up to 32 + C*T = 544 threads (C = 32, T = 16); the register budget that
@@ -279,14 +354,15 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
 
 template <int T, int E, bool IMAG>
 __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
-    aug_spmmv_staged_kernel(const StagedParams p, const int init)
+    aug_spmmv_staged_kernel(const StagedParams p)
 {
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
     constexpr int P = 32 / T;
     constexpr int RB = T * E;
     constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
-    // [full[NS], empty[NS] | abort flag at byte 128 | record ring at 256 |
-    //  stages from bar_bytes on]
+    // [full[NS], empty[NS] | abort flag at 128 | record ring at 256 | eta
+    //  sum at kRedOffset | problem table at kTableOffset | stages from
+    //  bar_bytes on]
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -294,6 +370,8 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
     const int n_cw = (blockDim.x >> 5) - 1;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);
+    StagedProblem *tab = reinterpret_cast<StagedProblem *>(smem + kTableOffset);
+    double *red = reinterpret_cast<double *>(smem + kRedOffset);
     if (threadIdx.x == 0) {
         *abort_flag = 0;
         for (int s = 0; s < NS; s++) {
@@ -302,13 +380,19 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    {
+        const StagedProblem *src = p.probs ? p.probs : &p.one;
+        const int words = p.n_probs * (int)(sizeof(StagedProblem) / 8);
+        for (int i = threadIdx.x; i < words; i += blockDim.x)
+            reinterpret_cast<uint64_t *>(tab)[i] = reinterpret_cast<const uint64_t *>(src)[i];
+    }
     __syncthreads();
+    const int64_t total = tab[p.n_probs - 1].tile0 + tab[p.n_probs - 1].n_tiles;
 
-    EtaAcc<float, IMAG> acc[E];
     if (warp == 0) {
-        const int64_t armed = produce<RB>(p, smem, init, abort_flag);
+        const int64_t armed = produce<RB>(p, smem, tab, total, abort_flag);
         // the copies of the last armed stages must land before the block's
-        // shared memory is reused or released
+        // shared memory is released
         if (lane == 0)
             for (int64_t k = armed > NS ? armed - NS : 0; k < armed; k++)
                 mbar_wait_bounded(full0 + 8 * (uint32_t)(k % NS), (uint32_t)((k / NS) & 1),
@@ -319,22 +403,33 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
         const int tl = lane % T, team = lane / T;
         const int rit = cw * P + team;  // row within the chunk
         const int C = p.C;
-        float *W = static_cast<float *>(p.W);
+        EtaAcc<float, IMAG> acc[E];
+        int cur = -1;        // problem whose eta terms acc holds
+        int64_t slot = 0;    // its partial slot: this block's first chunk of it
         int64_t k = 0;
-        for (int64_t tile = blockIdx.x; tile < p.n_chunks; tile += gridDim.x, k++) {
+        for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, k++) {
             const int s = (int)(k % NS);
             const uint32_t ph = (uint32_t)((k / NS) & 1);
             const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
             if (!__all_sync(0xffffffffu, ok))
                 break;
             const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
-            const int len = reinterpret_cast<const volatile int *>(st + p.off_meta)[0];
+            const volatile int *meta = reinterpret_cast<const volatile int *>(st + p.off_meta);
+            const int len = meta[0], pi = meta[1];
+            const int64_t lt = meta[2];
+            if (pi != cur) {
+                if (cur >= 0)
+                    flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
+                cur = pi;
+                slot = lt;
+            }
+            const StagedProblem &Pb = tab[pi];
             const float *vb = reinterpret_cast<const float *>(st);
             const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
             const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
 
             float acc_s[2 * E];
-            if (init) {
+            if (p.init) {
 #pragma unroll
                 for (int q = 0; q < 2 * E; q++)
                     acc_s[q] = 0.f;
@@ -371,13 +466,14 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
                     }
                 }
             }
-            if (init) {
+            if (p.init) {
 #pragma unroll
                 for (int q = 0; q < 2 * E; q++)
                     acc_s[q] *= 0.5f;
             }
-            const int64_t row = tile * (int64_t)C + rit;
-            store_owned<float, T, E>(W, row * p.ld + p.col0 + tl * EV, acc_s);
+            const int64_t row = lt * (int64_t)C + rit;
+            float *W = static_cast<float *>(Pb.buf[p.parity ^ 1]);
+            store_owned<float, T, E>(W, row * Pb.ld + Pb.col0 + tl * EV, acc_s);
             // the row's own V entries: local position rit of the list
             const float *ov = vb + (size_t)rit * 2 * RB;
 #pragma unroll
@@ -394,11 +490,15 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
             if (lane == 0)
                 mbar_arrive(empty0 + 8 * s);
         }
+        if (cur >= 0) {
+            flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
+        } else if (p.probs == nullptr) {
+            // a single problem's partials are read for every block: a block
+            // without chunks contributes zeros
+            for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
+                tab[0].partial[(int64_t)blockIdx.x * tab[0].ps + t * tab[0].qs] = 0.0;
+        }
     }
-    __syncthreads();
-    // the stages are idle now: reuse them for the block's eta sum
-    block_eta_sum<float, T, E, IMAG>(acc, reinterpret_cast<double *>(smem + p.bar_bytes),
-                                     p.partial + (int64_t)blockIdx.x * 3 * RB, 1);
 }
 
 }  // namespace
@@ -417,12 +517,12 @@ bool staged_shape_supported(int T, int E)
     return false;
 }
 
-bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, size_t max_smem,
-                   StagedLayout &o)
+bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n_probs,
+                   size_t max_smem, StagedLayout &o)
 {
     auto up = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
-    if (C < 8 || T < 1 || RB < 1 || u_max < C || l_max < 0 || stages < 1 || stages > 8 ||
-        (C * T) % 32 != 0 || 32 + C * T > KPM_STAGED_MAX_THREADS)
+    if (C < 8 || T < 1 || RB < 1 || RB > 64 || u_max < C || l_max < 0 || stages < 1 ||
+        stages > 8 || n_probs < 1 || (C * T) % 32 != 0 || 32 + C * T > KPM_STAGED_MAX_THREADS)
         return false;
     const uint64_t row_bytes = (uint64_t)RB * 8;
     uint64_t off = up((uint64_t)u_max * row_bytes, 128);
@@ -435,13 +535,10 @@ bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, size_
     o.off_meta = (uint32_t)off;
     off = up(off + 16, 128);
     o.stage_bytes = (uint32_t)off;
-    o.bar_bytes = kBarBytes;
+    o.bar_bytes = (uint32_t)up(kTableOffset + (uint64_t)n_probs * sizeof(StagedProblem), 128);
     o.stages = stages;
     o.smem = o.bar_bytes + (uint64_t)stages * o.stage_bytes;
-    // the block's eta sum reuses the stages: one [3][RB] double row per warp
-    const uint64_t red = (uint64_t)(1 + C * T / 32) * 3 * RB * 8;
-    return o.smem <= max_smem && (uint64_t)stages * o.stage_bytes >= red &&
-           o.stage_bytes < (1u << 20);
+    return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 
 int staged_max_blocks_per_sm(int T, int E, int C, size_t smem)
@@ -465,11 +562,11 @@ int staged_max_blocks_per_sm(int T, int E, int C, size_t smem)
     return 0;
 }
 
-int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, bool init,
-                        void *stream)
+int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream)
 {
     const int threads = 32 + p.C * T;
-    if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8)
+    if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8 ||
+        p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1))
         return KPM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
@@ -483,7 +580,7 @@ int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t sm
                     return KPM_ECUDA;                                                          \
                 set_t = smem;                                                                  \
             }                                                                                  \
-            aug_spmmv_staged_kernel<T_, E_, true><<<grid, threads, smem, st>>>(p, init ? 1 : 0); \
+            aug_spmmv_staged_kernel<T_, E_, true><<<grid, threads, smem, st>>>(p);             \
         } else {                                                                               \
             if (set_f < smem) {                                                                \
                 if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, false>,               \
@@ -492,7 +589,7 @@ int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t sm
                     return KPM_ECUDA;                                                          \
                 set_f = smem;                                                                  \
             }                                                                                  \
-            aug_spmmv_staged_kernel<T_, E_, false><<<grid, threads, smem, st>>>(p, init ? 1 : 0); \
+            aug_spmmv_staged_kernel<T_, E_, false><<<grid, threads, smem, st>>>(p);             \
         }                                                                                      \
         return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;                         \
     }

@@ -210,8 +210,18 @@ int batch_grid(int n_sm)
 
 }  // namespace
 
+// A class whose problems run the staged kernel (complex float with gather
+// lists): its launch shape and shared-memory layout.
+struct StagedClass {
+    bool on = false;
+    int T = 0, E = 4, grid = 0;
+    StagedLayout L{};
+};
+
 struct kpm_batch {
     int device = 0, precision = 0, count = 0, steps = 0, grid = 0;
+    std::vector<StagedClass> staged;       // per class
+    StagedProblem *d_sprobs = nullptr;     // per sorted problem (staged classes)
     std::vector<kpm_ctx *> ctx;      // original order
     std::vector<int> M, R;           // original order
     std::vector<int> n_active;       // [step][class]: running problems of each class
@@ -241,6 +251,7 @@ void batch_release(kpm_batch *b)
     if (!b->ctx.empty()) {
         dev_free(b->ctx[0], b->d_probs);
         dev_free(b->ctx[0], b->d_prefix);
+        dev_free(b->ctx[0], b->d_sprobs);
     }
     delete b;
 }
@@ -310,14 +321,47 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     if (b->grid < 1)
         return fail(KPM_ECUDA);
     std::vector<BatchProblem> probs(count);
+    std::vector<StagedProblem> sprobs(count);
     std::vector<int64_t> prefix;  // per class: tile prefix over its problems (count_c + 1)
     double bytes = 0.0;
-    for (int i = 0; i < count; i++) {
-        if (i == 0 || shape_of(order[i]) != shape_of(order[i - 1])) {
+    for (int i = 0; i < count; i++)
+        if (i == 0 || shape_of(order[i]) != shape_of(order[i - 1]))
             b->class_first.push_back(i);
+    b->class_first.push_back(count);
+    // Complex float classes run the staged kernel when every problem has
+    // gather lists with one chunk height and the stages fit.
+    b->staged.assign(b->class_first.size() - 1, StagedClass());
+    for (size_t cl = 0; cl + 1 < b->class_first.size() && !fp64; cl++) {
+        const int first = b->class_first[cl], last = b->class_first[cl + 1];
+        const int RB = R[order[first]];
+        StagedClass &sc = b->staged[cl];
+        sc.T = RB / 4;
+        bool ok = RB >= 8 && staged_shape_supported(sc.T, sc.E);
+        int u_max = 0, l_max = 0;
+        for (int i = first; i < last && ok; i++) {
+            const kpm_ctx *c = ctx[order[i]];
+            ok = c->gather_ok && c->C == ctx[order[first]]->C;
+            u_max = std::max(u_max, c->u_max);
+            l_max = std::max(l_max, c->l_max);
+        }
+        ok = ok && staged_layout(ctx[order[first]]->C, sc.T, RB, u_max, l_max, 2, last - first,
+                                 ctx[0]->max_smem, sc.L);
+        if (ok) {
+            const int bps = staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem);
+            sc.grid = bps * ctx[0]->n_sm;
+            ok = bps > 0;
+        }
+        sc.on = ok;
+    }
+    for (int i = 0; i < count; i++) {
+        int cl = 0;
+        while (b->class_first[cl + 1] <= i)
+            cl++;
+        if (i == b->class_first[cl]) {
             b->class_prefix.push_back((int)prefix.size());
             prefix.push_back(0);
         }
+        const StagedClass &sc = b->staged[cl];
         const int p = order[i];
         kpm_ctx *c = ctx[p];
         int rc = ensure_vectors(c, R[p]);
@@ -329,9 +373,9 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         const int T = fp64 ? batch_team<double>(shape) : batch_team<float>(shape);
         const int rows_per_group = (kBatchThreads / 32) * (32 / T);
         const int tg = kBatchTileGroups[fp64 ? 0 : 1];
-        const int64_t tile_rows = (int64_t)rows_per_group * tg;
+        const int64_t tile_rows = sc.on ? c->C : (int64_t)rows_per_group * tg;
         const int64_t n_tiles = (c->n_pad + tile_rows - 1) / tile_rows;
-        const int64_t slots = std::min<int64_t>(b->grid, n_tiles);
+        const int64_t slots = std::min<int64_t>(sc.on ? sc.grid : b->grid, n_tiles);
         rc = ensure_partial(c, 3 * (int64_t)R[p] * slots);
         if (rc)
             return fail(rc);
@@ -357,12 +401,27 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         bp.shape = shape;
         bp.tile_groups = tg;
         bp.M = M[p];
+        if (sc.on) {
+            StagedProblem &sp = sprobs[i];
+            sp.rec = c->d_rec;
+            sp.ovf = c->d_ovf;
+            sp.lidx = c->d_lidx;
+            sp.val = c->d_val;
+            sp.buf[0] = c->d_V;
+            sp.buf[1] = c->d_W;
+            sp.partial = c->d_partial;  // [3*RB][slots]
+            sp.tile0 = prefix.back();
+            sp.n_tiles = n_tiles;
+            sp.ps = 1;
+            sp.qs = slots;
+            sp.ld = bp.ld;
+            sp.col0 = 0;
+        }
         prefix.push_back(prefix.back() + n_tiles);
         const double mat = (double)c->nnz * (sd + 4);
         bytes += mat + 2.0 * R[p] * sd * c->n + (M[p] / 2 - 1) * (mat + 3.0 * R[p] * sd * c->n);
         b->info.sweeps += M[p] / 2;
     }
-    b->class_first.push_back(count);
     b->steps = 0;
     for (int i = 0; i < count; i++)
         b->steps = std::max(b->steps, M[order[i]] / 2);
@@ -385,6 +444,17 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int64_t) * prefix.size(),
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(KPM_ECUDA);
+    bool any_staged = false;
+    for (const StagedClass &sc : b->staged)
+        any_staged = any_staged || sc.on;
+    if (any_staged) {
+        b->d_sprobs = (StagedProblem *)dev_alloc(ctx[0], sizeof(StagedProblem) * count);
+        if (!b->d_sprobs)
+            return fail(KPM_ENOMEM);
+        if (cudaMemcpy(b->d_sprobs, sprobs.data(), sizeof(StagedProblem) * count,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(KPM_ECUDA);
+    }
 
     // ---- capture the schedule
     if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess)
@@ -408,7 +478,28 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 continue;
             const BatchProblem *cp = b->d_probs + b->class_first[cl];
             const int64_t *cpre = b->d_prefix + b->class_prefix[cl];
-            if (fp64)
+            const StagedClass &sc = b->staged[cl];
+            if (sc.on) {
+                // the running problems are a prefix of the class: a table of na
+                StagedParams q{};
+                q.probs = b->d_sprobs + b->class_first[cl];
+                q.n_probs = na;
+                q.parity = s & 1;
+                q.C = ctx[order[b->class_first[cl]]]->C;
+                q.stages = sc.L.stages;
+                q.with_imag = 0;
+                q.init = s == 0 ? 1 : 0;
+                q.err = ctx[0]->d_err;
+                q.bar_bytes = sc.L.bar_bytes;
+                q.stage_bytes = sc.L.stage_bytes;
+                q.off_w = sc.L.off_w;
+                q.off_val = sc.L.off_val;
+                q.off_lidx = sc.L.off_lidx;
+                q.off_meta = sc.L.off_meta;
+                rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
+                if (rc != KPM_OK)
+                    break;
+            } else if (fp64)
                 batch_sweep_kernel<double><<<b->grid, kBatchThreads, smem, b->capture>>>(
                     cp, cpre, na, s);
             else
@@ -442,6 +533,9 @@ int kpm_batch_launch(kpm_batch *b, void *stream)
     if (!b || !b->exec)
         return KPM_EINVAL;
     DeviceGuard guard(b->device);
+    // the staged launches record bounded-wait expiries in the first
+    // context's error word; kpm_batch_eta reports them
+    KPM_CUDA(cudaMemsetAsync(b->ctx[0]->d_err, 0, sizeof(int), (cudaStream_t)stream));
     return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
 }
 
@@ -453,7 +547,10 @@ int kpm_batch_eta(kpm_batch *b, int32_t p, double *eta, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = (int64_t)b->M[p] * b->R[p];
     KPM_CUDA(cudaMemcpyAsync(eta, b->ctx[p]->d_eta, n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    return cuda_status(cudaStreamSynchronize(st));
+    int word = 0;
+    KPM_CUDA(cudaMemcpyAsync(&word, b->ctx[0]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    return word ? KPM_ETIMEOUT : KPM_OK;
 }
 
 int kpm_batch_get_info(const kpm_batch *b, kpm_batch_info *out)

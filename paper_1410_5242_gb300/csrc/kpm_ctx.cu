@@ -180,7 +180,7 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
         // the second block)
         for (int ns = 2; ns >= 2; ns--) {
             StagedLayout L;
-            if (staged_layout(c->C, s.T, RB, c->u_max, c->l_max, ns, c->max_smem, L)) {
+            if (staged_layout(c->C, s.T, RB, c->u_max, c->l_max, ns, 1, c->max_smem, L)) {
                 s.stages = ns;
                 break;
             }
@@ -196,7 +196,7 @@ bool shape_layout(const kpm_ctx *c, const LaunchShape &s, StagedLayout &L)
     if (s.stages < 1 || c->precision != KPM_PREC_FP32 || !c->gather_ok ||
         !staged_shape_supported(s.T, s.E))
         return false;
-    return staged_layout(c->C, s.T, s.T * s.E, c->u_max, c->l_max, s.stages, c->max_smem, L);
+    return staged_layout(c->C, s.T, s.T * s.E, c->u_max, c->l_max, s.stages, 1, c->max_smem, L);
 }
 
 int resolve_grid(kpm_ctx *c, LaunchShape &s)
@@ -311,27 +311,34 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         if (!shape_layout(c, cb.shape, L))
             return KPM_EUNSUPPORTED;
         StagedParams q;
-        q.rec = c->d_rec;
-        q.ovf = c->d_ovf;
-        q.lidx = c->d_lidx;
-        q.val = c->d_val;
-        q.V = p.V;
-        q.W = p.W;
-        q.partial = p.partial;
-        q.err = c->d_err;
-        q.n_chunks = c->n_chunks;
+        q.one.rec = c->d_rec;
+        q.one.ovf = c->d_ovf;
+        q.one.lidx = c->d_lidx;
+        q.one.val = c->d_val;
+        q.one.buf[0] = const_cast<void *>(p.V);
+        q.one.buf[1] = p.W;
+        q.one.partial = p.partial;
+        q.one.tile0 = 0;
+        q.one.n_tiles = c->n_chunks;
+        q.one.ps = 3 * cb.RB;  // [grid][3][RB]
+        q.one.qs = 1;
+        q.one.ld = p.ld;
+        q.one.col0 = p.col0;
+        q.probs = nullptr;
+        q.n_probs = 1;
+        q.parity = 0;
         q.C = c->C;
-        q.ld = p.ld;
-        q.col0 = p.col0;
         q.stages = L.stages;
         q.with_imag = p.with_imag;
+        q.init = init ? 1 : 0;
+        q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
         q.stage_bytes = L.stage_bytes;
         q.off_w = L.off_w;
         q.off_val = L.off_val;
         q.off_lidx = L.off_lidx;
         q.off_meta = L.off_meta;
-        return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, init, st);
+        return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
     }
     if (c->precision == KPM_PREC_FP64)
         return launch_sweep_fp64(p, cb.shape, cb.grid, init, st);

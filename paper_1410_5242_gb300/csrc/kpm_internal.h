@@ -52,17 +52,36 @@ struct SweepParams {
 #define KPM_REC_WORDS 32
 #define KPM_REC_INLINE_RUNS 29
 
+// One problem of a staged launch: its arrays, where its chunks sit in the
+// launch's global tile sequence, and where its eta partials go (slot s,
+// entry t = q*RB + r at partial[s*ps + t*qs]; slot = the first chunk of the
+// problem a block handled, so slots < min(grid, n_tiles)).
+struct StagedProblem {
+    const int2 *rec;       // [n_tiles][KPM_REC_WORDS]
+    const int2 *ovf;       // runs beyond the inline ones
+    const uint16_t *lidx;  // [n_stored] local positions
+    const void *val;       // [n_stored] complex float
+    void *buf[2];          // vector blocks: V = buf[parity], W = buf[parity ^ 1]
+    double *partial;
+    int64_t tile0, n_tiles;
+    int64_t ps, qs;
+    int32_t ld, col0;
+};
+
+static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte words");
+
+// Arguments of one staged sweep (aug_spmmv_staged.cu) over a table of
+// problems (probs, n_probs entries, in device memory) or the single problem
+// `one` (probs = NULL, n_probs = 1), and the shared-memory layout of one
+// stage: V rows [u_max][RB] at 0, old W rows [C][RB] at off_w, values
+// [l_max*C] at off_val, local indices at off_lidx, the chunk's length,
+// problem and chunk number at off_meta.  Stages start at bar_bytes.
 struct StagedParams {
-    const int2 *rec;   // [n_chunks][KPM_REC_WORDS]
-    const int2 *ovf;   // runs beyond the inline ones
-    const uint16_t *lidx;
-    const void *val;
-    const void *V;
-    void *W;
-    double *partial;  // [grid][3][RB]
-    int *err;         // device error word (KPM_DEVERR_*)
-    int64_t n_chunks;
-    int32_t C, ld, col0, stages, with_imag;
+    StagedProblem one;
+    const StagedProblem *probs;
+    int32_t n_probs, parity;
+    int32_t C, stages, with_imag, init;
+    int *err;  // device error word (KPM_DEVERR_*)
     uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx, off_meta;
 };
 
@@ -73,11 +92,10 @@ struct StagedLayout {
     int stages;
     size_t smem;
 };
-bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, size_t max_smem,
-                   StagedLayout &out);
+bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n_probs,
+                   size_t max_smem, StagedLayout &out);
 bool staged_shape_supported(int T, int E);
-int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, bool init,
-                        void *stream);
+int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream);
 int staged_max_blocks_per_sm(int T, int E, int C, size_t smem);
 
 // stages = 0: the register-path kernel of aug_spmmv.cuh with `threads` per

@@ -128,3 +128,38 @@ def test_ensemble_recipe_sampled_against_oracle(kpm, orc):
         dmu = np.abs(kpm.eta_to_mu(eta[:2]) - orc.eta_to_mu(ref)).max()
         assert dmu <= 1e-5, dmu
         ctx.close()
+
+
+def test_staged_batch_classes_with_several_problems(kpm, orc):
+    """Complex float classes of several problems each (R = 16 and 32) run the
+    staged kernel over the concatenated chunks of the running problems; the
+    eta flush at every problem boundary must give each problem its own
+    moments.  Sizes include a lattice with fewer chunks than blocks and a
+    ragged matrix whose rows are not a multiple of the chunk height."""
+    probs = [
+        (ham.ti_hamiltonian(8, 8, 8, gamma=0.5, seed=1), 80, 16, 21),
+        (ham.ti_hamiltonian(3, 3, 3, gamma=1.0, seed=2), 40, 16, 22),
+        (ham.random_hermitian(517, 9, seed=3, empty_rows=0.05), 64, 16, 23),
+        (ham.ti_hamiltonian(12, 10, 9, gamma=2.5, seed=4), 120, 32, 24),
+        (ham.ti_hamiltonian(5, 6, 4, gamma=0.1, seed=5), 24, 32, 25),
+        (ham.ti_hamiltonian(16, 16, 8, gamma=1.5, seed=6), 64, 32, 26),
+    ]
+    ctxs = []
+    for h, M, R, seed in probs:
+        a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+        ctxs.append((kpm.create(h, a, b, precision=kpm.PREC_FP32), h, a, b))
+    for c, *_ in ctxs:
+        assert c.get_launch(16)["stages"] >= 1 and c.get_launch(32)["stages"] >= 1
+    etas = kpm.moments_batch([c for c, *_ in ctxs], [p[1] for p in probs], [p[2] for p in probs],
+                             [p[3] for p in probs])
+    etas2 = kpm.moments_batch([c for c, *_ in ctxs], [p[1] for p in probs],
+                              [p[2] for p in probs], [p[3] for p in probs])
+    for (ctx, h, a, b), (_, M, R, seed), eta, eta2 in zip(ctxs, probs, etas, etas2):
+        assert np.array_equal(eta, eta2)
+        single = ctx.moments(M, R, seed)
+        cols = [0, R - 1]
+        ref, _ = orc.moments(h, a, b, M, seed, cols)
+        assert np.abs(kpm.eta_to_mu(eta) - kpm.eta_to_mu(single)).max() <= 1e-6
+        assert np.abs(kpm.eta_to_mu(eta[cols]) - orc.eta_to_mu(ref)).max() <= 1e-5
+    for c, *_ in ctxs:
+        c.close()
