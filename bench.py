@@ -46,20 +46,24 @@ FALLBACK_HBM_GBS = 6800.0
 # SM x 152 SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s (nominal 1.25).
 FP64_PEAK_TFLOPS = 1.25
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "aug_spmmv_traffic.txt")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1410_5242_gb300", "csrc", f)
-                  for f in ("aug_spmmv.cuh", "aug_spmmv_fp64.cu", "aug_spmmv_fp32.cu")]
+# the sources of each form's sweep kernel (complex double: register path;
+# complex float: the staged kernel)
+KERNEL_SOURCES = {
+    "fp64": ("aug_spmmv.cuh", "aug_spmmv_fp64.cu"),
+    "fp32": ("aug_spmmv.cuh", "aug_spmmv_staged.cu", "kpm_internal.h"),
+}
 
 
-def kernel_hash():
+def kernel_hash(form):
     h = hashlib.sha1()
-    for p in KERNEL_SOURCES:
-        h.update(open(p, "rb").read())
+    for f in KERNEL_SOURCES[form]:
+        h.update(open(os.path.join(ROOT, "paper_1410_5242_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
 
-def measured_traffic(key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def measured_traffic(form):
+    """DRAM bytes per launch of the form's sweep kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     vals = {}
@@ -67,9 +71,9 @@ def measured_traffic(key):
         parts = line.split()
         if len(parts) >= 2 and not line.startswith("#"):
             vals[parts[0]] = parts[1]
-    if vals.get("kernel_hash") != kernel_hash():
+    if vals.get(form + "_kernel_hash") != kernel_hash(form):
         return None
-    v = vals.get(key)
+    v = vals.get(form + "_dram_bytes_per_launch")
     return float(v) if v is not None else None
 
 
@@ -260,7 +264,7 @@ def bench_ours(args, world, rank, local):
     k_flops = model.fused_fp64_flops(nnz, n, R)
     achieved_tf = k_flops / t_k / 1e12
     k_gbs = k_bytes / t_k / 1e9
-    traffic = measured_traffic("fp64_dram_bytes_per_launch")
+    traffic = measured_traffic("fp64")
     launch_shape = ctx.get_launch(R)
 
     # ---------------- FP32-storage form on the same lattice shape
@@ -283,7 +287,8 @@ def bench_ours(args, world, rank, local):
     t_k32 = kernel_only(ctx32, R4, args.kernel_launches, stream)
     k32_bytes = model.sweep_bytes(h4["n"], nnz4, R4, 8)
     k32_gbs = k32_bytes / t_k32 / 1e9
-    traffic32 = measured_traffic("fp32_dram_bytes_per_launch")
+    traffic32 = measured_traffic("fp32")
+    launch32 = ctx32.get_launch(R4)
 
     fp32_err = None
     if rank == 0 and not args.skip_accuracy:
@@ -374,7 +379,14 @@ def bench_ours(args, world, rank, local):
             "roofline": {"bound": "hbm", "achieved": round(k32_gbs, 1), "peak": hbm_peak,
                          "unit": "GB/s", "frac": round(k32_gbs / hbm_peak, 4),
                          "traffic": traffic32, "avg_launch_ms": round(t_k32 * 1e3, 4),
-                         "algorithmic_bytes": k32_bytes},
+                         "algorithmic_bytes": k32_bytes,
+                         "kernel": ("aug_spmmv_staged_kernel<%d,%d>, %d stages"
+                                    % (launch32["lanes_per_row"], launch32["cols_per_lane"],
+                                       launch32["stages"]) if launch32["stages"] else
+                                    "aug_spmmv_kernel<float,%d,%d>"
+                                    % (launch32["lanes_per_row"], launch32["cols_per_lane"])),
+                         "launch": launch32,
+                         "peak_source": "HBM %s %.0f GB/s" % (peak_src, hbm_peak)},
             "accuracy": fp32_err,
         },
         "r_sweep": r_sweep,

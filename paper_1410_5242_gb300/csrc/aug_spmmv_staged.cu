@@ -128,7 +128,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // tiles are fetched with cp.async (8 bytes per lane) into shared memory, so
 // the per-tile metadata never waits on a memory round trip.
 constexpr int kMetaDepth = 8;
-constexpr uint32_t kRingOffset = 256;  // after the barriers and the abort flag
+constexpr uint32_t kMetaOffset = 256;  // per stage: chunk length, problem, chunk number
+constexpr uint32_t kRingOffset = kMetaOffset + 8 * 16;
 constexpr uint32_t kRedOffset = kRingOffset + kMetaDepth * KPM_REC_WORDS * 8;
 constexpr uint32_t kTableOffset = kRedOffset + 3 * 64 * 8;  // eta sum of up to 64 columns
 
@@ -206,19 +207,31 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
     const int64_t G = gridDim.x;
     const int par = p.parity;
 
-    // the record stream runs kMetaDepth tiles ahead of the issue stream
-    int pj = 0;
+    // the record stream runs kMetaDepth tiles ahead of the issue stream; the
+    // fields of the problem each stream is in are kept in registers
+    int pj = -1;
+    int64_t j_end = -1, j_tile0 = 0;
+    const int2 *j_rec = nullptr;
     auto fetch_record = [&](int64_t t, uint32_t slot) {
         if (t < total) {
-            pj = advance_problem(tab, p.n_probs, pj, t);
+            if (t >= j_end) {
+                pj = advance_problem(tab, p.n_probs, pj < 0 ? 0 : pj, t);
+                j_rec = tab[pj].rec;
+                j_tile0 = tab[pj].tile0;
+                j_end = j_tile0 + tab[pj].n_tiles;
+            }
             cp_async8(ring0 + (slot * KPM_REC_WORDS + lane) * 8,
-                      tab[pj].rec + (t - tab[pj].tile0) * KPM_REC_WORDS + lane);
+                      j_rec + (t - j_tile0) * KPM_REC_WORDS + lane);
         }
         cp_async_commit();
     };
     for (int i = 0; i < kMetaDepth; i++)
         fetch_record(blockIdx.x + i * G, (uint32_t)i);
-    int pi = 0;
+    int pi = -1;
+    int64_t i_end = -1, i_tile0 = 0;
+    const char *Vb = nullptr, *Wb = nullptr, *valb = nullptr, *lidxb = nullptr;
+    const int2 *ovfp = nullptr;
+    int ld = 0, col0 = 0;
     int64_t k = 0;
     for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         const int slot = (int)(k % kMetaDepth);
@@ -227,18 +240,28 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const int2 word = ring[slot * KPM_REC_WORDS + lane];
         __syncwarp();
         fetch_record(gt + kMetaDepth * G, (uint32_t)slot);
-        pi = advance_problem(tab, p.n_probs, pi, gt);
-        const StagedProblem &P = tab[pi];
-        const int64_t lt = gt - P.tile0;  // chunk within the problem
-        const char *Vb = static_cast<const char *>(P.buf[par]);
-        const char *Wb = static_cast<const char *>(P.buf[par ^ 1]);
+        if (gt >= i_end) {
+            pi = advance_problem(tab, p.n_probs, pi < 0 ? 0 : pi, gt);
+            const StagedProblem &P = tab[pi];
+            i_tile0 = P.tile0;
+            i_end = i_tile0 + P.n_tiles;
+            Vb = static_cast<const char *>(P.buf[par]);
+            Wb = static_cast<const char *>(P.buf[par ^ 1]);
+            valb = static_cast<const char *>(P.val);
+            lidxb = reinterpret_cast<const char *>(P.lidx);
+            ovfp = P.ovf;
+            ld = P.ld;
+            col0 = P.col0;
+        }
+        const int64_t lt = gt - i_tile0;  // chunk within the problem
 
-        const int64_t e0 = (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, 0) |
-                           ((int64_t)__shfl_sync(0xffffffffu, word.y, 0) << 32);
+        auto word64 = [&](int w) {
+            return (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, w) |
+                   ((int64_t)__shfl_sync(0xffffffffu, word.y, w) << 32);
+        };
+        const int64_t e0 = word64(0), ovf0 = word64(2);
         const int len = __shfl_sync(0xffffffffu, word.x, 1);
         const int nruns = __shfl_sync(0xffffffffu, word.y, 1);
-        const int64_t ovf0 = (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, 2) |
-                             ((int64_t)__shfl_sync(0xffffffffu, word.y, 2) << 32);
         const int n_inline = min(nruns, KPM_REC_INLINE_RUNS);
         const bool has_run = lane >= 3 && lane - 3 < n_inline;
         const int count = has_run ? word.y : 0;
@@ -246,7 +269,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         uint32_t total_rows = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
         for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
             const int2 r = g + lane < nruns
-                               ? __ldg(P.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                               ? __ldg(ovfp + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
                                : make_int2(0, 0);
             total_rows += (uint32_t)__shfl_sync(0xffffffffu, warp_incl_scan(r.y, lane), 31);
         }
@@ -261,40 +284,38 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                 break;
         }
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
-        const uint32_t mat_entries = (uint32_t)len * (uint32_t)p.C;
-        const uint32_t bytes = total_rows * row_bytes + mat_entries * 10u +
+        const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * 8u;
+        const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
+        const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes +
                                (p.init ? 0u : (uint32_t)p.C * row_bytes);
         if (lane == 0) {
-            volatile int *meta = reinterpret_cast<volatile int *>(
-                smem + p.bar_bytes + (size_t)s * p.stage_bytes + p.off_meta);
+            volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
             meta[1] = pi;
             meta[2] = (int)lt;
             mbar_arrive_expect_tx(full, bytes);
         }
         __syncwarp();
-        if (mat_entries > 0) {
+        if (len > 0) {
             if (lane == 0)
-                bulk_g2s(st + p.off_val, static_cast<const char *>(P.val) + e0 * 8,
-                         mat_entries * 8u, full);
+                bulk_g2s(st + p.off_val, valb + e0 * 8, val_bytes, full);
             if (lane == 1)
-                bulk_g2s(st + p.off_lidx, reinterpret_cast<const char *>(P.lidx) + e0 * 2,
-                         mat_entries * 2u, full);
+                bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, lidx_bytes, full);
         }
         if (!p.init && lane == 2)
-            copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, P.ld, P.col0, row_bytes, full);
+            copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, ld, col0, row_bytes, full);
         if (has_run && count > 0)
-            copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, P.ld, P.col0,
+            copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, ld, col0,
                       row_bytes, full);
         uint32_t base = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
         for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
             const int2 r = g + lane < nruns
-                               ? __ldg(P.ovf + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
+                               ? __ldg(ovfp + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
                                : make_int2(0, 0);
             const int ri = warp_incl_scan(r.y, lane);
             if (r.y > 0)
-                copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, P.ld,
-                          P.col0, row_bytes, full);
+                copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, ld, col0,
+                          row_bytes, full);
             base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
         }
     }
@@ -360,9 +381,9 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
     constexpr int P = 32 / T;
     constexpr int RB = T * E;
     constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
-    // [full[NS], empty[NS] | abort flag at 128 | record ring at 256 | eta
-    //  sum at kRedOffset | problem table at kTableOffset | stages from
-    //  bar_bytes on]
+    // [full[NS], empty[NS] | abort flag at 128 | stage metadata at
+    //  kMetaOffset | record ring at kRingOffset | eta sum at kRedOffset |
+    //  problem table at kTableOffset | stages from bar_bytes on]
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -406,6 +427,8 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
         EtaAcc<float, IMAG> acc[E];
         int cur = -1;        // problem whose eta terms acc holds
         int64_t slot = 0;    // its partial slot: this block's first chunk of it
+        float *Wp = nullptr;  // its W block, row length and first column
+        int ldw = 0, col0 = 0;
         int64_t k = 0;
         for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, k++) {
             const int s = (int)(k % NS);
@@ -414,7 +437,8 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
             if (!__all_sync(0xffffffffu, ok))
                 break;
             const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
-            const volatile int *meta = reinterpret_cast<const volatile int *>(st + p.off_meta);
+            const volatile int *meta =
+                reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
             const int len = meta[0], pi = meta[1];
             const int64_t lt = meta[2];
             if (pi != cur) {
@@ -422,8 +446,10 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
                     flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
                 cur = pi;
                 slot = lt;
+                Wp = static_cast<float *>(tab[pi].buf[p.parity ^ 1]);
+                ldw = tab[pi].ld;
+                col0 = tab[pi].col0;
             }
-            const StagedProblem &Pb = tab[pi];
             const float *vb = reinterpret_cast<const float *>(st);
             const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
             const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
@@ -472,8 +498,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
                     acc_s[q] *= 0.5f;
             }
             const int64_t row = lt * (int64_t)C + rit;
-            float *W = static_cast<float *>(Pb.buf[p.parity ^ 1]);
-            store_owned<float, T, E>(W, row * Pb.ld + Pb.col0 + tl * EV, acc_s);
+            store_owned<float, T, E>(Wp, row * ldw + col0 + tl * EV, acc_s);
             // the row's own V entries: local position rit of the list
             const float *ov = vb + (size_t)rit * 2 * RB;
 #pragma unroll
@@ -532,8 +557,6 @@ bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n
     off = up(off + (uint64_t)C * l_max * 8, 128);
     o.off_lidx = (uint32_t)off;
     off = up(off + (uint64_t)C * l_max * 2, 128);
-    o.off_meta = (uint32_t)off;
-    off = up(off + 16, 128);
     o.stage_bytes = (uint32_t)off;
     o.bar_bytes = (uint32_t)up(kTableOffset + (uint64_t)n_probs * sizeof(StagedProblem), 128);
     o.stages = stages;

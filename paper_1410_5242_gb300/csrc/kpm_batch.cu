@@ -495,7 +495,6 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.off_w = sc.L.off_w;
                 q.off_val = sc.L.off_val;
                 q.off_lidx = sc.L.off_lidx;
-                q.off_meta = sc.L.off_meta;
                 rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
                 if (rc != KPM_OK)
                     break;

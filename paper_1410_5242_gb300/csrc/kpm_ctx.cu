@@ -337,7 +337,6 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.off_w = L.off_w;
         q.off_val = L.off_val;
         q.off_lidx = L.off_lidx;
-        q.off_meta = L.off_meta;
         return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
     }
     if (c->precision == KPM_PREC_FP64)
@@ -619,8 +618,9 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sell.n_stored);
             c->d_rec = (int2 *)dev_alloc(c, sizeof(int2) * rec.size());
             c->d_ovf = (int2 *)dev_alloc(c, sizeof(int2) * (ovf.empty() ? 1 : ovf.size()));
+            const bool alloc_ok = c->d_lidx && c->d_rec && c->d_ovf;
             const bool ok =
-                c->d_lidx && c->d_rec && c->d_ovf &&
+                alloc_ok &&
                 cudaMemcpy(c->d_lidx, g.lidx, sizeof(uint16_t) * sell.n_stored,
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 cudaMemcpy(c->d_rec, rec.data(), sizeof(int2) * rec.size(),
@@ -631,7 +631,7 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             c->l_max = g.l_max;
             kpm_gather_release(&g);
             if (!ok)
-                return fail(c->d_lidx && c->d_rec && c->d_ovf ? KPM_ECUDA : KPM_ENOMEM);
+                return fail(alloc_ok ? KPM_ECUDA : KPM_ENOMEM);
             c->gather_ok = true;
         }
     }

@@ -39,16 +39,10 @@ struct SweepParams {
 // Device-side error codes a kernel records in the context's error word.
 #define KPM_DEVERR_TIMEOUT 1
 
-// Arguments of one staged sweep (aug_spmmv_staged.cu): the SELL arrays
-// plus the gather lists of kpm_gather_build, and the shared-memory layout
-// of one stage: V rows [u_max][RB] at 0, old W rows [C][RB] at off_w,
-// values [l_max*C] at off_val, local indices at off_lidx, the chunk's
-// length at off_meta.  Stages start at bar_bytes (barriers and the abort
-// flag before them).
 // Per-chunk producer record of the staged kernel: 32 int2 (256 bytes),
-// [0] = first stored entry (int64 as lo, hi), [1] = (chunk_len, run count),
-// [2] = index of run kRecInlineRuns in the overflow array (int64 as lo, hi),
-// [3 + q] = run q (first row, row count) for q < kRecInlineRuns.
+// [0] = first stored entry of the chunk (int64 as lo, hi), [1] = (chunk_len,
+// run count), [2] = index of run KPM_REC_INLINE_RUNS in the overflow array
+// (int64), [3 + q] = run q (first row, row count) for q < KPM_REC_INLINE_RUNS.
 #define KPM_REC_WORDS 32
 #define KPM_REC_INLINE_RUNS 29
 
@@ -59,8 +53,8 @@ struct SweepParams {
 struct StagedProblem {
     const int2 *rec;       // [n_tiles][KPM_REC_WORDS]
     const int2 *ovf;       // runs beyond the inline ones
-    const uint16_t *lidx;  // [n_stored] local positions
-    const void *val;       // [n_stored] complex float
+    const uint16_t *lidx;  // [n_stored] local positions (SELL order)
+    const void *val;       // [n_stored] complex float values (SELL order)
     void *buf[2];          // vector blocks: V = buf[parity], W = buf[parity ^ 1]
     double *partial;
     int64_t tile0, n_tiles;
@@ -74,21 +68,23 @@ static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte
 // problems (probs, n_probs entries, in device memory) or the single problem
 // `one` (probs = NULL, n_probs = 1), and the shared-memory layout of one
 // stage: V rows [u_max][RB] at 0, old W rows [C][RB] at off_w, values
-// [l_max*C] at off_val, local indices at off_lidx, the chunk's length,
-// problem and chunk number at off_meta.  Stages start at bar_bytes.
+// [l_max][C] at off_val, local indices [l_max][C] at off_lidx (SELL order,
+// column-major in the chunk).  Stages start at bar_bytes; the barriers, each
+// stage's chunk length, problem and chunk number, the record ring, the eta
+// sum and the problem table sit before them.
 struct StagedParams {
     StagedProblem one;
     const StagedProblem *probs;
     int32_t n_probs, parity;
     int32_t C, stages, with_imag, init;
     int *err;  // device error word (KPM_DEVERR_*)
-    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx, off_meta;
+    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx;
 };
 
 // The shared-memory layout of a staged launch; false if fewer than
 // min_stages stages fit in max_smem bytes.
 struct StagedLayout {
-    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx, off_meta;
+    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx;
     int stages;
     size_t smem;
 };
@@ -186,8 +182,8 @@ struct kpm_ctx {
 
     // gather lists of the staged kernel (complex float contexts)
     bool gather_ok = false;
-    uint16_t *d_lidx = nullptr;
-    int2 *d_rec = nullptr;  // [n_chunks][KPM_REC_WORDS]
+    uint16_t *d_lidx = nullptr;  // [n_stored] local positions (SELL order)
+    int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;
     int32_t u_max = 0, l_max = 0;
     int *d_err = nullptr;  // device error word, KPM_DEVERR_*
