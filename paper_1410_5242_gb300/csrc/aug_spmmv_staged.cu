@@ -24,10 +24,10 @@
 // tile sequence moves on to the next problem.  A single problem is a table
 // of one.
 //
-// Arithmetic per row and column is that of aug_spmmv.cuh (same lane/column
-// ownership, same entry order, same eta accumulation and block sum): W
-// equals the register path's bit for bit; eta differs from it only in the
-// order in which rows are summed (and is itself reproducible run to run).
+// Lane/column ownership and the eta accumulation are those of aug_spmmv.cuh;
+// the products are accumulated with paired FMAs (real and imaginary parts of
+// h times a column in two packed sums), so W agrees with the register path
+// to single-precision rounding, and eta is reproducible run to run.
 //
 // Every wait is bounded (about two seconds of SM clock): on expiry the
 // thread records KPM_DEVERR_TIMEOUT in *err, raises the block's abort flag
@@ -163,6 +163,27 @@ __device__ __forceinline__ void copy_rows(uint32_t dst, const char *block, int64
         for (int i = 0; i < nrows; i++)
             bulk_g2s(dst + (uint32_t)i * row_bytes, src + i * ld_bytes, row_bytes, bar);
     }
+}
+
+// Two floats in one 64-bit register pair, and the paired FMA of sm_100+
+// (d.lo = a.lo * b.lo + c.lo, d.hi = a.hi * b.hi + c.hi, each rounded once).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi)
+{
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
 // Inclusive prefix sum over the warp's lanes.
@@ -369,12 +390,18 @@ __device__ __forceinline__ void flush_eta(EtaAcc<float, IMAG> (&acc)[E], double 
         acc[k] = EtaAcc<float, IMAG>();
 }
 
-// Up to 32 + C*T = 544 threads (C = 32, T = 16); the register budget that
-// leaves (112 per thread) holds a consumer's accumulators without spills.
+// Up to 32 + C*T = 544 threads (C = 32, T = 16).  Four columns per lane
+// (E = 4) need up to 96 registers, one block of that size per SM; two
+// columns per lane fit 56 registers, two blocks of 544 threads per SM.
 #define KPM_STAGED_MAX_THREADS 576
 
+template <int E>
+struct StagedMinBlocks {
+    static constexpr int value = E >= 4 ? 1 : 2;
+};
+
 template <int T, int E, bool IMAG>
-__global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
+__global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::value)
     aug_spmmv_staged_kernel(const StagedParams p)
 {
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
@@ -454,43 +481,57 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
             const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
             const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
 
-            float acc_s[2 * E];
+            // W row <- H' V - W with two packed (re, im) accumulators per
+            // column: a = -W + sum_j Re(h_j) v_j, b = sum_j Im(h_j) v_j, so
+            // each entry costs two paired FMAs per column; at the end
+            // W = (a.re - b.im, a.im + b.re)
+            uint64_t pa[E], pb[E];
             if (p.init) {
 #pragma unroll
-                for (int q = 0; q < 2 * E; q++)
-                    acc_s[q] = 0.f;
+                for (int c = 0; c < E; c++)
+                    pa[c] = pb[c] = 0ull;
             } else {
                 const float *wr = reinterpret_cast<const float *>(st + p.off_w) + rit * 2 * RB;
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
                     const float4 w4 =
                         *reinterpret_cast<const float4 *>(wr + 2 * (q * T * EV + tl * EV));
-                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                    for (int i = 0; i < 2 * EV; i++)
-                        acc_s[q * 2 * EV + i] = -wv[i];
+                    pa[q * EV] = pack2(-w4.x, -w4.y);
+                    pb[q * EV] = 0ull;
+                    if constexpr (EV == 2) {
+                        pa[q * EV + 1] = pack2(-w4.z, -w4.w);
+                        pb[q * EV + 1] = 0ull;
+                    }
                 }
             }
 #pragma unroll 4
             for (int j = 0; j < len; j++) {
                 const int u = lid[j * C + rit];
                 const float2 h = vals[j * C + rit];
+                const uint64_t hx2 = pack2(h.x, h.x), hy2 = pack2(h.y, h.y);
                 const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
                     const float4 v4 =
                         *reinterpret_cast<const float4 *>(vr + 2 * (q * T * EV + tl * EV));
-                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                    for (int e = 0; e < EV; e++) {
-                        float &sr = acc_s[q * 2 * EV + 2 * e];
-                        float &si = acc_s[q * 2 * EV + 2 * e + 1];
-                        sr = fmaf(h.x, v[2 * e], sr);
-                        sr = fmaf(-h.y, v[2 * e + 1], sr);
-                        si = fmaf(h.x, v[2 * e + 1], si);
-                        si = fmaf(h.y, v[2 * e], si);
+                    const uint64_t v0 = pack2(v4.x, v4.y);
+                    pa[q * EV] = ffma2(hx2, v0, pa[q * EV]);
+                    pb[q * EV] = ffma2(hy2, v0, pb[q * EV]);
+                    if constexpr (EV == 2) {
+                        const uint64_t v1 = pack2(v4.z, v4.w);
+                        pa[q * EV + 1] = ffma2(hx2, v1, pa[q * EV + 1]);
+                        pb[q * EV + 1] = ffma2(hy2, v1, pb[q * EV + 1]);
                     }
                 }
+            }
+            float acc_s[2 * E];
+#pragma unroll
+            for (int c = 0; c < E; c++) {
+                float ar, ai, br, bi;
+                unpack2(pa[c], ar, ai);
+                unpack2(pb[c], br, bi);
+                acc_s[2 * c] = ar - bi;
+                acc_s[2 * c + 1] = ai + br;
             }
             if (p.init) {
 #pragma unroll
@@ -529,8 +570,9 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, 1)
 }  // namespace
 
 // (T, E) shapes of the staged kernel: 4 complex columns per lane as two
-// 16-byte pieces, widths 8..64.
-#define KPM_STAGED_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(16, 4)
+// 16-byte pieces (widths 8..64), or 2 as one piece (widths 8..32: twice the
+// lanes per row, for more warps per SM).
+#define KPM_STAGED_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(16, 4) X(4, 2) X(8, 2) X(16, 2)
 
 bool staged_shape_supported(int T, int E)
 {

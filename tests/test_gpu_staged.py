@@ -1,10 +1,12 @@
 """GPU tests of the staged sweep kernel (complex float storage; the V rows
 each SELL chunk gathers are copied once into shared memory by bulk copies,
-see include/kpm.h, kpm_launch.stages): the updated W must equal the
-register-path kernel's bit for bit (same products, same order per row), eta
-must agree with it to rounding of the summation order, and the moments must
-match the FP64 oracle within the FP32-form tolerance, for every stage count,
-block width, column-block split and row ordering."""
+see include/kpm.h, kpm_launch.stages): the updated W must agree with the
+register-path kernel's to single-precision rounding (the staged kernel sums
+the real- and imaginary-part products of a row in two paired accumulators,
+the register path in one chain) and be identical across stage counts, eta
+must agree with it to the same rounding, and the moments must match the
+FP64 oracle within the FP32-form tolerance, for every stage count, block
+width, column-block split and row ordering."""
 import numpy as np
 import pytest
 
@@ -56,7 +58,7 @@ def test_staged_is_the_complex_float_default(kpm):
 
 @pytest.mark.parametrize("R", [8, 16, 24, 32, 64, 100])
 @pytest.mark.parametrize("order", ["lattice", "cube"])
-def test_staged_sweep_equals_register_path(kpm, R, order):
+def test_staged_sweep_matches_register_path(kpm, R, order):
     dims = (8, 6, 5)
     h = ham.ti_hamiltonian(*dims, gamma=0.8, seed=2)
     a, b = scaled(h, kpm)
@@ -67,7 +69,7 @@ def test_staged_sweep_equals_register_path(kpm, R, order):
     with kpm.create(h, a, b, precision=kpm.PREC_FP32, row_order=row_order) as ctx:
         widths = [w for w in (64, 32, 16, 8, 4, 2, 1) if R & w]
         for init in (False, True):
-            ref = None
+            ref = first = None
             for stages in (0, 2, 3, 4):
                 try:
                     for w in widths:
@@ -81,10 +83,15 @@ def test_staged_sweep_equals_register_path(kpm, R, order):
                     continue
                 Wg, eg = sweep(ctx, R, V, W, init)
                 if ref is None:
-                    ref = (Wg, eg)
+                    ref = (Wg, eg)  # the register path
                     continue
-                assert np.array_equal(Wg, ref[0]), (stages, init)
-                np.testing.assert_allclose(eg, ref[1], rtol=0, atol=1e-12 * ref[1][0].max())
+                if first is None:
+                    first = Wg
+                assert np.array_equal(Wg, first), (stages, init)
+                # a few float roundings of a row's 13 products and the old W
+                wscale = np.abs(ref[0]).max()
+                np.testing.assert_allclose(Wg, ref[0], rtol=0, atol=4e-6 * wscale)
+                np.testing.assert_allclose(eg, ref[1], rtol=0, atol=1e-5 * ref[1][0].max())
 
 
 @pytest.mark.parametrize("stages", [2, 3, 4])
@@ -121,9 +128,9 @@ def test_staged_ragged_matrix(kpm, orc):
             assert dmu <= FP32_MU_TOL, (C, sigma, dmu)
 
 
-def test_staged_full_size_sweep_equals_register_path(kpm):
-    """64^3 lattice (N = 1,048,576), R = 32 in the bench's launch: W of one
-    sweep bit for bit and eta against the register path."""
+def test_staged_full_size_sweep_matches_register_path(kpm):
+    """64^3 lattice (N = 1,048,576), R = 32 in the bench's launch: W and eta
+    of one sweep against the register path, to float rounding."""
     import torch
     h = ham.ti_hamiltonian(64, 64, 64, gamma=1.0, seed=2)
     a, b = scaled(h, kpm)
@@ -136,6 +143,6 @@ def test_staged_full_size_sweep_equals_register_path(kpm):
         Ws, es = sweep(ctx, R, V, W, False)
         ctx.set_launch(R, 8, 4, 128, stages=0)
         Wr, er = sweep(ctx, R, V, W, False)
-    assert np.array_equal(Ws, Wr)
-    np.testing.assert_allclose(es, er, rtol=0, atol=1e-12 * er[0].max())
+    np.testing.assert_allclose(Ws, Wr, rtol=0, atol=4e-6 * np.abs(Wr).max())
+    np.testing.assert_allclose(es, er, rtol=0, atol=1e-5 * er[0].max())
     torch.cuda.synchronize()
