@@ -410,7 +410,8 @@ int kpm_set_launch(kpm_ctx *ctx, int32_t R, const kpm_launch *launch);
 /* Autotuner for block width R: times `sweeps` aug_spmmv sweeps (after two
  * untimed ones) on the context's work blocks for every built launch shape
  * -- lanes per row T and columns per lane E with T*E = width, 128..512
- * threads per block, 1 or 4 row groups per tile -- and for the widest
+ * threads per block, 1 or 4 row groups per tile, and for complex float the
+ * staged kernel with 1..3 stages where they fit -- and for the widest
  * column block (64, 32 or 16 columns, R split into powers of two up to
  * it), and keeps the fastest for later calls.  best (may be NULL) receives
  * the shape chosen for the widest block.  Synchronises stream. */

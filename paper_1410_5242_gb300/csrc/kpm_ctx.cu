@@ -877,6 +877,14 @@ std::vector<LaunchShape> shape_candidates(const kpm_ctx *c, int RB)
                 if (sweep_max_blocks_per_sm(c->precision, s, false) > 0)
                     out.push_back(s);
             }
+        // the staged kernel with 1..3 stages where they fit
+        for (int ns = 1; ns <= 3; ns++) {
+            LaunchShape s{T, E, 128, 0, 1};
+            s.stages = ns;
+            StagedLayout L;
+            if (shape_layout(c, s, L) && staged_max_blocks_per_sm(T, E, c->C, L.smem) > 0)
+                out.push_back(s);
+        }
     }
     return out;
 }
