@@ -362,7 +362,9 @@ int kpm_moments_device(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double
  *   variant 0: fully augmented sweep (kpm_aug_spmmv with eta_dev = NULL),
  *   variant 1: augmented SpMMV without the scalar products, W <- H'V - W,
  *   variant 2: plain SpMMV, W <- (1/2) H'V (W not read).
- * KPM_EINVAL for another variant. */
+ * Variants 1 and 2 run the kernel the context uses for the full sweep
+ * (register path, or the staged kernel for complex float) without the
+ * scalar products.  KPM_EINVAL for another variant. */
 int kpm_sweep_variant(kpm_ctx *ctx, int32_t R, const void *V, void *W, int32_t variant,
                       void *stream);
 

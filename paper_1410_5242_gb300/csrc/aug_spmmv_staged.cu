@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
             const int len = meta[0], pi = meta[1];
             const int64_t lt = meta[2];
             if (pi != cur) {
-                if (cur >= 0)
+                if (cur >= 0 && p.dots)
                     flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
                 cur = pi;
                 slot = lt;
@@ -541,22 +541,27 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
             const int64_t row = lt * (int64_t)C + rit;
             store_owned<float, T, E>(Wp, row * ldw + col0 + tl * EV, acc_s);
             // the row's own V entries: local position rit of the list
-            const float *ov = vb + (size_t)rit * 2 * RB;
+            if (p.dots) {
+                const float *ov = vb + (size_t)rit * 2 * RB;
 #pragma unroll
-            for (int q = 0; q < NP; q++) {
-                const float4 v4 =
-                    *reinterpret_cast<const float4 *>(ov + 2 * (q * T * EV + tl * EV));
-                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                for (int q = 0; q < NP; q++) {
+                    const float4 v4 =
+                        *reinterpret_cast<const float4 *>(ov + 2 * (q * T * EV + tl * EV));
+                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                for (int e = 0; e < EV; e++)
-                    acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e], acc_s[q * 2 * EV + 2 * e + 1],
-                                        v[2 * e], v[2 * e + 1]);
+                    for (int e = 0; e < EV; e++)
+                        acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e],
+                                            acc_s[q * 2 * EV + 2 * e + 1], v[2 * e],
+                                            v[2 * e + 1]);
+                }
             }
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(empty0 + 8 * s);
         }
-        if (cur >= 0) {
+        if (!p.dots) {
+            // no scalar products: nothing to write
+        } else if (cur >= 0) {
             flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
         } else if (p.probs == nullptr) {
             // a single problem's partials are read for every block: a block

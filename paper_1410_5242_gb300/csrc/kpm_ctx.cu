@@ -303,7 +303,7 @@ SweepParams sweep_params(const kpm_ctx *c, const ColumnBlock &cb, int R, const v
 }
 
 int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init,
-               cudaStream_t st)
+               cudaStream_t st, bool dots = true)
 {
     c->launches++;
     if (cb.shape.stages > 0) {
@@ -331,6 +331,7 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.stages = L.stages;
         q.with_imag = p.with_imag;
         q.init = init ? 1 : 0;
+        q.dots = dots ? 1 : 0;
         q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
         q.stage_bytes = L.stage_bytes;
@@ -781,6 +782,11 @@ int kpm_sweep_variant(kpm_ctx *c, int32_t R, const void *V, void *W, int32_t var
     KPM_TRY(plan_blocks(c, R, blocks, slot_doubles));
     for (const ColumnBlock &cb : blocks) {
         SweepParams p = sweep_params(c, cb, R, V, W, nullptr, false);
+        if (cb.shape.stages > 0) {
+            // the staged kernel without its scalar products
+            KPM_TRY(launch_one(c, cb, p, variant == 2, st, false));
+            continue;
+        }
         c->launches++;
         KPM_TRY(c->precision == KPM_PREC_FP64
                     ? launch_nodot_fp64(p, cb.shape, cb.grid, variant == 2, st)

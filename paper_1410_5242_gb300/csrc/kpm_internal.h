@@ -77,6 +77,7 @@ struct StagedParams {
     const StagedProblem *probs;
     int32_t n_probs, parity;
     int32_t C, stages, with_imag, init;
+    int32_t dots;  // 0: no scalar products (the ablation's reduced sweeps)
     int *err;  // device error word (KPM_DEVERR_*)
     uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx;
 };
