@@ -24,10 +24,11 @@
 // tile sequence moves on to the next problem.  A single problem is a table
 // of one.
 //
-// Lane/column ownership and the eta accumulation are those of aug_spmmv.cuh;
-// the products are accumulated with paired FMAs (real and imaginary parts of
-// h times a column in two packed sums), so W agrees with the register path
-// to single-precision rounding, and eta is reproducible run to run.
+// Lane/column ownership is that of aug_spmmv.cuh; the products are
+// accumulated with paired FMAs (real and imaginary parts of h times a column
+// in two packed sums), so W agrees with the register path to
+// single-precision rounding, and eta (packed 8-row partials folded into
+// TwoSum pairs, StagedEta) is reproducible run to run.
 //
 // Every wait is bounded (about two seconds of SM clock): on expiry the
 // thread records KPM_DEVERR_TIMEOUT in *err, raises the block's abort flag
@@ -185,6 +186,63 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+
+// A lane's eta terms for one column.  Each row adds |v|^2 and Re(conj(w) v)
+// as paired FMAs into packed single-precision pending sums ((v_re^2, v_im^2)
+// and (w_re v_re, w_im v_im)); every kEtaFold chunks fold() adds the pending
+// sums to (hi, lo) pairs with Knuth's TwoSum, so the running sum is carried
+// without rounding loss and only an 8-row partial is ever rounded in single
+// precision.  IMAG adds Im(conj(w) v) the same way in scalar form.
+constexpr int kEtaFold = 8;
+
+__device__ __forceinline__ void two_sum_pair(float &hi, float &lo, float p)
+{
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+template <bool IMAG>
+struct StagedEta {
+    uint64_t pvv = 0ull, pwv = 0ull;
+    float pwvi = 0.f;
+    float vv_h = 0.f, vv_l = 0.f, wv_h = 0.f, wv_l = 0.f, wvi_h = 0.f, wvi_l = 0.f;
+    __device__ __forceinline__ void add(float wr, float wi, float vr, float vi)
+    {
+        const uint64_t v2 = pack2(vr, vi), w2 = pack2(wr, wi);
+        pvv = ffma2(v2, v2, pvv);
+        pwv = ffma2(w2, v2, pwv);
+        if constexpr (IMAG) {
+            pwvi = __fmaf_rn(wr, vi, pwvi);
+            pwvi = __fmaf_rn(-wi, vr, pwvi);
+        }
+    }
+    __device__ __forceinline__ void fold()
+    {
+        float a, b;
+        unpack2(pvv, a, b);
+        two_sum_pair(vv_h, vv_l, __fadd_rn(a, b));
+        unpack2(pwv, a, b);
+        two_sum_pair(wv_h, wv_l, __fadd_rn(a, b));
+        pvv = pwv = 0ull;
+        if constexpr (IMAG) {
+            two_sum_pair(wvi_h, wvi_l, pwvi);
+            pwvi = 0.f;
+        }
+    }
+    // after fold()
+    __device__ __forceinline__ double get(int k) const
+    {
+        if (k == 0)
+            return (double)vv_h + (double)vv_l;
+        if (k == 1)
+            return (double)wv_h + (double)wv_l;
+        return IMAG ? (double)wvi_h + (double)wvi_l : 0.0;
+    }
+};
 
 // Inclusive prefix sum over the warp's lanes.
 __device__ __forceinline__ int warp_incl_scan(int v, int lane)
@@ -353,7 +411,7 @@ __device__ __forceinline__ void consumer_bar(int n_cw)
 // equal columns by an xor butterfly, then warp after warp into red (3*RB
 // doubles), then red to the problem's partial slot.  Resets acc.
 template <int T, int E, bool IMAG>
-__device__ __forceinline__ void flush_eta(EtaAcc<float, IMAG> (&acc)[E], double *red,
+__device__ __forceinline__ void flush_eta(StagedEta<IMAG> (&acc)[E], double *red,
                                           const StagedProblem &P, int64_t slot, int cw, int n_cw)
 {
     constexpr int RB = T * E;
@@ -361,10 +419,12 @@ __device__ __forceinline__ void flush_eta(EtaAcc<float, IMAG> (&acc)[E], double 
     const int tl = lane % T, team = lane / T;
     double out[3 * E];
 #pragma unroll
-    for (int k = 0; k < E; k++)
+    for (int k = 0; k < E; k++) {
+        acc[k].fold();
 #pragma unroll
         for (int q = 0; q < 3; q++)
             out[q * E + k] = acc[k].get(q);
+    }
 #pragma unroll
     for (int off = T; off < 32; off <<= 1)
 #pragma unroll
@@ -387,12 +447,14 @@ __device__ __forceinline__ void flush_eta(EtaAcc<float, IMAG> (&acc)[E], double 
     consumer_bar(n_cw);
 #pragma unroll
     for (int k = 0; k < E; k++)
-        acc[k] = EtaAcc<float, IMAG>();
+        acc[k] = StagedEta<IMAG>();
 }
 
-// Up to 32 + C*T = 544 threads (C = 32, T = 16).  Four columns per lane
-// (E = 4) need up to 96 registers, one block of that size per SM; two
-// columns per lane fit 56 registers, two blocks of 544 threads per SM.
+// Up to 32 + C*T = 544 threads (C = 32, T = 16).  A launch bound of 576
+// threads caps four columns per lane (E = 4) at 96 registers: 18 warps of
+// that size fit the register file of an SM's four sub-partitions (two
+// 288-thread blocks at width 32, or one 544-thread block at width 64); two
+// columns per lane get 56 (two 544-thread blocks).
 #define KPM_STAGED_MAX_THREADS 576
 
 template <int E>
@@ -451,7 +513,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
         const int tl = lane % T, team = lane / T;
         const int rit = cw * P + team;  // row within the chunk
         const int C = p.C;
-        EtaAcc<float, IMAG> acc[E];
+        StagedEta<IMAG> acc[E];
         int cur = -1;        // problem whose eta terms acc holds
         int64_t slot = 0;    // its partial slot: this block's first chunk of it
         float *Wp = nullptr;  // its W block, row length and first column
@@ -553,6 +615,11 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
                         acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e],
                                             acc_s[q * 2 * EV + 2 * e + 1], v[2 * e],
                                             v[2 * e + 1]);
+                }
+                if ((k % kEtaFold) == kEtaFold - 1) {
+#pragma unroll
+                    for (int c = 0; c < E; c++)
+                        acc[c].fold();
                 }
             }
             __syncwarp();
