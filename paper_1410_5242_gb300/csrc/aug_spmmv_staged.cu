@@ -6,11 +6,13 @@
 // have in flight are capped by its register file, and each V row is read
 // from L2 once per entry that uses it (13 times at 13 entries per row).
 // Here one producer warp per block copies, per SELL chunk, the matrix
-// values, the 16-bit local column indices, the old W rows and every V row
-// the chunk reads -- once, however many of its entries read it (the chunk's
-// gather list, kpm_gather_build) -- into a ring of shared-memory stages with
+// values, the 16-bit local column indices and every V row the chunk reads
+// -- once, however many of its entries read it (the chunk's gather list,
+// kpm_gather_build) -- into a ring of shared-memory stages with
 // cp.async.bulk, which completes on an mbarrier and occupies no registers.
-// The consumer warps compute the chunk's rows from shared memory.
+// The consumer warps compute the chunk's rows from shared memory; each
+// reads its row's old W from global memory (requested in L2 by the
+// producer) while the entry loop runs.
 //
 // Per stage s: full[s] (the producer's arrive + the copies' byte count)
 // and empty[s] (one arrive per consumer warp once it has read the stage).
@@ -137,6 +139,11 @@ constexpr uint32_t kTableOffset = kRedOffset + 3 * 64 * 8;  // eta sum of up to 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit()
@@ -365,8 +372,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
         const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * 8u;
         const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
-        const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes +
-                               (p.init ? 0u : (uint32_t)p.C * row_bytes);
+        const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes;
         if (lane == 0) {
             volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
@@ -381,8 +387,10 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             if (lane == 1)
                 bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, lidx_bytes, full);
         }
-        if (!p.init && lane == 2)
-            copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, ld, col0, row_bytes, full);
+        // the consumers read the chunk's old W rows themselves; ask L2 for
+        // them now (whole rows: contiguous, 16-byte multiples)
+        if (!p.init && lane == 2 && ((int64_t)ld * 8 & 15) == 0)
+            prefetch_l2(Wb + lt * (int64_t)p.C * ld * 8, (uint64_t)p.C * ld * 8);
         if (has_run && count > 0)
             copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, ld, col0,
                       row_bytes, full);
@@ -472,7 +480,8 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
     constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
     // [full[NS], empty[NS] | abort flag at 128 | stage metadata at
     //  kMetaOffset | record ring at kRingOffset | eta sum at kRedOffset |
-    //  problem table at kTableOffset | stages from bar_bytes on]
+    //  problem table at kTableOffset | stages from bar_bytes on | W buffer
+    //  at off_wbuf]
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -544,28 +553,27 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
             const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
 
             // W row <- H' V - W with two packed (re, im) accumulators per
-            // column: a = -W + sum_j Re(h_j) v_j, b = sum_j Im(h_j) v_j, so
-            // each entry costs two paired FMAs per column; at the end
-            // W = (a.re - b.im, a.im + b.re)
-            uint64_t pa[E], pb[E];
-            if (p.init) {
+            // column: a = sum_j Re(h_j) v_j, b = sum_j Im(h_j) v_j, so each
+            // entry costs two paired FMAs per column; at the end
+            // W = (a.re - b.im - W_re, a.im + b.re - W_im).  The old W row is
+            // requested from global memory first (the producer asked L2 for
+            // it when it armed the stage); the entry loop hides its latency.
+            const int64_t row = lt * (int64_t)C + rit;
+            const int64_t wbase = row * ldw + col0 + tl * EV;
+            // this lane's old W pieces go to the block's W buffer (the row's
+            // slot, written and read by this lane only) with cp.async
+            float *wsm = reinterpret_cast<float *>(smem + p.off_wbuf) + rit * 2 * RB;
+            if (!p.init) {
 #pragma unroll
-                for (int c = 0; c < E; c++)
-                    pa[c] = pb[c] = 0ull;
-            } else {
-                const float *wr = reinterpret_cast<const float *>(st + p.off_w) + rit * 2 * RB;
-#pragma unroll
-                for (int q = 0; q < NP; q++) {
-                    const float4 w4 =
-                        *reinterpret_cast<const float4 *>(wr + 2 * (q * T * EV + tl * EV));
-                    pa[q * EV] = pack2(-w4.x, -w4.y);
-                    pb[q * EV] = 0ull;
-                    if constexpr (EV == 2) {
-                        pa[q * EV + 1] = pack2(-w4.z, -w4.w);
-                        pb[q * EV + 1] = 0ull;
-                    }
-                }
+                for (int q = 0; q < NP; q++)
+                    cp_async16(smem_u32(wsm + 2 * (q * T * EV + tl * EV)),
+                               Wp + 2 * (wbase + (int64_t)q * T * EV));
+                cp_async_commit();
             }
+            uint64_t pa[E], pb[E];
+#pragma unroll
+            for (int c = 0; c < E; c++)
+                pa[c] = pb[c] = 0ull;
 #pragma unroll 4
             for (int j = 0; j < len; j++) {
                 const int u = lid[j * C + rit];
@@ -599,9 +607,21 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
 #pragma unroll
                 for (int q = 0; q < 2 * E; q++)
                     acc_s[q] *= 0.5f;
+            } else {
+                cp_async_wait<0>();
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    const float4 w4 =
+                        *reinterpret_cast<const float4 *>(wsm + 2 * (q * T * EV + tl * EV));
+                    acc_s[q * 2 * EV] -= w4.x;
+                    acc_s[q * 2 * EV + 1] -= w4.y;
+                    if constexpr (EV == 2) {
+                        acc_s[q * 2 * EV + 2] -= w4.z;
+                        acc_s[q * 2 * EV + 3] -= w4.w;
+                    }
+                }
             }
-            const int64_t row = lt * (int64_t)C + rit;
-            store_owned<float, T, E>(Wp, row * ldw + col0 + tl * EV, acc_s);
+            store_owned<float, T, E>(Wp, wbase, acc_s);
             // the row's own V entries: local position rit of the list
             if (p.dots) {
                 const float *ov = vb + (size_t)rit * 2 * RB;
@@ -665,8 +685,6 @@ bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n
         return false;
     const uint64_t row_bytes = (uint64_t)RB * 8;
     uint64_t off = up((uint64_t)u_max * row_bytes, 128);
-    o.off_w = (uint32_t)off;
-    off = up(off + (uint64_t)C * row_bytes, 128);
     o.off_val = (uint32_t)off;
     off = up(off + (uint64_t)C * l_max * 8, 128);
     o.off_lidx = (uint32_t)off;
@@ -674,7 +692,9 @@ bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n
     o.stage_bytes = (uint32_t)off;
     o.bar_bytes = (uint32_t)up(kTableOffset + (uint64_t)n_probs * sizeof(StagedProblem), 128);
     o.stages = stages;
-    o.smem = o.bar_bytes + (uint64_t)stages * o.stage_bytes;
+    // after the stages: the block's W buffer, one slot per row of a chunk
+    o.off_wbuf = (uint32_t)(o.bar_bytes + (uint64_t)stages * o.stage_bytes);
+    o.smem = o.off_wbuf + (uint64_t)C * row_bytes;
     return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 

@@ -493,9 +493,9 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.err = ctx[0]->d_err;
                 q.bar_bytes = sc.L.bar_bytes;
                 q.stage_bytes = sc.L.stage_bytes;
-                q.off_w = sc.L.off_w;
                 q.off_val = sc.L.off_val;
                 q.off_lidx = sc.L.off_lidx;
+                q.off_wbuf = sc.L.off_wbuf;
                 rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
                 if (rc != KPM_OK)
                     break;

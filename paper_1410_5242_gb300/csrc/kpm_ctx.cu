@@ -335,9 +335,9 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
         q.stage_bytes = L.stage_bytes;
-        q.off_w = L.off_w;
         q.off_val = L.off_val;
         q.off_lidx = L.off_lidx;
+        q.off_wbuf = L.off_wbuf;
         return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
     }
     if (c->precision == KPM_PREC_FP64)

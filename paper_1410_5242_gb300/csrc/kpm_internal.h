@@ -67,11 +67,11 @@ static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte
 // Arguments of one staged sweep (aug_spmmv_staged.cu) over a table of
 // problems (probs, n_probs entries, in device memory) or the single problem
 // `one` (probs = NULL, n_probs = 1), and the shared-memory layout of one
-// stage: V rows [u_max][RB] at 0, old W rows [C][RB] at off_w, values
-// [l_max][C] at off_val, local indices [l_max][C] at off_lidx (SELL order,
-// column-major in the chunk).  Stages start at bar_bytes; the barriers, each
+// stage: V rows [u_max][RB] at 0, values [l_max][C] at off_val, local
+// indices [l_max][C] at off_lidx (SELL order, column-major in the chunk).  Stages start at bar_bytes; the barriers, each
 // stage's chunk length, problem and chunk number, the record ring, the eta
-// sum and the problem table sit before them.
+// sum and the problem table sit before them, the block's W buffer (C rows
+// of RB columns) after them at off_wbuf.
 struct StagedParams {
     StagedProblem one;
     const StagedProblem *probs;
@@ -79,13 +79,13 @@ struct StagedParams {
     int32_t C, stages, with_imag, init;
     int32_t dots;  // 0: no scalar products (the ablation's reduced sweeps)
     int *err;  // device error word (KPM_DEVERR_*)
-    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
 };
 
 // The shared-memory layout of a staged launch; false if fewer than
 // min_stages stages fit in max_smem bytes.
 struct StagedLayout {
-    uint32_t bar_bytes, stage_bytes, off_w, off_val, off_lidx;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
     int stages;
     size_t smem;
 };
