@@ -399,11 +399,11 @@ typedef struct kpm_launch {
     int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
     int32_t stages;  /* 0: register-path kernel (block_threads per block, tile_groups);
                         1..8: complex float only, the staged kernel -- per SELL chunk
-                        one producer warp copies the matrix entries, the old W rows and
-                        each V row the chunk reads (once, kpm_gather_build) into one of
+                        one producer warp copies the matrix entries and each V row the
+                        chunk reads (once, kpm_gather_build) into one of
                         `stages` shared-memory stages with bulk copies, and C*T/32
                         consumer warps compute from there; block_threads = 32 + C*T,
-                        cols_per_lane = 4, width 8..64 */
+                        cols_per_lane 4 (width 8..64) or 2 (width 8..32) */
 } kpm_launch;
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */
