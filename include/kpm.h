@@ -300,6 +300,15 @@ int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);
  * to the caller.  Synchronous. */
 int kpm_check_device_error(kpm_ctx *ctx);
 
+/* Test hook for the bounded waits (not for production use): from now on the
+ * staged kernel's producer stops after chunks_per_block chunks in every
+ * block, so the consumers' waits for the next stage expire (after about two
+ * seconds of SM clock), the launch records a timeout in the device error word
+ * (kpm_check_device_error then returns KPM_ETIMEOUT) and its results are
+ * invalid; the context stays usable.  -1 switches the hook off.  KPM_EINVAL
+ * for values below -1. */
+int kpm_test_stall_staged(kpm_ctx *ctx, int64_t chunks_per_block);
+
 /* Bytes of one device vector block of width R in the context's layout:
  * n_pad rows of ld(R) complex numbers (complex double for FP64, complex
  * float for FP32), ld(R) = R, rounded up to even for FP32 when R > 1,

@@ -320,6 +320,8 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
     int ld = 0, col0 = 0;
     int64_t k = 0;
     for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
+        if (p.stall_after >= 0 && k >= p.stall_after)
+            break;  // test hook: leave the remaining stages unarmed
         const int slot = (int)(k % kMetaDepth);
         cp_async_wait<kMetaDepth - 1>();
         __syncwarp();

@@ -490,6 +490,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.with_imag = 0;
                 q.init = s == 0 ? 1 : 0;
                 q.dots = 1;
+                q.stall_after = -1;
                 q.err = ctx[0]->d_err;
                 q.bar_bytes = sc.L.bar_bytes;
                 q.stage_bytes = sc.L.stage_bytes;

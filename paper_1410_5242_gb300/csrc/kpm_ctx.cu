@@ -332,6 +332,7 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.with_imag = p.with_imag;
         q.init = init ? 1 : 0;
         q.dots = dots ? 1 : 0;
+        q.stall_after = c->stall_after;
         q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
         q.stage_bytes = L.stage_bytes;
@@ -662,6 +663,14 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_ovf);
     dev_free(c, c->d_err);
     delete c;
+}
+
+int kpm_test_stall_staged(kpm_ctx *c, int64_t chunks_per_block)
+{
+    if (!c || chunks_per_block < -1)
+        return KPM_EINVAL;
+    c->stall_after = chunks_per_block;
+    return KPM_OK;
 }
 
 int kpm_check_device_error(kpm_ctx *c)

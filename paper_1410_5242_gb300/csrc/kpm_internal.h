@@ -78,6 +78,8 @@ struct StagedParams {
     int32_t n_probs, parity;
     int32_t C, stages, with_imag, init;
     int32_t dots;  // 0: no scalar products (the ablation's reduced sweeps)
+    int64_t stall_after;  // >= 0: the producer stops after this many chunks per
+                          // block (test of the bounded waits); -1: never
     int *err;  // device error word (KPM_DEVERR_*)
     uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
 };
@@ -188,6 +190,7 @@ struct kpm_ctx {
     int2 *d_ovf = nullptr;
     int32_t u_max = 0, l_max = 0;
     int *d_err = nullptr;  // device error word, KPM_DEVERR_*
+    int64_t stall_after = -1;  // kpm_test_stall_staged
     size_t max_smem = 0;   // opt-in shared memory per block
 
     // work buffers (grown on demand)

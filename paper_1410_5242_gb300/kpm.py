@@ -93,6 +93,7 @@ _SIGS = {
     "kpm_gather_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather)]),
     "kpm_gather_release": (None, [ctypes.POINTER(Gather)]),
     "kpm_check_device_error": (_int, [_vp]),
+    "kpm_test_stall_staged": (_int, [_vp, _i64]),
     "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
                           ctypes.POINTER(_vp)]),
     "kpm_destroy": (None, [_vp]),
@@ -363,6 +364,9 @@ class Context:
 
     def check_device_error(self):
         _check(lib.kpm_check_device_error(self.handle), "kpm_check_device_error")
+
+    def test_stall_staged(self, chunks_per_block):
+        _check(lib.kpm_test_stall_staged(self.handle, chunks_per_block), "kpm_test_stall_staged")
 
     def autotune(self, R, sweeps=5, stream=None):
         """kpm_autotune: returns the launch shape chosen for the widest block."""

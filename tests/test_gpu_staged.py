@@ -146,3 +146,40 @@ def test_staged_full_size_sweep_matches_register_path(kpm):
     np.testing.assert_allclose(Ws, Wr, rtol=0, atol=4e-6 * np.abs(Wr).max())
     np.testing.assert_allclose(es, er, rtol=0, atol=1e-5 * er[0].max())
     torch.cuda.synchronize()
+
+
+def test_staged_bounded_wait_expires_and_context_recovers(kpm):
+    """The staged kernel's waits are bounded: with the producer stopped after
+    one chunk per block (test hook), the consumers' wait for the second stage
+    expires after about two seconds, the launch records KPM_ETIMEOUT in the
+    context's error word, and the context computes correctly afterwards."""
+    import time
+
+    import torch
+    h = ham.ti_hamiltonian(16, 16, 16, gamma=0.5, seed=1)  # 512 chunks: > 1 per block
+    a, b = scaled(h, kpm)
+    R = 32
+    g = np.random.default_rng(3)
+    V = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+    W = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        assert ctx.get_launch(R)["stages"] >= 1
+        want, want_eta = sweep(ctx, R, V, W, False)
+        ctx.test_stall_staged(1)
+        dV, dW = ctx.new_block(R), ctx.new_block(R)
+        ctx.block_upload(R, V, dV)
+        ctx.block_upload(R, W, dW)
+        eta = torch.zeros(3 * R, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        ctx.aug_spmmv(R, dV, dW, eta)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t0
+        with pytest.raises(kpm.KPMError) as e:
+            ctx.check_device_error()
+        assert e.value.status == kpm.KPM_ETIMEOUT
+        assert 0.5 < waited < 30.0
+        ctx.check_device_error()  # read and cleared
+        ctx.test_stall_staged(-1)
+        got, got_eta = sweep(ctx, R, V, W, False)
+    assert np.array_equal(got, want)
+    assert np.array_equal(got_eta, want_eta)
