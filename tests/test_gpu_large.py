@@ -23,9 +23,14 @@ def kpm():
     return k
 
 
-def test_large_lattice_fp64(kpm, orc):
+@pytest.fixture(scope="module")
+def large():
     cfg = workloads.TI_LARGE
-    h = ham.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+    return cfg, ham.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+
+
+def test_large_lattice_fp64(kpm, orc, large):
+    cfg, h = large
     n, R, M, seed = h["n"], cfg["R"], cfg["M"], cfg["seed"]
     assert n == 27_648_000 and len(h["col"]) == 13 * n
     a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
@@ -46,3 +51,26 @@ def test_large_lattice_fp64(kpm, orc):
     assert mu[0] == pytest.approx(1.0, abs=1e-15)
     _, rho = kpm.dos(mu, 4096, a, b)
     assert rho.min() > -1e-6 * rho.max()
+
+
+def test_large_lattice_fp32_staged(kpm, orc, large):
+    """The same lattice in complex float on the staged kernel (864,000
+    chunks): the first 8 moments of vectors 0 and 31 against the oracle
+    within the float form's tolerance, and the invariants of a 256-moment
+    run."""
+    cfg, h = large
+    n, R, seed = h["n"], cfg["R"], cfg["seed"]
+    a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        assert ctx.get_launch(R)["stages"] >= 1
+        short = ctx.moments(8, R, seed)
+        full = ctx.moments(256, R, seed)
+    ref, _ = orc.moments(h, a, b, 8, seed, [0, R - 1])
+    got = short[[0, R - 1]]
+    assert np.abs(kpm.eta_to_mu(got) - orc.eta_to_mu(ref)).max() <= 1e-5
+    np.testing.assert_allclose(got[:, 0], ref[:, 0], rtol=1e-6)
+    np.testing.assert_allclose(full[:, :8], short, rtol=0, atol=1e-9 * n)
+    np.testing.assert_allclose(full[:, 0], n, rtol=1e-6)
+    assert np.all(full[:, 0::2] >= 0)
+    mu = kpm.eta_to_mu(full)
+    assert np.max(np.abs(mu)) <= 1 + 1e-5
