@@ -588,6 +588,47 @@ def bench_reference(args, world, rank):
     print(json.dumps(out))
 
 
+def large_lattice(args):
+    """The 240 x 240 x 120 lattice (N = 27,648,000 rows, 359M entries; the
+    single-GPU roofline workload): the sweep kernel alone at R = 32 in both
+    forms, CUDA events on the launching stream.  Not part of the default run
+    (building the lattice and its layouts takes a few minutes of host time)."""
+    import torch
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm
+    cfg = workloads.TI_LARGE
+    t0 = time.perf_counter()
+    h, a, b = ti_problem(cfg)
+    t_build = time.perf_counter() - t0
+    n, R = h["n"], cfg["R"]
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_src = peaks()
+    out = {"workload": "TI lattice 240x240x120 (N=%d, nnz=%d), R=%d, gamma=%g, seed %d"
+                       % (n, len(h["col"]), R, cfg["gamma"], cfg["seed"]),
+           "lattice_build_s": round(t_build, 1)}
+    for name, prec, sd, launches in (("fp64", kpm.PREC_FP64, 16, 5), ("fp32", kpm.PREC_FP32, 8, 20)):
+        t0 = time.perf_counter()
+        ctx = kpm.create(h, a, b, precision=prec)
+        t_create = time.perf_counter() - t0
+        nnz = ctx.info()["nnz"]
+        t = kernel_only(ctx, R, launches, stream)
+        byt = model.sweep_bytes(n, nnz, R, sd)
+        entry = {"create_s": round(t_create, 1), "launch": ctx.get_launch(R),
+                 "avg_launch_ms": round(t * 1e3, 3), "algorithmic_bytes": byt,
+                 "GBs": round(byt / t / 1e9, 1), "frac_of_hbm_peak": round(byt / t / 1e9 / hbm_peak, 4)}
+        if prec == kpm.PREC_FP64:
+            fl = model.fused_fp64_flops(nnz, n, R)
+            entry["TFLOPs"] = round(fl / t / 1e12, 4)
+            entry["frac_of_fp64_peak"] = round(fl / t / 1e12 / FP64_PEAK_TFLOPS, 4)
+        out[name] = entry
+        ctx.close()
+        torch.cuda.empty_cache()
+    out["peak_source"] = "HBM %s %.0f GB/s; FP64 %.2f TFLOP/s nominal" % (peak_src, hbm_peak,
+                                                                         FP64_PEAK_TFLOPS)
+    print(json.dumps({"large_lattice": out}))
+
+
 def profile_sweeps(args):
     """A short program for ncu: 3 warm-up sweeps, then --kernel-launches
     sweeps of the 64^3 lattice at R = 32 in one form, nothing else."""
@@ -624,7 +665,12 @@ def main():
                     help="only run a few sweep launches of one form (for ncu captures)")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="only the 64-problem ensemble (one warm-up and --ensemble-runs timed runs)")
+    ap.add_argument("--large", action="store_true",
+                    help="only the 240x240x120 lattice: the sweep kernel alone in both forms")
     args = ap.parse_args()
+    if args.large:
+        large_lattice(args)
+        return
     if args.profile_sweeps:
         profile_sweeps(args)
         return
