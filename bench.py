@@ -464,6 +464,23 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
         Rs.append(p["R"])
         seeds.append(p["seed"])
     t_setup = time.perf_counter() - t0
+    # autotune the launch shape of each block-width class on its largest
+    # problem (kpm_autotune) and give it to the class's other problems: the
+    # batch launches each class with its first problem's shape
+    t0 = time.perf_counter()
+    tuned = {}
+    for R in sorted(set(Rs)):
+        members = [c for c, r in zip(ctxs, Rs) if r == R]
+        rep = max(members, key=lambda c: c.n)
+        rep.autotune(R, sweeps=3, stream=stream)
+        shape = rep.get_launch(R)
+        for c in members:
+            if c is not rep:
+                c.set_launch(R, shape["lanes_per_row"], shape["cols_per_lane"],
+                             shape["block_threads"], shape["blocks_per_sm"],
+                             shape["tile_groups"], shape["stages"])
+        tuned[str(R)] = shape
+    t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     batch = kpm.Batch(ctxs, Ms, Rs, seeds)
     t_capture = time.perf_counter() - t0
@@ -479,7 +496,8 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
            "ms_per_run": round(t * 1e3, 1), "runs": args.ensemble_runs, "warmup": 1,
            "algorithmic_bytes_per_run": info["algorithmic_bytes"], "sweeps": info["sweeps"],
            "steps": info["steps"], "graph_kernel_nodes": info["kernel_launches"],
-           "setup_s": round(t_setup, 1), "capture_s": round(t_capture, 2),
+           "setup_s": round(t_setup, 1), "autotune_s": round(t_tune, 1), "tuned_launch": tuned,
+           "capture_s": round(t_capture, 2),
            "mu0_problem0": float(kpm.eta_to_mu(eta0)[0])}
     batch.close()
     for c in ctxs:

@@ -246,7 +246,10 @@ int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, doub
  * CUDA graph and run as one graph launch.  Complex float classes of width
  * 8..64 whose contexts all have gather lists with one chunk height run the
  * staged kernel (kpm_launch.stages) over the class's chunks, the others the
- * register-path kernel.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
+ * register-path kernel.  A class takes the launch shape and stage count
+ * that its first problem's context (the one with the largest M) uses for
+ * the width -- the default, or what kpm_autotune / kpm_set_launch chose --
+ * with fewer stages where the class's widest gather list needs it.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
  * + kpm_batch_eta for every problem + kpm_batch_destroy. */
 int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
                       const uint64_t *seed, double *const *eta, void *stream);

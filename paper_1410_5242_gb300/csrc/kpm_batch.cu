@@ -329,23 +329,36 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             b->class_first.push_back(i);
     b->class_first.push_back(count);
     // Complex float classes run the staged kernel when every problem has
-    // gather lists with one chunk height and the stages fit.
+    // gather lists with one chunk height and the stages fit.  The class takes
+    // the lane shape and stage count its first problem's context uses for
+    // width R (as tuned by kpm_autotune or kpm_set_launch, else the default);
+    // a register-path choice there keeps the class on the register path.
     b->staged.assign(b->class_first.size() - 1, StagedClass());
     for (size_t cl = 0; cl + 1 < b->class_first.size() && !fp64; cl++) {
         const int first = b->class_first[cl], last = b->class_first[cl + 1];
         const int RB = R[order[first]];
+        const kpm_ctx *c0 = ctx[order[first]];
+        auto it = c0->shapes.find(RB);
+        const LaunchShape sh = it != c0->shapes.end() ? it->second : default_shape(c0, RB);
         StagedClass &sc = b->staged[cl];
-        sc.T = RB / 4;
-        bool ok = RB >= 8 && staged_shape_supported(sc.T, sc.E);
+        sc.T = sh.T;
+        sc.E = sh.E;
+        bool ok = sh.stages > 0 && RB >= 8 && sh.T * sh.E == RB &&
+                  staged_shape_supported(sc.T, sc.E);
         int u_max = 0, l_max = 0;
         for (int i = first; i < last && ok; i++) {
             const kpm_ctx *c = ctx[order[i]];
-            ok = c->gather_ok && c->C == ctx[order[first]]->C;
+            ok = c->gather_ok && c->C == c0->C;
             u_max = std::max(u_max, c->u_max);
             l_max = std::max(l_max, c->l_max);
         }
-        ok = ok && staged_layout(ctx[order[first]]->C, sc.T, RB, u_max, l_max, 2, last - first,
+        // the class's stage count, or fewer where the wider gather lists of
+        // other problems (or the problem table) do not leave room
+        bool fits = false;
+        for (int ns = ok ? sh.stages : 0; ns >= 1 && !fits; ns--)
+            fits = staged_layout(c0->C, sc.T, RB, u_max, l_max, ns, last - first,
                                  ctx[0]->max_smem, sc.L);
+        ok = ok && fits;
         if (ok) {
             const int bps = staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem);
             sc.grid = bps * ctx[0]->n_sm;

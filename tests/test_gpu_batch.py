@@ -163,3 +163,31 @@ def test_staged_batch_classes_with_several_problems(kpm, orc):
         assert np.abs(kpm.eta_to_mu(eta[cols]) - orc.eta_to_mu(ref)).max() <= 1e-5
     for c, *_ in ctxs:
         c.close()
+
+
+def test_batch_classes_take_their_first_problems_launch_shape(kpm, orc):
+    """A class runs with the launch shape its first problem's context uses
+    for the width (kpm_set_launch / kpm_autotune): the register path for one
+    class, one stage for another; the moments stay those of the single
+    problems."""
+    probs = [
+        (ham.ti_hamiltonian(8, 8, 6, gamma=0.5, seed=1), 48, 16, 31),
+        (ham.ti_hamiltonian(5, 5, 5, gamma=1.0, seed=2), 32, 16, 32),
+        (ham.ti_hamiltonian(9, 7, 6, gamma=2.0, seed=3), 40, 32, 33),
+        (ham.ti_hamiltonian(6, 6, 6, gamma=0.3, seed=4), 24, 32, 34),
+    ]
+    ctxs = []
+    for h, M, R, seed in probs:
+        a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+        ctxs.append((kpm.create(h, a, b, precision=kpm.PREC_FP32), h, a, b))
+    # batch order is by width, then by decreasing M: the first problem of
+    # each class is the one with the largest M
+    ctxs[0][0].set_launch(16, 4, 4, 128, tile_groups=1, stages=0)
+    ctxs[2][0].set_launch(32, 8, 4, 128, stages=1)
+    etas = kpm.moments_batch([c for c, *_ in ctxs], [p[1] for p in probs], [p[2] for p in probs],
+                             [p[3] for p in probs])
+    for (ctx, h, a, b), (_, M, R, seed), eta in zip(ctxs, probs, etas):
+        ref, _ = orc.moments(h, a, b, M, seed, [0, R - 1])
+        assert np.abs(kpm.eta_to_mu(eta[[0, R - 1]]) - orc.eta_to_mu(ref)).max() <= 1e-5
+    for c, *_ in ctxs:
+        c.close()
