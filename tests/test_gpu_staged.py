@@ -114,12 +114,13 @@ def test_staged_moments_match_oracle(kpm, orc, stages, R):
 
 
 def test_staged_ragged_matrix(kpm, orc):
-    # rows of different lengths, empty rows, padding rows, C = 16 and 64
+    # rows of different lengths, empty rows, padding rows, C = 8, 16 and 64
+    # (gather lists past the inline runs at C = 64)
     h = ham.random_hermitian(517, 9, seed=13, empty_rows=0.08)
     a, b = scaled(h, kpm)
     M, R = 40, 16
     ref, _ = orc.moments(h, a, b, M, 5, range(R))
-    for C in (16, 64):
+    for C in (8, 16, 64):  # C = 8: one consumer warp per block
         for sigma in (1, 64):
             with kpm.create(h, a, b, precision=kpm.PREC_FP32, chunk_height=C, sigma=sigma) as ctx:
                 assert ctx.get_launch(R)["stages"] >= 2
