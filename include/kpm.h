@@ -349,7 +349,7 @@ int kpm_aug_spmmv(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_d
  *   - R needing more partials than the scratch holds is rejected with
  *     KPM_EINVAL before anything is launched.  The need is the sum over
  *     column blocks of grid * 3 * width doubles; with the default launch
- *     shapes (256-thread blocks) every R <= 256 fits.
+ *     shapes of both forms every R <= 256 fits.
  *   - Nothing in the scratch has to start at zero: every call writes each
  *     partial it later reads.  Calls share the one array and it keeps the
  *     last call's contents, so calls that overlap on the GPU (other streams,
