@@ -46,12 +46,22 @@ FALLBACK_HBM_GBS = 6800.0
 # SM x 152 SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s (nominal 1.25).
 FP64_PEAK_TFLOPS = 1.25
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "aug_spmmv_traffic.txt")
-# the sources of each form's sweep kernel (complex double: register path;
-# complex float: the staged kernel)
+# the sources of each form's sweep kernel (the staged kernel in both forms
+# at the bench's widths)
 KERNEL_SOURCES = {
-    "fp64": ("aug_spmmv.cuh", "aug_spmmv_fp64.cu"),
+    "fp64": ("aug_spmmv.cuh", "aug_spmmv_staged.cu", "kpm_internal.h"),
     "fp32": ("aug_spmmv.cuh", "aug_spmmv_staged.cu", "kpm_internal.h"),
 }
+
+
+def kernel_name(prec, launch, half=False):
+    """The sweep kernel a launch shape runs (template arguments as built)."""
+    real = "double" if prec == "fp64" else "float"
+    if launch["stages"]:
+        return "aug_spmmv_staged_kernel<%s,%d,%d,false,%s>, %d stages" % (
+            real, launch["lanes_per_row"], launch["cols_per_lane"],
+            "true" if half else "false", launch["stages"])
+    return "aug_spmmv_kernel<%s,%d,%d>" % (real, launch["lanes_per_row"], launch["cols_per_lane"])
 
 
 def kernel_hash(form):
@@ -261,7 +271,9 @@ def bench_ours(args, world, rank, local):
     # the sweep kernel alone (roofline of the dominant kernel)
     t_k = kernel_only(ctx, R, args.kernel_launches, stream)
     k_bytes = model.sweep_bytes(n, nnz, R, 16)
-    k_flops = model.fused_fp64_flops(nnz, n, R)
+    # executed flops: the half-complex form skips the zero products
+    half = bool(info["half_complex"])
+    k_flops = model.fused_fp64_flops(nnz, n, R, half=half)
     achieved_tf = k_flops / t_k / 1e12
     k_gbs = k_bytes / t_k / 1e9
     traffic = measured_traffic("fp64")
@@ -305,10 +317,14 @@ def bench_ours(args, world, rank, local):
             r_sweep.append({
                 "R": Rs, "B_min_fp64_bytes_per_flop": round(model.code_balance(nnz / n, Rs), 3),
                 "fp64_ms": round(t64 * 1e3, 4), "fp64_GBs": round(b64 / t64 / 1e9, 1),
-                "fp64_TFLOPs": round(model.fused_fp64_flops(nnz, n, Rs) / t64 / 1e12, 4),
+                "fp64_TFLOPs": round(model.fused_fp64_flops(nnz, n, Rs, half=half) / t64 / 1e12,
+                                     4),
                 "fp32_ms": round(t32s * 1e3, 4), "fp32_GBs": round(b32 / t32s / 1e9, 1),
                 "fp32_frac_hbm": round(b32 / t32s / 1e9 / hbm_peak, 4),
-                "launch_fp64": ctx.get_launch(Rs), "launch_fp32": ctx32.get_launch(Rs)})
+                # the widest column block's shape (complex double splits R = 64
+                # into two 32-wide blocks)
+                "launch_fp64": ctx.get_launch(min(Rs, ctx.max_block_width())),
+                "launch_fp32": ctx32.get_launch(min(Rs, ctx32.max_block_width()))})
 
     # ---------------- optimisation stages of the paper on this GPU
     ablation = None
@@ -361,8 +377,8 @@ def bench_ours(args, world, rank, local):
             "bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
             "traffic": traffic,
-            "kernel": "aug_spmmv_kernel<double,%d,%d>" % (launch_shape["lanes_per_row"],
-                                                         launch_shape["cols_per_lane"]),
+            "kernel": kernel_name("fp64", launch_shape, half),
+            "half_complex": half,
             "avg_launch_ms": round(t_k * 1e3, 4),
             "algorithmic_bytes": k_bytes, "algorithmic_flops": k_flops,
             "hbm_gbs": round(k_gbs, 1), "hbm_frac": round(k_gbs / hbm_peak, 4),
@@ -380,11 +396,7 @@ def bench_ours(args, world, rank, local):
                          "unit": "GB/s", "frac": round(k32_gbs / hbm_peak, 4),
                          "traffic": traffic32, "avg_launch_ms": round(t_k32 * 1e3, 4),
                          "algorithmic_bytes": k32_bytes,
-                         "kernel": ("aug_spmmv_staged_kernel<%d,%d>, %d stages"
-                                    % (launch32["lanes_per_row"], launch32["cols_per_lane"],
-                                       launch32["stages"]) if launch32["stages"] else
-                                    "aug_spmmv_kernel<float,%d,%d>"
-                                    % (launch32["lanes_per_row"], launch32["cols_per_lane"])),
+                         "kernel": kernel_name("fp32", launch32),
                          "launch": launch32,
                          "peak_source": "HBM %s %.0f GB/s" % (peak_src, hbm_peak)},
             "accuracy": fp32_err,
@@ -636,7 +648,7 @@ def large_lattice(args):
                  "avg_launch_ms": round(t * 1e3, 3), "algorithmic_bytes": byt,
                  "GBs": round(byt / t / 1e9, 1), "frac_of_hbm_peak": round(byt / t / 1e9 / hbm_peak, 4)}
         if prec == kpm.PREC_FP64:
-            fl = model.fused_fp64_flops(nnz, n, R)
+            fl = model.fused_fp64_flops(nnz, n, R, half=bool(ctx.info()["half_complex"]))
             entry["TFLOPs"] = round(fl / t / 1e12, 4)
             entry["frac_of_fp64_peak"] = round(fl / t / 1e12 / FP64_PEAK_TFLOPS, 4)
         out[name] = entry

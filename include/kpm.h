@@ -292,6 +292,9 @@ typedef struct kpm_info {
     double a, b;
     int64_t matrix_bytes;   /* device bytes of values + column indices */
     int64_t kernel_launches; /* kernels this context has launched so far */
+    int32_t gather_lists;    /* 1: the staged kernel's gather lists were built */
+    int32_t half_complex;    /* 1: complex double, every stored entry purely real or
+                                purely imaginary (the staged kernel's two-FMA form) */
 } kpm_info;
 
 int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);
@@ -375,8 +378,7 @@ int kpm_moments_device(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double
  *   variant 1: augmented SpMMV without the scalar products, W <- H'V - W,
  *   variant 2: plain SpMMV, W <- (1/2) H'V (W not read).
  * Variants 1 and 2 run the kernel the context uses for the full sweep
- * (register path, or the staged kernel for complex float) without the
- * scalar products.  KPM_EINVAL for another variant. */
+ * (register path or staged kernel) without the scalar products.  KPM_EINVAL for another variant. */
 int kpm_sweep_variant(kpm_ctx *ctx, int32_t R, const void *V, void *W, int32_t variant,
                       void *stream);
 
@@ -404,18 +406,26 @@ void kpm_naive_destroy(kpm_naive *nv);
  * (0 = occupancy maximum), row groups per warp in one block tile (a
  * tile is threads/32 * (32/T) * tile_groups consecutive rows; 0 = 4) and
  * the kernel (stages), as chosen by the defaults or the autotuner.  The
- * complex float default is the staged kernel with two stages wherever the
- * context has gather lists (C >= 8), the width is 8..64 and two stages fit
- * in shared memory; everything else runs the register-path kernel. */
+ * default is the staged kernel with two stages wherever the context has
+ * gather lists (C >= 8), the width is 8..64 (complex float, 4 columns per
+ * lane) or 8..32 (complex double, 2 columns per lane) and two stages fit in
+ * shared memory; everything else runs the register-path kernel.  Complex
+ * double contexts with gather lists split R into blocks of at most 32
+ * columns (kpm_get_max_block_width).  For a complex double matrix whose
+ * every stored entry is purely real or purely imaginary (the topological
+ * insulator, Sec. "Application Scenario"), the staged kernel multiplies
+ * with two real FMAs per entry and column instead of four (the skipped
+ * products are exact zeros, so W is the same). */
 typedef struct kpm_launch {
     int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
     int32_t stages;  /* 0: register-path kernel (block_threads per block, tile_groups);
-                        1..8: complex float only, the staged kernel -- per SELL chunk
+                        1..8: the staged kernel -- per SELL chunk
                         one producer warp copies the matrix entries and each V row the
                         chunk reads (once, kpm_gather_build) into one of
                         `stages` shared-memory stages with bulk copies, and C*T/32
-                        consumer warps compute from there; block_threads = 32 + C*T,
-                        cols_per_lane 4 (width 8..64) or 2 (width 8..32) */
+                        consumer warps compute from there; block_threads = 32 + C*T;
+                        complex float: cols_per_lane 4 (width 8..64) or 2 (width
+                        8..32); complex double: cols_per_lane 2 (width 8..32) */
 } kpm_launch;
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */
@@ -424,15 +434,15 @@ int kpm_set_launch(kpm_ctx *ctx, int32_t R, const kpm_launch *launch);
 /* Autotuner for block width R: times `sweeps` aug_spmmv sweeps (after two
  * untimed ones) on the context's work blocks for every built launch shape
  * -- lanes per row T and columns per lane E with T*E = width, 128..512
- * threads per block, 1 or 4 row groups per tile, and for complex float the
- * staged kernel with 1..3 stages where they fit -- and for the widest
+ * threads per block, 1 or 4 row groups per tile, and the staged kernel
+ * with 1..3 stages where they fit -- and for the widest
  * column block (64, 32 or 16 columns, R split into powers of two up to
  * it), and keeps the fastest for later calls.  best (may be NULL) receives
  * the shape chosen for the widest block.  Synchronises stream. */
 int kpm_autotune(kpm_ctx *ctx, int32_t R, int32_t sweeps, void *stream, kpm_launch *best);
 
-/* Widest column block the context uses (64 unless the autotuner chose
- * less). */
+/* Widest column block the context uses (64, or 32 for complex double
+ * contexts with gather lists, unless the autotuner chose otherwise). */
 int kpm_get_max_block_width(const kpm_ctx *ctx);
 
 /* Layout autotuner: builds trial contexts with SELL chunk heights C in

@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "aug_spmmv.cuh"
 #include "kpm_internal.h"
@@ -158,13 +159,15 @@ __device__ __forceinline__ void cp_async_wait()
 }
 
 // Copies rows [row0, row0 + nrows) of a vector block (rows of ld complex
-// floats; columns col0 .. col0 + RB - 1) to consecutive RB-wide rows at
-// dst: one copy when the block's rows are exactly RB wide, else one per row.
+// numbers of csize bytes; columns col0 .. col0 + RB - 1) to consecutive
+// RB-wide rows at dst: one copy when the block's rows are exactly RB wide,
+// else one per row.
 __device__ __forceinline__ void copy_rows(uint32_t dst, const char *block, int64_t row0, int nrows,
-                                          int ld, int col0, uint32_t row_bytes, uint32_t bar)
+                                          int ld, int col0, uint32_t row_bytes, uint32_t bar,
+                                          int csize)
 {
-    const int64_t ld_bytes = (int64_t)ld * 8;
-    const char *src = block + row0 * ld_bytes + (int64_t)col0 * 8;
+    const int64_t ld_bytes = (int64_t)ld * csize;
+    const char *src = block + row0 * ld_bytes + (int64_t)col0 * csize;
     if (ld_bytes == (int64_t)row_bytes) {
         bulk_g2s(dst, src, (uint32_t)nrows * row_bytes, bar);
     } else {
@@ -251,6 +254,19 @@ struct StagedEta {
     }
 };
 
+// A lane's eta terms for one column in complex double: plain FMA chains
+// (aug_spmmv.cuh's EtaAcc); fold() has nothing to do.
+template <bool IMAG>
+struct StagedEta64 {
+    EtaAcc<double, IMAG> a;
+    __device__ __forceinline__ void add(double wr, double wi, double vr, double vi)
+    {
+        a.add(wr, wi, vr, vi);
+    }
+    __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ double get(int k) const { return a.get(k); }
+};
+
 // Inclusive prefix sum over the warp's lanes.
 __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 {
@@ -278,12 +294,12 @@ __device__ __forceinline__ int advance_problem(const StagedProblem *tab, int n_p
 // word l of the tile's record, i.e. inline run l - 3; runs past the inline
 // ones are read from the overflow array 32 at a time.  Returns the number
 // of tiles armed.
-template <int RB>
+template <int RB, int CSIZE>
 __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem,
                                            const StagedProblem *tab, int64_t total,
                                            volatile int *abort_flag)
 {
-    constexpr uint32_t row_bytes = RB * 8;
+    constexpr uint32_t row_bytes = RB * CSIZE;
     const int lane = threadIdx.x & 31;
     const int NS = p.stages;
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
@@ -372,7 +388,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                 break;
         }
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
-        const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * 8u;
+        const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * (uint32_t)CSIZE;
         const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
         const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes;
         if (lane == 0) {
@@ -385,17 +401,17 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         __syncwarp();
         if (len > 0) {
             if (lane == 0)
-                bulk_g2s(st + p.off_val, valb + e0 * 8, val_bytes, full);
+                bulk_g2s(st + p.off_val, valb + e0 * CSIZE, val_bytes, full);
             if (lane == 1)
                 bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, lidx_bytes, full);
         }
         // the consumers read the chunk's old W rows themselves; ask L2 for
         // them now (whole rows: contiguous, 16-byte multiples)
-        if (!p.init && lane == 2 && ((int64_t)ld * 8 & 15) == 0)
-            prefetch_l2(Wb + lt * (int64_t)p.C * ld * 8, (uint64_t)p.C * ld * 8);
+        if (!p.init && lane == 2 && ((int64_t)ld * CSIZE & 15) == 0)
+            prefetch_l2(Wb + lt * (int64_t)p.C * ld * CSIZE, (uint64_t)p.C * ld * CSIZE);
         if (has_run && count > 0)
             copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, ld, col0,
-                      row_bytes, full);
+                      row_bytes, full, CSIZE);
         uint32_t base = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
         for (int g = KPM_REC_INLINE_RUNS; g < nruns; g += 32) {
             const int2 r = g + lane < nruns
@@ -404,7 +420,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             const int ri = warp_incl_scan(r.y, lane);
             if (r.y > 0)
                 copy_rows(st + (base + (uint32_t)(ri - r.y)) * row_bytes, Vb, r.x, r.y, ld, col0,
-                          row_bytes, full);
+                          row_bytes, full, CSIZE);
             base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
         }
     }
@@ -420,8 +436,8 @@ __device__ __forceinline__ void consumer_bar(int n_cw)
 // The consumer warps' eta sums for one problem, in a fixed order: lanes of
 // equal columns by an xor butterfly, then warp after warp into red (3*RB
 // doubles), then red to the problem's partial slot.  Resets acc.
-template <int T, int E, bool IMAG>
-__device__ __forceinline__ void flush_eta(StagedEta<IMAG> (&acc)[E], double *red,
+template <typename Real, int T, int E, typename Acc>
+__device__ __forceinline__ void flush_eta(Acc (&acc)[E], double *red,
                                           const StagedProblem &P, int64_t slot, int cw, int n_cw)
 {
     constexpr int RB = T * E;
@@ -446,7 +462,7 @@ __device__ __forceinline__ void flush_eta(StagedEta<IMAG> (&acc)[E], double *red
             for (int q = 0; q < 3; q++)
 #pragma unroll
                 for (int k = 0; k < E; k++) {
-                    double &d = red[q * RB + owned_column<float, T, E>(tl, k)];
+                    double &d = red[q * RB + owned_column<Real, T, E>(tl, k)];
                     d = w == 0 ? out[q * E + k] : d + out[q * E + k];
                 }
         }
@@ -457,29 +473,98 @@ __device__ __forceinline__ void flush_eta(StagedEta<IMAG> (&acc)[E], double *red
     consumer_bar(n_cw);
 #pragma unroll
     for (int k = 0; k < E; k++)
-        acc[k] = StagedEta<IMAG>();
+        acc[k] = Acc();
 }
 
 // Up to 32 + C*T = 544 threads (C = 32, T = 16).  A launch bound of 576
 // threads caps four columns per lane (E = 4) at 96 registers: 18 warps of
 // that size fit the register file of an SM's four sub-partitions (two
 // 288-thread blocks at width 32, or one 544-thread block at width 64); two
-// columns per lane get 56 (two 544-thread blocks).
+// columns per lane get 56 (two 544-thread blocks).  Complex double keeps
+// one block per SM: its stages are twice as large.
 #define KPM_STAGED_MAX_THREADS 576
 
-template <int E>
+template <typename Real, int E>
 struct StagedMinBlocks {
-    static constexpr int value = E >= 4 ? 1 : 2;
+    static constexpr int value = (E >= 4 || sizeof(Real) == 8) ? 1 : 2;
 };
 
-template <int T, int E, bool IMAG>
-__global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::value)
+// One row's H' V for this lane's E columns from a stage, complex double:
+// one 16-byte piece per column and lane and four FMAs per entry and column;
+// or, with HALF (every stored entry purely real or purely imaginary), two.
+// There the value array holds operand pairs (a, b) and bit 15 of the local
+// index marks an imaginary entry: a real one, (r, r), adds (r x, r y) to
+// (re, im); an imaginary one, (-m, m), adds (-m y, m x), so the halves of v
+// are read in swapped order.  The two FMAs are the general form's nonzero
+// products in the same order (the skipped ones add exact zeros), so both
+// forms give the same W.
+template <int T, int E, bool HALF>
+__device__ __forceinline__ void row_product(const double *vb, const double2 *vals,
+                                            const uint16_t *lid, int C, int len, int rit, int tl,
+                                            double (&acc_s)[2 * E])
+{
+    constexpr int RB = T * E;
+#pragma unroll
+    for (int q = 0; q < 2 * E; q++)
+        acc_s[q] = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < len; j++) {
+        const int l = lid[j * C + rit];
+        const double2 h = vals[j * C + rit];
+        if constexpr (HALF) {
+            const int sw = l >> 15;
+            const double *vr = vb + (size_t)(l & 0x7fff) * 2 * RB + 2 * tl;
+            const double *v0 = vr + sw, *v1 = vr + (sw ^ 1);
+#pragma unroll
+            for (int k = 0; k < E; k++) {
+                acc_s[2 * k] = fma(h.x, v0[2 * k * T], acc_s[2 * k]);
+                acc_s[2 * k + 1] = fma(h.y, v1[2 * k * T], acc_s[2 * k + 1]);
+            }
+        } else {
+            const double *vr = vb + (size_t)l * 2 * RB;
+#pragma unroll
+            for (int k = 0; k < E; k++) {
+                const double2 v = *reinterpret_cast<const double2 *>(vr + 2 * (k * T + tl));
+                acc_s[2 * k] = fma(h.x, v.x, acc_s[2 * k]);
+                acc_s[2 * k] = fma(-h.y, v.y, acc_s[2 * k]);
+                acc_s[2 * k + 1] = fma(h.x, v.y, acc_s[2 * k + 1]);
+                acc_s[2 * k + 1] = fma(h.y, v.x, acc_s[2 * k + 1]);
+            }
+        }
+    }
+}
+
+// One 16-byte piece (two complex floats or one complex double) from
+// shared memory.
+__device__ __forceinline__ void lds_piece(const float *src, float (&out)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(src);
+    out[0] = t.x;
+    out[1] = t.y;
+    out[2] = t.z;
+    out[3] = t.w;
+}
+
+__device__ __forceinline__ void lds_piece(const double *src, double (&out)[2])
+{
+    const double2 t = *reinterpret_cast<const double2 *>(src);
+    out[0] = t.x;
+    out[1] = t.y;
+}
+
+template <typename Real, int T, int E, bool IMAG, bool HALF>
+__global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, E>::value)
     aug_spmmv_staged_kernel(const StagedParams p)
 {
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
+    static_assert(!HALF || sizeof(Real) == 8, "the half-complex form is complex double only");
     constexpr int P = 32 / T;
     constexpr int RB = T * E;
-    constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
+    constexpr int CSIZE = 2 * (int)sizeof(Real);
+    constexpr int EV = Pieces<Real, E>::EV, NP = Pieces<Real, E>::NP;
+    static_assert(2 * EV * sizeof(Real) == 16, "16-byte pieces");
+    using Acc = typename std::conditional<sizeof(Real) == 4, StagedEta<IMAG>,
+                                          StagedEta64<IMAG>>::type;
     // [full[NS], empty[NS] | abort flag at 128 | stage metadata at
     //  kMetaOffset | record ring at kRingOffset | eta sum at kRedOffset |
     //  problem table at kTableOffset | stages from bar_bytes on | W buffer
@@ -511,7 +596,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
     const int64_t total = tab[p.n_probs - 1].tile0 + tab[p.n_probs - 1].n_tiles;
 
     if (warp == 0) {
-        const int64_t armed = produce<RB>(p, smem, tab, total, abort_flag);
+        const int64_t armed = produce<RB, CSIZE>(p, smem, tab, total, abort_flag);
         // the copies of the last armed stages must land before the block's
         // shared memory is released
         if (lane == 0)
@@ -524,10 +609,10 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
         const int tl = lane % T, team = lane / T;
         const int rit = cw * P + team;  // row within the chunk
         const int C = p.C;
-        StagedEta<IMAG> acc[E];
+        Acc acc[E];
         int cur = -1;        // problem whose eta terms acc holds
         int64_t slot = 0;    // its partial slot: this block's first chunk of it
-        float *Wp = nullptr;  // its W block, row length and first column
+        Real *Wp = nullptr;  // its W block, row length and first column
         int ldw = 0, col0 = 0;
         int64_t k = 0;
         for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, k++) {
@@ -543,28 +628,26 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
             const int64_t lt = meta[2];
             if (pi != cur) {
                 if (cur >= 0 && p.dots)
-                    flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
+                    flush_eta<Real, T, E>(acc, red, tab[cur], slot, cw, n_cw);
                 cur = pi;
                 slot = lt;
-                Wp = static_cast<float *>(tab[pi].buf[p.parity ^ 1]);
+                Wp = static_cast<Real *>(tab[pi].buf[p.parity ^ 1]);
                 ldw = tab[pi].ld;
                 col0 = tab[pi].col0;
             }
-            const float *vb = reinterpret_cast<const float *>(st);
-            const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
+            using Real2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+            const Real *vb = reinterpret_cast<const Real *>(st);
+            const Real2 *vals = reinterpret_cast<const Real2 *>(st + p.off_val);
             const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
 
-            // W row <- H' V - W with two packed (re, im) accumulators per
-            // column: a = sum_j Re(h_j) v_j, b = sum_j Im(h_j) v_j, so each
-            // entry costs two paired FMAs per column; at the end
-            // W = (a.re - b.im - W_re, a.im + b.re - W_im).  The old W row is
-            // requested from global memory first (the producer asked L2 for
-            // it when it armed the stage); the entry loop hides its latency.
+            // The old W row is requested from global memory first (the
+            // producer asked L2 for it when it armed the stage): this lane's
+            // 16-byte pieces go to the block's W buffer (the row's slot,
+            // written and read by this lane only) with cp.async, and the
+            // entry loop hides their latency.
             const int64_t row = lt * (int64_t)C + rit;
             const int64_t wbase = row * ldw + col0 + tl * EV;
-            // this lane's old W pieces go to the block's W buffer (the row's
-            // slot, written and read by this lane only) with cp.async
-            float *wsm = reinterpret_cast<float *>(smem + p.off_wbuf) + rit * 2 * RB;
+            Real *wsm = reinterpret_cast<Real *>(smem + p.off_wbuf) + rit * 2 * RB;
             if (!p.init) {
 #pragma unroll
                 for (int q = 0; q < NP; q++)
@@ -572,66 +655,70 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
                                Wp + 2 * (wbase + (int64_t)q * T * EV));
                 cp_async_commit();
             }
-            uint64_t pa[E], pb[E];
+            Real acc_s[2 * E];
+            if constexpr (sizeof(Real) == 4) {
+                // complex float: two packed (re, im) accumulators per
+                // column, a = sum_j Re(h_j) v_j and b = sum_j Im(h_j) v_j, so
+                // each entry costs two paired FMAs per column; then
+                // H' V = (a.re - b.im, a.im + b.re)
+                uint64_t pa[E], pb[E];
 #pragma unroll
-            for (int c = 0; c < E; c++)
-                pa[c] = pb[c] = 0ull;
+                for (int c = 0; c < E; c++)
+                    pa[c] = pb[c] = 0ull;
 #pragma unroll 4
-            for (int j = 0; j < len; j++) {
-                const int u = lid[j * C + rit];
-                const float2 h = vals[j * C + rit];
-                const uint64_t hx2 = pack2(h.x, h.x), hy2 = pack2(h.y, h.y);
-                const float *vr = vb + (size_t)u * 2 * RB;
+                for (int j = 0; j < len; j++) {
+                    const int u = lid[j * C + rit];
+                    const float2 h = vals[j * C + rit];
+                    const uint64_t hx2 = pack2(h.x, h.x), hy2 = pack2(h.y, h.y);
+                    const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
-                for (int q = 0; q < NP; q++) {
-                    const float4 v4 =
-                        *reinterpret_cast<const float4 *>(vr + 2 * (q * T * EV + tl * EV));
-                    const uint64_t v0 = pack2(v4.x, v4.y);
-                    pa[q * EV] = ffma2(hx2, v0, pa[q * EV]);
-                    pb[q * EV] = ffma2(hy2, v0, pb[q * EV]);
-                    if constexpr (EV == 2) {
-                        const uint64_t v1 = pack2(v4.z, v4.w);
-                        pa[q * EV + 1] = ffma2(hx2, v1, pa[q * EV + 1]);
-                        pb[q * EV + 1] = ffma2(hy2, v1, pb[q * EV + 1]);
+                    for (int q = 0; q < NP; q++) {
+                        const float4 v4 =
+                            *reinterpret_cast<const float4 *>(vr + 2 * (q * T * EV + tl * EV));
+                        const uint64_t v0 = pack2(v4.x, v4.y);
+                        pa[q * EV] = ffma2(hx2, v0, pa[q * EV]);
+                        pb[q * EV] = ffma2(hy2, v0, pb[q * EV]);
+                        if constexpr (EV == 2) {
+                            const uint64_t v1 = pack2(v4.z, v4.w);
+                            pa[q * EV + 1] = ffma2(hx2, v1, pa[q * EV + 1]);
+                            pb[q * EV + 1] = ffma2(hy2, v1, pb[q * EV + 1]);
+                        }
                     }
                 }
-            }
-            float acc_s[2 * E];
 #pragma unroll
-            for (int c = 0; c < E; c++) {
-                float ar, ai, br, bi;
-                unpack2(pa[c], ar, ai);
-                unpack2(pb[c], br, bi);
-                acc_s[2 * c] = ar - bi;
-                acc_s[2 * c + 1] = ai + br;
+                for (int c = 0; c < E; c++) {
+                    float ar, ai, br, bi;
+                    unpack2(pa[c], ar, ai);
+                    unpack2(pb[c], br, bi);
+                    acc_s[2 * c] = ar - bi;
+                    acc_s[2 * c + 1] = ai + br;
+                }
+            } else {
+                row_product<T, E, HALF>(vb, vals, lid, C, len, rit, tl, acc_s);
             }
             if (p.init) {
 #pragma unroll
                 for (int q = 0; q < 2 * E; q++)
-                    acc_s[q] *= 0.5f;
+                    acc_s[q] *= Real(0.5);
             } else {
                 cp_async_wait<0>();
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
-                    const float4 w4 =
-                        *reinterpret_cast<const float4 *>(wsm + 2 * (q * T * EV + tl * EV));
-                    acc_s[q * 2 * EV] -= w4.x;
-                    acc_s[q * 2 * EV + 1] -= w4.y;
-                    if constexpr (EV == 2) {
-                        acc_s[q * 2 * EV + 2] -= w4.z;
-                        acc_s[q * 2 * EV + 3] -= w4.w;
-                    }
+                    Real w[2 * EV];
+                    lds_piece(wsm + 2 * (q * T * EV + tl * EV), w);
+#pragma unroll
+                    for (int i = 0; i < 2 * EV; i++)
+                        acc_s[q * 2 * EV + i] -= w[i];
                 }
             }
-            store_owned<float, T, E>(Wp, wbase, acc_s);
+            store_owned<Real, T, E>(Wp, wbase, acc_s);
             // the row's own V entries: local position rit of the list
             if (p.dots) {
-                const float *ov = vb + (size_t)rit * 2 * RB;
+                const Real *ov = vb + (size_t)rit * 2 * RB;
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
-                    const float4 v4 =
-                        *reinterpret_cast<const float4 *>(ov + 2 * (q * T * EV + tl * EV));
-                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                    Real v[2 * EV];
+                    lds_piece(ov + 2 * (q * T * EV + tl * EV), v);
 #pragma unroll
                     for (int e = 0; e < EV; e++)
                         acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e],
@@ -651,7 +738,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
         if (!p.dots) {
             // no scalar products: nothing to write
         } else if (cur >= 0) {
-            flush_eta<T, E, IMAG>(acc, red, tab[cur], slot, cw, n_cw);
+            flush_eta<Real, T, E>(acc, red, tab[cur], slot, cw, n_cw);
         } else if (p.probs == nullptr) {
             // a single problem's partials are read for every block: a block
             // without chunks contributes zeros
@@ -663,32 +750,40 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<E>::va
 
 }  // namespace
 
-// (T, E) shapes of the staged kernel: 4 complex columns per lane as two
-// 16-byte pieces (widths 8..64), or 2 as one piece (widths 8..32: twice the
-// lanes per row, for more warps per SM).
+// (T, E) shapes of the staged kernel.  Complex float: 4 columns per lane
+// as two 16-byte pieces (widths 8..64), or 2 as one piece (widths 8..32:
+// twice the lanes per row, for more warps per SM).  Complex double: 2
+// columns per lane as two pieces (widths 8..32; a 64-wide stage would not
+// fit twice), each with and without the half-complex shortcut.
 #define KPM_STAGED_SHAPES(X) X(2, 4) X(4, 4) X(8, 4) X(16, 4) X(4, 2) X(8, 2) X(16, 2)
+#define KPM_STAGED_SHAPES64(X) X(4, 2) X(8, 2) X(16, 2)
 
-bool staged_shape_supported(int T, int E)
+bool staged_shape_supported(int T, int E, bool fp64)
 {
 #define KPM_CASE(T_, E_) \
     if (T == T_ && E == E_) \
         return true;
-    KPM_STAGED_SHAPES(KPM_CASE)
+    if (fp64) {
+        KPM_STAGED_SHAPES64(KPM_CASE)
+    } else {
+        KPM_STAGED_SHAPES(KPM_CASE)
+    }
 #undef KPM_CASE
     return false;
 }
 
-bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n_probs,
-                   size_t max_smem, StagedLayout &o)
+bool staged_layout(int C, int T, int RB, int csize, int u_max, int l_max, int stages,
+                   int n_probs, size_t max_smem, StagedLayout &o)
 {
     auto up = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
-    if (C < 8 || T < 1 || RB < 1 || RB > 64 || u_max < C || l_max < 0 || stages < 1 ||
-        stages > 8 || n_probs < 1 || (C * T) % 32 != 0 || 32 + C * T > KPM_STAGED_MAX_THREADS)
+    if (C < 8 || T < 1 || RB < 1 || RB > 64 || (csize != 8 && csize != 16) || u_max < C ||
+        l_max < 0 || stages < 1 || stages > 8 || n_probs < 1 || (C * T) % 32 != 0 ||
+        32 + C * T > KPM_STAGED_MAX_THREADS)
         return false;
-    const uint64_t row_bytes = (uint64_t)RB * 8;
+    const uint64_t row_bytes = (uint64_t)RB * csize;
     uint64_t off = up((uint64_t)u_max * row_bytes, 128);
     o.off_val = (uint32_t)off;
-    off = up(off + (uint64_t)C * l_max * 8, 128);
+    off = up(off + (uint64_t)C * l_max * csize, 128);
     o.off_lidx = (uint32_t)off;
     off = up(off + (uint64_t)C * l_max * 2, 128);
     o.stage_bytes = (uint32_t)off;
@@ -700,24 +795,57 @@ bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n
     return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 
-int staged_max_blocks_per_sm(int T, int E, int C, size_t smem)
+namespace {
+
+template <typename Real, int T, int E, bool IMAG, bool HALF>
+int occupancy_of(int threads, size_t smem)
+{
+    int nb = 0;
+    if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+// Launches one instantiation, raising its dynamic shared-memory limit the
+// first time a launch needs more.
+template <typename Real, int T, int E, bool IMAG, bool HALF>
+int launch_one_staged(const StagedParams &p, int grid, int threads, size_t smem, cudaStream_t st)
+{
+    static size_t set = 0;
+    if (set < smem) {
+        if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return KPM_ECUDA;
+        set = smem;
+    }
+    aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF><<<grid, threads, smem, st>>>(p);
+    return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;
+}
+
+}  // namespace
+
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64)
 {
     const int threads = 32 + C * T;
-    int nb = 0;
-#define KPM_CASE(T_, E_)                                                                       \
-    if (T == T_ && E == E_) {                                                                  \
-        if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, false>,                       \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=    \
-                cudaSuccess ||                                                                 \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                     \
-                &nb, aug_spmmv_staged_kernel<T_, E_, false>, threads, smem) != cudaSuccess) {  \
-            cudaGetLastError();                                                                \
-            return 0;                                                                          \
-        }                                                                                      \
-        return nb;                                                                             \
+#define KPM_CASE(T_, E_) \
+    if (T == T_ && E == E_) \
+        return occupancy_of<float, T_, E_, false, false>(threads, smem);
+#define KPM_CASE64(T_, E_) \
+    if (T == T_ && E == E_) \
+        return occupancy_of<double, T_, E_, false, false>(threads, smem);
+    if (fp64) {
+        KPM_STAGED_SHAPES64(KPM_CASE64)
+    } else {
+        KPM_STAGED_SHAPES(KPM_CASE)
     }
-    KPM_STAGED_SHAPES(KPM_CASE)
 #undef KPM_CASE
+#undef KPM_CASE64
     return 0;
 }
 
@@ -725,35 +853,30 @@ int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t sm
 {
     const int threads = 32 + p.C * T;
     if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8 ||
-        p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1))
+        p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1) || (p.half && !p.fp64))
         return KPM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
+    if (T == T_ && E == E_)                                                                    \
+        return p.with_imag ? launch_one_staged<float, T_, E_, true, false>(p, grid, threads, smem, st) \
+                           : launch_one_staged<float, T_, E_, false, false>(p, grid, threads, smem, st);
+#define KPM_CASE64(T_, E_)                                                                     \
     if (T == T_ && E == E_) {                                                                  \
-        static size_t set_t = 0, set_f = 0;                                                    \
-        if (p.with_imag) {                                                                     \
-            if (set_t < smem) {                                                                \
-                if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, true>,                \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                                         (int)smem) != cudaSuccess)                            \
-                    return KPM_ECUDA;                                                          \
-                set_t = smem;                                                                  \
-            }                                                                                  \
-            aug_spmmv_staged_kernel<T_, E_, true><<<grid, threads, smem, st>>>(p);             \
-        } else {                                                                               \
-            if (set_f < smem) {                                                                \
-                if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<T_, E_, false>,               \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                                         (int)smem) != cudaSuccess)                            \
-                    return KPM_ECUDA;                                                          \
-                set_f = smem;                                                                  \
-            }                                                                                  \
-            aug_spmmv_staged_kernel<T_, E_, false><<<grid, threads, smem, st>>>(p);             \
-        }                                                                                      \
-        return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;                         \
+        if (p.half)                                                                            \
+            return p.with_imag                                                                 \
+                       ? launch_one_staged<double, T_, E_, true, true>(p, grid, threads, smem, st) \
+                       : launch_one_staged<double, T_, E_, false, true>(p, grid, threads, smem, st); \
+        return p.with_imag                                                                     \
+                   ? launch_one_staged<double, T_, E_, true, false>(p, grid, threads, smem, st) \
+                   : launch_one_staged<double, T_, E_, false, false>(p, grid, threads, smem, st); \
     }
-    KPM_STAGED_SHAPES(KPM_CASE)
+    if (p.fp64) {
+        KPM_STAGED_SHAPES64(KPM_CASE64)
+    } else {
+        KPM_STAGED_SHAPES(KPM_CASE)
+    }
 #undef KPM_CASE
+#undef KPM_CASE64
     return KPM_EUNSUPPORTED;
 }
 

@@ -344,7 +344,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         sc.T = sh.T;
         sc.E = sh.E;
         bool ok = sh.stages > 0 && RB >= 8 && sh.T * sh.E == RB &&
-                  staged_shape_supported(sc.T, sc.E);
+                  staged_shape_supported(sc.T, sc.E, false);
         int u_max = 0, l_max = 0;
         for (int i = first; i < last && ok; i++) {
             const kpm_ctx *c = ctx[order[i]];
@@ -356,11 +356,12 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         // other problems (or the problem table) do not leave room
         bool fits = false;
         for (int ns = ok ? sh.stages : 0; ns >= 1 && !fits; ns--)
-            fits = staged_layout(c0->C, sc.T, RB, u_max, l_max, ns, last - first,
+            fits = staged_layout(c0->C, sc.T, RB, 8, u_max, l_max, ns, last - first,
                                  ctx[0]->max_smem, sc.L);
         ok = ok && fits;
         if (ok) {
-            const int bps = staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem);
+            const int bps =
+                staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem, false);
             sc.grid = bps * ctx[0]->n_sm;
             ok = bps > 0;
         }

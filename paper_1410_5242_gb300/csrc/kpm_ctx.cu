@@ -161,8 +161,9 @@ std::vector<int> column_widths(int R, int cap)
 LaunchShape default_shape(const kpm_ctx *c, int RB)
 {
     LaunchShape s;
-    s.threads = c->precision == KPM_PREC_FP64 ? 256 : 128;
-    if (c->precision == KPM_PREC_FP64) {
+    const bool fp64 = c->precision == KPM_PREC_FP64;
+    s.threads = fp64 ? 256 : 128;
+    if (fp64) {
         s.E = RB >= 64 ? 2 : 1;
         s.T = RB / s.E;
     } else {
@@ -170,20 +171,23 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
         s.T = RB / s.E;
     }
     s.blocks_per_sm = 0;  // 0 = occupancy maximum
-    s.tile_groups = c->precision == KPM_PREC_FP64 ? 8 : 1;
+    s.tile_groups = fp64 ? 8 : 1;
     s.stages = 0;
-    if (c->precision == KPM_PREC_FP32 && c->gather_ok && s.E == 4 &&
-        staged_shape_supported(s.T, s.E)) {
-        // two stages: the copies of one chunk fly while the consumers work
-        // on the other, and two blocks fit per SM at width 32 (measured
-        // best at widths 16..64 on the 64^3 lattice; a third stage costs
-        // the second block)
-        for (int ns = 2; ns >= 2; ns--) {
-            StagedLayout L;
-            if (staged_layout(c->C, s.T, RB, c->u_max, c->l_max, ns, 1, c->max_smem, L)) {
-                s.stages = ns;
-                break;
-            }
+    // The staged kernel where it is built and two stages fit: the copies of
+    // one chunk fly while the consumers work on the other.  Complex float
+    // takes 4 columns per lane (two blocks per SM at width 32; measured best
+    // at widths 16..64 on the 64^3 lattice, a third stage costs the second
+    // block); complex double 2 columns per lane at widths 8..32 (one block
+    // per SM at width 32; measured faster than the register path at widths
+    // 8..32 on the 64^3 lattice, with and without the half-complex form).
+    const int E = fp64 ? 2 : 4;
+    if (c->gather_ok && RB >= 8 && RB % E == 0 && staged_shape_supported(RB / E, E, fp64)) {
+        StagedLayout L;
+        if (staged_layout(c->C, RB / E, RB, fp64 ? 16 : 8, c->u_max, c->l_max, 2, 1,
+                          c->max_smem, L)) {
+            s.E = E;
+            s.T = RB / E;
+            s.stages = 2;
         }
     }
     return s;
@@ -193,10 +197,17 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
 // not fit or the context has no gather lists).
 bool shape_layout(const kpm_ctx *c, const LaunchShape &s, StagedLayout &L)
 {
-    if (s.stages < 1 || c->precision != KPM_PREC_FP32 || !c->gather_ok ||
-        !staged_shape_supported(s.T, s.E))
+    const bool fp64 = c->precision == KPM_PREC_FP64;
+    if (s.stages < 1 || !c->gather_ok || !staged_shape_supported(s.T, s.E, fp64))
         return false;
-    return staged_layout(c->C, s.T, s.T * s.E, c->u_max, c->l_max, s.stages, 1, c->max_smem, L);
+    return staged_layout(c->C, s.T, s.T * s.E, fp64 ? 16 : 8, c->u_max, c->l_max, s.stages, 1,
+                         c->max_smem, L);
+}
+
+// Blocks per SM of a staged shape with layout L.
+int staged_occupancy(const kpm_ctx *c, const LaunchShape &s, const StagedLayout &L)
+{
+    return staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem, c->precision == KPM_PREC_FP64);
 }
 
 int resolve_grid(kpm_ctx *c, LaunchShape &s)
@@ -206,7 +217,7 @@ int resolve_grid(kpm_ctx *c, LaunchShape &s)
         StagedLayout L;
         if (!shape_layout(c, s, L))
             return -1;
-        occ = staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem);
+        occ = staged_occupancy(c, s, L);
     } else {
         occ = sweep_max_blocks_per_sm(c->precision, s, false);
     }
@@ -314,7 +325,7 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.one.rec = c->d_rec;
         q.one.ovf = c->d_ovf;
         q.one.lidx = c->d_lidx;
-        q.one.val = c->d_val;
+        q.one.val = c->half_ok ? c->d_val_half : c->d_val;
         q.one.buf[0] = const_cast<void *>(p.V);
         q.one.buf[1] = p.W;
         q.one.partial = p.partial;
@@ -332,6 +343,8 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.with_imag = p.with_imag;
         q.init = init ? 1 : 0;
         q.dots = dots ? 1 : 0;
+        q.fp64 = c->precision == KPM_PREC_FP64 ? 1 : 0;
+        q.half = q.fp64 && c->half_ok ? 1 : 0;
         q.stall_after = c->stall_after;
         q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
@@ -584,7 +597,12 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             cudaSuccess)
             return fail(KPM_ECUDA);
     }
-    if (c->precision == KPM_PREC_FP32 && sell.C >= 8) {
+    // complex double with every stored entry purely real or purely
+    // imaginary: the staged kernel's two-FMA form
+    bool half = c->precision == KPM_PREC_FP64;
+    for (int64_t k = 0; k < sell.n_stored && half; k++)
+        half = sell.val_ri[2 * k] == 0.0 || sell.val_ri[2 * k + 1] == 0.0;
+    if (sell.C >= 8) {
         // gather lists for the staged kernel; a matrix whose lists do not fit
         // the 16-bit local indices keeps the register-path kernel only
         kpm_gather g;
@@ -617,6 +635,39 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                 kpm_gather_release(&g);
                 return fail(KPM_ENOMEM);
             }
+            // The two-FMA form's operands: entry h = (r, 0) is stored as
+            // (r, r) and adds (r x, r y); h = (0, m) as (-m, m) with bit 15 of
+            // its local index set, and adds (-m y, m x): the kernel reads the
+            // V row's halves in swapped order for it.  Lists of more than
+            // 32768 rows keep the four-FMA form.
+            std::vector<double> hv;
+            half = half && g.u_max <= 32768;
+            if (half) {
+                try {
+                    hv.resize(2 * (size_t)sell.n_stored);
+                } catch (const std::bad_alloc &) {
+                    kpm_gather_release(&g);
+                    return fail(KPM_ENOMEM);
+                }
+                for (int64_t e = 0; e < sell.n_stored; e++) {
+                    const double re = sell.val_ri[2 * e], im = sell.val_ri[2 * e + 1];
+                    const bool imag = re == 0.0;
+                    hv[2 * e] = imag ? -im : re;
+                    hv[2 * e + 1] = imag ? im : re;
+                    if (imag)
+                        g.lidx[e] = (uint16_t)(g.lidx[e] | 0x8000u);
+                }
+                c->d_val_half = dev_alloc(c, 16 * sell.n_stored);
+                if (!c->d_val_half) {
+                    kpm_gather_release(&g);
+                    return fail(KPM_ENOMEM);
+                }
+                if (cudaMemcpy(c->d_val_half, hv.data(), 16 * sell.n_stored,
+                               cudaMemcpyHostToDevice) != cudaSuccess) {
+                    kpm_gather_release(&g);
+                    return fail(KPM_ECUDA);
+                }
+            }
             c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sell.n_stored);
             c->d_rec = (int2 *)dev_alloc(c, sizeof(int2) * rec.size());
             c->d_ovf = (int2 *)dev_alloc(c, sizeof(int2) * (ovf.empty() ? 1 : ovf.size()));
@@ -635,6 +686,12 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             if (!ok)
                 return fail(alloc_ok ? KPM_ECUDA : KPM_ENOMEM);
             c->gather_ok = true;
+            c->half_ok = half;
+            // complex double: the staged kernel's widest block is 32 columns
+            // (wider rows would leave room for one stage only), and two
+            // 32-wide staged sweeps beat one 64-wide register-path sweep
+            if (c->precision == KPM_PREC_FP64)
+                c->max_rb = 32;
         }
     }
     kpm_sell_release(&sell);
@@ -659,6 +716,7 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_eta);
     dev_free(c, c->d_eta_im);
     dev_free(c, c->d_lidx);
+    dev_free(c, c->d_val_half);
     dev_free(c, c->d_rec);
     dev_free(c, c->d_ovf);
     dev_free(c, c->d_err);
@@ -702,6 +760,8 @@ int kpm_get_info(const kpm_ctx *c, kpm_info *out)
     out->a = c->a;
     out->b = c->b;
     out->matrix_bytes = c->n_stored * ((int64_t)c->sdc + 4);
+    out->gather_lists = c->gather_ok ? 1 : 0;
+    out->half_complex = c->half_ok ? 1 : 0;
     out->kernel_launches = c->launches;
     return KPM_OK;
 }
@@ -897,7 +957,8 @@ std::vector<LaunchShape> shape_candidates(const kpm_ctx *c, int RB)
             LaunchShape s{T, E, 128, 0, 1};
             s.stages = ns;
             StagedLayout L;
-            if (shape_layout(c, s, L) && staged_max_blocks_per_sm(T, E, c->C, L.smem) > 0)
+            if (shape_layout(c, s, L) &&
+                staged_occupancy(c, s, L) > 0)
                 out.push_back(s);
         }
     }
@@ -1018,6 +1079,7 @@ int kpm_autotune(kpm_ctx *c, int32_t R, int32_t sweeps, void *stream,
         best->block_threads = s.threads;
         best->blocks_per_sm = s.blocks_per_sm;
         best->tile_groups = s.tile_groups;
+        best->stages = s.stages;
     }
     return KPM_OK;
 }
@@ -1092,7 +1154,7 @@ int kpm_get_launch(const kpm_ctx *c, int32_t R, kpm_launch *out)
         StagedLayout L;
         if (s.stages > 0)
             s.blocks_per_sm = shape_layout(c, s, L)
-                                  ? staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem)
+                                  ? staged_occupancy(c, s, L)
                                   : 0;
         else
             s.blocks_per_sm = sweep_max_blocks_per_sm(c->precision, s, false);
@@ -1122,7 +1184,7 @@ int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
     DeviceGuard guard(c->device);
     if (s.stages > 0) {
         StagedLayout L;
-        if (!shape_layout(c, s, L) || staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem) < 1)
+        if (!shape_layout(c, s, L) || staged_occupancy(c, s, L) < 1)
             return KPM_EUNSUPPORTED;
         // the register-path fields stay valid for the ablation variants
         if (sweep_max_blocks_per_sm(c->precision, s, false) < 1)

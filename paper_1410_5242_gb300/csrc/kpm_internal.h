@@ -82,6 +82,8 @@ struct StagedParams {
                           // block (test of the bounded waits); -1: never
     int *err;  // device error word (KPM_DEVERR_*)
     uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
+    int32_t fp64;  // complex double (else complex float)
+    int32_t half;  // complex double, every stored entry purely real or imaginary
 };
 
 // The shared-memory layout of a staged launch; false if fewer than
@@ -91,15 +93,16 @@ struct StagedLayout {
     int stages;
     size_t smem;
 };
-bool staged_layout(int C, int T, int RB, int u_max, int l_max, int stages, int n_probs,
-                   size_t max_smem, StagedLayout &out);
-bool staged_shape_supported(int T, int E);
+// csize: bytes of one complex number (8 or 16).
+bool staged_layout(int C, int T, int RB, int csize, int u_max, int l_max, int stages,
+                   int n_probs, size_t max_smem, StagedLayout &out);
+bool staged_shape_supported(int T, int E, bool fp64);
 int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream);
-int staged_max_blocks_per_sm(int T, int E, int C, size_t smem);
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64);
 
 // stages = 0: the register-path kernel of aug_spmmv.cuh with `threads` per
-// block; stages >= 2: the staged kernel (complex float) with that many
-// shared-memory stages and 32 + C*T threads per block.
+// block; stages >= 1: the staged kernel of aug_spmmv_staged.cu with that
+// many shared-memory stages and 32 + C*T threads per block.
 struct LaunchShape {
     int T, E, threads, blocks_per_sm, tile_groups;
     int stages = 0;
@@ -183,8 +186,13 @@ struct kpm_ctx {
     int32_t *d_perm = nullptr;
     std::vector<int32_t> perm;  // host copy: new row -> original row
 
-    // gather lists of the staged kernel (complex float contexts)
+    // gather lists of the staged kernel (contexts with C >= 8)
     bool gather_ok = false;
+    // every stored entry purely real or purely imaginary (complex double
+    // contexts: the staged kernel's two-FMA form, with its own operand
+    // array and bit 15 of d_lidx marking the imaginary entries)
+    bool half_ok = false;
+    void *d_val_half = nullptr;  // [n_stored] (a, b) operand pairs
     uint16_t *d_lidx = nullptr;  // [n_stored] local positions (SELL order)
     int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;

@@ -52,7 +52,8 @@ class Info(ctypes.Structure):
                 ("n_stored", ctypes.c_int64), ("n_chunks", ctypes.c_int64), ("C", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("matrix_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("gather_lists", ctypes.c_int32),
+                ("half_complex", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -361,6 +362,10 @@ class Context:
                    tile_groups=0, stages=0):
         l = Launch(lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups, stages)
         _check(lib.kpm_set_launch(self.handle, R, ctypes.byref(l)), "kpm_set_launch")
+
+    def max_block_width(self):
+        """kpm_get_max_block_width: widest column block this context uses."""
+        return lib.kpm_get_max_block_width(self.handle)
 
     def check_device_error(self):
         _check(lib.kpm_check_device_error(self.handle), "kpm_check_device_error")

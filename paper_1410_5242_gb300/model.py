@@ -25,11 +25,13 @@ def sweep_flops(n, nnz, R):
     return R * (nnz * (F_A + F_M) + n * (math.ceil(7 * F_A / 2) + math.ceil(9 * F_M / 2)))
 
 
-def fused_fp64_flops(nnz, n, R):
+def fused_fp64_flops(nnz, n, R, half=False):
     """Floating-point work the fused kernel executes with H' = 2a(H - b 1)
     folded: one complex multiply-add (8 flops) per stored entry and column,
-    plus <V|V> and Re<W|V> (4 flops each) per row and column."""
-    return R * (8 * nnz + 8 * n)
+    or 4 when every entry is purely real or purely imaginary (half=True: the
+    other two products are zero), plus <V|V> and Re<W|V> (4 flops each) per
+    row and column."""
+    return R * ((4 if half else 8) * nnz + 8 * n)
 
 
 def kpm_traffic(M, n, nnz, R, sd, variant="aug_spmmv"):
