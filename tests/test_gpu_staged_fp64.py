@@ -54,6 +54,16 @@ def half_complex(h):
     return {"n": n, "row_ptr": h["row_ptr"], "col": h["col"], "val": val}
 
 
+def peierls(h, t=0.3):
+    """The TI matrix with a phase e^{i t} on every hopping above the diagonal
+    (e^{-i t} below: still Hermitian), so its entries are general complex."""
+    v = np.asarray(h["val"], dtype=np.complex128)
+    rows = np.repeat(np.arange(h["n"]), np.diff(h["row_ptr"]))
+    phase = np.where(h["col"] > rows, np.exp(1j * t), np.where(h["col"] < rows, np.exp(-1j * t), 1))
+    return {"n": h["n"], "row_ptr": h["row_ptr"], "col": h["col"], "val": v * phase}
+
+
+
 def sweep(ctx, R, V, W, init):
     import torch
     dV, dW = ctx.new_block(R), ctx.new_block(R)
@@ -141,13 +151,7 @@ def test_staged_fp64_sweep_matches_register_path(kpm, R, form):
 def test_staged_fp64_moments_match_oracle(kpm, orc, R, form):
     h = ham.ti_hamiltonian(6, 7, 5, gamma=1.5, seed=4)
     if form == "general":
-        # a Peierls-like phase on every hopping (e^{i t} above the diagonal,
-        # e^{-i t} below: still Hermitian) makes the entries general
-        v = np.asarray(h["val"], dtype=np.complex128)
-        rows = np.repeat(np.arange(h["n"]), np.diff(h["row_ptr"]))
-        phase = np.where(h["col"] > rows, np.exp(0.3j), np.where(h["col"] < rows, np.exp(-0.3j), 1))
-        v = v * phase
-        h = {"n": h["n"], "row_ptr": h["row_ptr"], "col": h["col"], "val": v}
+        h = peierls(h)
     a, b = scaled(h, kpm)
     M = 64
     cols = [0, R // 2, R - 1]
@@ -177,3 +181,34 @@ def test_staged_fp64_ragged_half_and_general(kpm, orc):
                     assert ctx.get_launch(R)["stages"] >= 1
                     eta = ctx.moments(M, R, 5)
                 check_eta_fp64(eta, ref)
+
+
+@pytest.mark.parametrize("form", ["half", "general"])
+def test_staged_fp64_many_chunks_per_block(kpm, orc, form):
+    """16^3 lattice: 512 chunks of 32 rows over at most 456 blocks, so blocks
+    take several chunks and the old W of a block's next chunk is read while
+    it works on the current one."""
+    h = ham.ti_hamiltonian(16, 16, 16, gamma=1.0, seed=6)
+    if form == "general":
+        h = peierls(h)
+    a, b = scaled(h, kpm)
+    for R in (8, 32):
+        g = np.random.default_rng(R)
+        V = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+        W = g.standard_normal((h["n"], R)) + 1j * g.standard_normal((h["n"], R))
+        with kpm.create(h, a, b) as ctx:
+            assert ctx.info()["half_complex"] == (1 if form == "half" else 0)
+            l = ctx.get_launch(R)
+            assert l["stages"] == 2
+            assert ctx.info()["n_chunks"] > l["blocks_per_sm"] * 152  # blocks take 2 or more
+            Ws, es = sweep(ctx, R, V, W, False)
+            ctx.set_launch(R, R, 1, 256)  # register path
+            Wr, er = sweep(ctx, R, V, W, False)
+        np.testing.assert_allclose(Ws, Wr, rtol=0, atol=1e-13 * np.abs(Wr).max())
+        np.testing.assert_allclose(es, er, rtol=0, atol=1e-12 * er[0].max())
+    M, R = 48, 32
+    cols = [0, 17, 31]
+    ref, _ = orc.moments(h, a, b, M, 3, cols)
+    with kpm.create(h, a, b) as ctx:
+        eta = ctx.moments(M, R, 3)
+    check_eta_fp64(eta[cols], ref)
