@@ -25,6 +25,7 @@ import hashlib
 import io
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -47,11 +48,28 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "aug_spmmv_traffic.txt")
 # the sources of each form's sweep kernel (the staged kernel in both forms
-# at the bench's widths)
+# at the bench's widths): the kernel files and, of kpm_internal.h, the
+# device-side interface (error codes, producer records, StagedProblem,
+# StagedParams); comments and blank lines do not count
 KERNEL_SOURCES = {
     "fp64": ("aug_spmmv.cuh", "aug_spmmv_staged.cu", "kpm_internal.h"),
     "fp32": ("aug_spmmv.cuh", "aug_spmmv_staged.cu", "kpm_internal.h"),
 }
+INTERFACE_BEGIN = "#define KPM_DEVERR_TIMEOUT"
+INTERFACE_END = "// The shared-memory layout of a staged launch"
+
+
+def kernel_hash(form):
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES[form]:
+        text = open(os.path.join(ROOT, "paper_1410_5242_gb300", "csrc", f)).read()
+        if f == "kpm_internal.h":
+            text = text[text.index(INTERFACE_BEGIN):text.index(INTERFACE_END)]
+        for line in text.splitlines():
+            code = re.sub(r"//.*", "", line).rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:12]
 
 
 def kernel_name(prec, launch, half=False):
@@ -62,13 +80,6 @@ def kernel_name(prec, launch, half=False):
             real, launch["lanes_per_row"], launch["cols_per_lane"],
             "true" if half else "false", launch["stages"])
     return "aug_spmmv_kernel<%s,%d,%d>" % (real, launch["lanes_per_row"], launch["cols_per_lane"])
-
-
-def kernel_hash(form):
-    h = hashlib.sha1()
-    for f in KERNEL_SOURCES[form]:
-        h.update(open(os.path.join(ROOT, "paper_1410_5242_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:12]
 
 
 def measured_traffic(form):
@@ -336,6 +347,11 @@ def bench_ours(args, world, rank, local):
     if not args.skip_ensemble:
         ens = ensemble_rate(kpm, dev, args, stream, world, hbm_peak)
 
+    # ---------------- A(k, E) through the device-built Bloch waves
+    spectral = None
+    if not args.skip_spectral:
+        spectral = spectral_rate(kpm, ctx, h["dims"], n, nnz, stream)
+
     # ---------------- end to end through the host-buffer C calls
     e2e = None
     if not args.skip_e2e:
@@ -404,6 +420,7 @@ def bench_ours(args, world, rank, local):
         "r_sweep": r_sweep,
         "ablation": ablation,
         "ensemble": ens,
+        "spectral_function": spectral,
         "e2e": e2e,
         "gpu_launches": launches * world,
         "clocks": clock_info,
@@ -572,6 +589,35 @@ def e2e_rate(kpm, h, a, b, cfg, M, R, seed, dev, steps, world):
             "steps": steps, "ms_per_step": round(t * 1e3, 1)}
 
 
+def spectral_rate(kpm, ctx, dims, n, nnz, stream):
+    """A(k, E) along a path of 8 Bloch vectors (Gamma -> X -> M -> R of the
+    cubic lattice), 4 orbitals each (R = 32), M = 512, through
+    kpm_moments_plane_wave with host output: start waves built on the
+    device, CUDA events around each call."""
+    import torch
+    L = np.asarray(dims, dtype=np.float64)
+    path = [(0, 0, 0), (0.25, 0, 0), (0.5, 0, 0), (0.5, 0.25, 0), (0.5, 0.5, 0),
+            (0.5, 0.5, 0.25), (0.5, 0.5, 0.5), (0.25, 0.25, 0.25)]
+    q = np.repeat(np.round(np.asarray(path) * L) / L, 4, axis=0)  # on the Bloch grid
+    orb = np.tile(np.arange(4), len(path))
+    M, R = 512, q.shape[0]
+    ctx.moments_plane_wave(M, dims, 4, q, orb, stream=stream)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = 3
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(runs):
+        eta = ctx.moments_plane_wave(M, dims, 4, q, orb, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / runs
+    mu0 = float(kpm.eta_to_mu(eta[:4])[0])
+    return {"workload": "A(k,E) at 8 Bloch vectors x 4 orbitals (R = %d) of the 64^3 lattice, "
+                        "M = %d, complex double" % (R, M),
+            "value": round(run_bytes(n, nnz, R, M, 16) / t / 1e9, 1), "unit": "GB/s",
+            "ms_per_run": round(t * 1e3, 2), "mu0_gamma": mu0}
+
+
 def cpu_baseline(h, a, b, cfg):
     cores = os.cpu_count() or 1
     cols = list(range(min(cores, cfg["R"])))
@@ -690,6 +736,7 @@ def main():
     ap.add_argument("--skip-ensemble", action="store_true")
     ap.add_argument("--skip-r-sweep", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
+    ap.add_argument("--skip-spectral", action="store_true")
     ap.add_argument("--ensemble-runs", type=int, default=1)
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")

@@ -235,6 +235,32 @@ int kpm_moments(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta,
 int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, double *eta,
                    double *eta_imag, void *stream);
 
+/* Local and momentum-resolved quantities (Sec. "Application Scenario": the
+ * local DOS and the spectral function A(k, E) of Fig. 2): the same moments
+ * as kpm_moments from start vectors built on the device, so no n x R block
+ * crosses the bus.  Output, synchronisation and M as in kpm_moments.
+ *
+ * kpm_moments_local: vector r is the unit vector of original row rows[r]
+ * (host int64[R]); its moments are those of the local DOS of that row,
+ * <e_i|T_n(H~)|e_i> after kpm_eta_to_mu (summing a site's orbitals with
+ * kpm_eta_to_mu over their R rows gives the site's LDOS).  KPM_EINVAL for a
+ * row outside [0, n).
+ *
+ * kpm_moments_plane_wave: for a lattice of nx*ny*nz sites with norb
+ * orbitals per site, original row i = norb*(x + nx*(y + ny*z)) + alpha (the
+ * numbering of the Hamiltonian of Eq. 1), vector r is the Bloch wave
+ * exp(2 pi i q_r . (x, y, z)) / sqrt(nx*ny*nz) on orbital orb[r] of every
+ * site (q host double[R][3], the wave vector k = 2 pi q per lattice
+ * spacing; orb host int32[R]).  Its moments after kpm_eta_to_mu are those of
+ * A(k, E) restricted to that orbital; kpm_eta_to_mu over the norb vectors of
+ * one q gives A(k, E) / norb.  KPM_EINVAL unless nx*ny*nz*norb = n,
+ * 0 <= orb[r] < norb and q is finite. */
+int kpm_moments_local(kpm_ctx *ctx, int32_t M, int32_t R, const int64_t *rows, double *eta,
+                      double *eta_imag, void *stream);
+int kpm_moments_plane_wave(kpm_ctx *ctx, int32_t M, int32_t R, int32_t nx, int32_t ny, int32_t nz,
+                           int32_t norb, const double *q, const int32_t *orb, double *eta,
+                           double *eta_imag, void *stream);
+
 /* Ensemble: count independent problems (each its own context, all on the
  * same device and of the same precision), problem p with M[p] moments
  * (even, >= 2), R[p] random-phase vectors from seed[p] (R[p] a power of two

@@ -64,6 +64,59 @@ __global__ void phases_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n
     }
 }
 
+// Start block of basis vectors (local quantities, Sec. "Application
+// Scenario"): column r is the unit vector of original row rows[r].
+template <typename Real>
+__global__ void basis_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n_pad, int R,
+                             int ld, const int64_t *rows)
+{
+    const int64_t total = n_pad * ld;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = idx / ld;
+        const int r = (int)(idx - p * ld);
+        const bool one = p < n && r < R && (int64_t)perm[p] == rows[r];
+        V[2 * idx] = one ? Real(1) : Real(0);
+        V[2 * idx + 1] = Real(0);
+    }
+}
+
+// Start block of Bloch plane waves (momentum-resolved quantities, A(k, E)):
+// on a lattice of nx*ny*nz sites with norb orbitals per site, original row
+// i = norb*(x + nx*(y + ny*z)) + alpha; column r is
+// exp(2 pi i q_r . (x, y, z)) / sqrt(sites) on orbital orb[r] of every site
+// and zero on the others (k = 2 pi q in units of the inverse lattice
+// spacing).  The phase's fraction of a turn is reduced to [0, 1) before
+// sincospi.
+template <typename Real>
+__global__ void plane_wave_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n_pad, int R,
+                                  int ld, const double *q, const int32_t *orb, int nx, int ny,
+                                  int norb, double scale)
+{
+    const int64_t total = n_pad * ld;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = idx / ld;
+        const int r = (int)(idx - p * ld);
+        double re = 0.0, im = 0.0;
+        if (p < n && r < R) {
+            const int64_t i = perm[p];
+            const int64_t site = i / norb;
+            if ((int)(i - site * norb) == orb[r]) {
+                const int64_t x = site % nx, y = (site / nx) % ny, z = site / ((int64_t)nx * ny);
+                double f = q[3 * r] * (double)x + q[3 * r + 1] * (double)y + q[3 * r + 2] * (double)z;
+                f -= floor(f);
+                double sn, cs;
+                sincospi(2.0 * f, &sn, &cs);
+                re = scale * cs;
+                im = scale * sn;
+            }
+        }
+        V[2 * idx] = (Real)re;
+        V[2 * idx + 1] = (Real)im;
+    }
+}
+
 // Sum the per-block partials of `slots` consecutive sweeps in block order.
 // partial: [slots][G][3][RB] (slot stride `slot_stride` doubles).  Sweep
 // m = m0 + s writes eta[(col0 + r) * M + 2m] = <V|V>,
@@ -287,6 +340,16 @@ int ensure_eta(kpm_ctx *c, int64_t doubles)
     c->d_eta_im = (double *)dev_alloc(c, doubles * sizeof(double));
     c->eta_doubles = (c->d_eta && c->d_eta_im) ? doubles : 0;
     return c->eta_doubles ? KPM_OK : KPM_ENOMEM;
+}
+
+int ensure_aux(kpm_ctx *c, int64_t bytes)
+{
+    if (bytes <= c->aux_bytes)
+        return KPM_OK;
+    dev_free(c, c->d_aux);
+    c->d_aux = dev_alloc(c, bytes);
+    c->aux_bytes = c->d_aux ? bytes : 0;
+    return c->d_aux ? KPM_OK : KPM_ENOMEM;
 }
 
 }  // namespace kpm
@@ -717,6 +780,7 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_eta_im);
     dev_free(c, c->d_lidx);
     dev_free(c, c->d_val_half);
+    dev_free(c, c->d_aux);
     dev_free(c, c->d_rec);
     dev_free(c, c->d_ovf);
     dev_free(c, c->d_err);
@@ -926,6 +990,76 @@ int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double
         KPM_TRY(autotune_shapes(c, R, 5, st));
     KPM_TRY(ensure_vectors(c, R));
     KPM_TRY(upload_block(c, R, v0_ri, c->d_V, st));
+    KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
+    return moments_to_host(c, M, R, eta, eta_imag, st);
+}
+
+int kpm_moments_local(kpm_ctx *c, int32_t M, int32_t R, const int64_t *rows, double *eta,
+                      double *eta_imag, void *stream)
+{
+    if (!c || M < 2 || (M & 1) || R < 1 || !eta || !rows)
+        return KPM_EINVAL;
+    for (int32_t r = 0; r < R; r++)
+        if (rows[r] < 0 || rows[r] >= c->n)
+            return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    KPM_TRY(ensure_aux(c, (int64_t)R * sizeof(int64_t)));
+    if (c->autotune && !c->tuned.count(R))
+        KPM_TRY(autotune_shapes(c, R, 5, st));
+    KPM_TRY(ensure_vectors(c, R));
+    KPM_CUDA(cudaMemcpyAsync(c->d_aux, rows, R * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    const int ld = (int)block_ld(c, R);
+    c->launches++;
+    if (c->precision == KPM_PREC_FP64)
+        basis_kernel<double><<<c->n_sm * 8, 256, 0, st>>>((double *)c->d_V, c->d_perm, c->n,
+                                                          c->n_pad, R, ld, (const int64_t *)c->d_aux);
+    else
+        basis_kernel<float><<<c->n_sm * 8, 256, 0, st>>>((float *)c->d_V, c->d_perm, c->n,
+                                                         c->n_pad, R, ld, (const int64_t *)c->d_aux);
+    KPM_CUDA(cudaGetLastError());
+    KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
+    return moments_to_host(c, M, R, eta, eta_imag, st);
+}
+
+int kpm_moments_plane_wave(kpm_ctx *c, int32_t M, int32_t R, int32_t nx, int32_t ny, int32_t nz,
+                           int32_t norb, const double *q, const int32_t *orb, double *eta,
+                           double *eta_imag, void *stream)
+{
+    if (!c || M < 2 || (M & 1) || R < 1 || !eta || !q || !orb || nx < 1 || ny < 1 || nz < 1 ||
+        norb < 1 || (int64_t)nx * ny * nz * norb != c->n)
+        return KPM_EINVAL;
+    for (int32_t r = 0; r < R; r++) {
+        if (orb[r] < 0 || orb[r] >= norb)
+            return KPM_EINVAL;
+        for (int j = 0; j < 3; j++)
+            if (!std::isfinite(q[3 * r + j]))
+                return KPM_EINVAL;
+    }
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    KPM_TRY(ensure_eta(c, (int64_t)M * R));
+    const int64_t qbytes = ((int64_t)R * 3 * sizeof(double) + 15) / 16 * 16;
+    KPM_TRY(ensure_aux(c, qbytes + (int64_t)R * sizeof(int32_t)));
+    if (c->autotune && !c->tuned.count(R))
+        KPM_TRY(autotune_shapes(c, R, 5, st));
+    KPM_TRY(ensure_vectors(c, R));
+    char *aux = (char *)c->d_aux;
+    KPM_CUDA(cudaMemcpyAsync(aux, q, R * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    KPM_CUDA(cudaMemcpyAsync(aux + qbytes, orb, R * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int ld = (int)block_ld(c, R);
+    const double scale = 1.0 / std::sqrt((double)nx * ny * nz);
+    c->launches++;
+    if (c->precision == KPM_PREC_FP64)
+        plane_wave_kernel<double><<<c->n_sm * 8, 256, 0, st>>>(
+            (double *)c->d_V, c->d_perm, c->n, c->n_pad, R, ld, (const double *)aux,
+            (const int32_t *)(aux + qbytes), nx, ny, norb, scale);
+    else
+        plane_wave_kernel<float><<<c->n_sm * 8, 256, 0, st>>>(
+            (float *)c->d_V, c->d_perm, c->n, c->n_pad, R, ld, (const double *)aux,
+            (const int32_t *)(aux + qbytes), nx, ny, norb, scale);
+    KPM_CUDA(cudaGetLastError());
     KPM_TRY(run_schedule(c, M, R, c->d_eta, eta_imag ? c->d_eta_im : nullptr, st));
     return moments_to_host(c, M, R, eta, eta_imag, st);
 }

@@ -54,7 +54,8 @@ struct StagedProblem {
     const int2 *rec;       // [n_tiles][KPM_REC_WORDS]
     const int2 *ovf;       // runs beyond the inline ones
     const uint16_t *lidx;  // [n_stored] local positions (SELL order)
-    const void *val;       // [n_stored] complex float values (SELL order)
+    const void *val;       // [n_stored] values (SELL order): complex float or double,
+                           // or the half-complex form's operand pairs
     void *buf[2];          // vector blocks: V = buf[parity], W = buf[parity ^ 1]
     double *partial;
     int64_t tile0, n_tiles;
@@ -207,6 +208,8 @@ struct kpm_ctx {
     double *d_partial = nullptr;
     int64_t partial_doubles = 0;
     double *d_eta = nullptr, *d_eta_im = nullptr;
+    void *d_aux = nullptr;  // small per-call inputs of the start-block kernels
+    int64_t aux_bytes = 0;
     int64_t eta_doubles = 0;
 
     std::map<int, kpm::LaunchShape> shapes;  // per column-block width
@@ -225,6 +228,7 @@ int64_t block_ld(const kpm_ctx *c, int R);
 int ensure_vectors(kpm_ctx *c, int R);
 int ensure_partial(kpm_ctx *c, int64_t doubles);
 int ensure_eta(kpm_ctx *c, int64_t doubles);
+int ensure_aux(kpm_ctx *c, int64_t bytes);
 int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st);
 // Random-phase block without a context: perm may be NULL (identity).
 int launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, int64_t n_pad, int R,

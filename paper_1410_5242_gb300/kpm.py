@@ -100,6 +100,9 @@ _SIGS = {
     "kpm_destroy": (None, [_vp]),
     "kpm_moments": (_int, [_vp, _i32, _i32, _u64, _pd, _pd, _vp]),
     "kpm_moments_v0": (_int, [_vp, _i32, _i32, _pd, _pd, _pd, _vp]),
+    "kpm_moments_local": (_int, [_vp, _i32, _i32, _pi64, _pd, _pd, _vp]),
+    "kpm_moments_plane_wave": (_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _pd, _pi32, _pd,
+                                      _pd, _vp]),
     "kpm_moments_batch": (_int, [ctypes.POINTER(_vp), _i32, _pi32, _pi32,
                                  ctypes.POINTER(_u64), ctypes.POINTER(_pd), _vp]),
     "kpm_get_info": (_int, [_vp, ctypes.POINTER(Info)]),
@@ -398,6 +401,34 @@ class Context:
         _check(lib.kpm_moments_v0(self.handle, M, R, _p(v0.view(np.float64), _d), _p(eta, _d),
                                   _p(eti, _d) if imag else None, _stream_ptr(stream)),
                "kpm_moments_v0")
+        return (eta, eti) if imag else eta
+
+    def moments_local(self, M, rows, imag=False, stream=None):
+        """kpm_moments_local: eta[R][M] of the unit vectors of `rows`."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        R = rows.size
+        eta = np.empty((R, M))
+        eti = np.empty((R, M)) if imag else None
+        _check(lib.kpm_moments_local(self.handle, M, R, _p(rows, _i64), _p(eta, _d),
+                                     _p(eti, _d) if imag else None, _stream_ptr(stream)),
+               "kpm_moments_local")
+        return (eta, eti) if imag else eta
+
+    def moments_plane_wave(self, M, dims, norb, q, orb, imag=False, stream=None):
+        """kpm_moments_plane_wave: eta[R][M] of the Bloch waves with wave
+        vectors 2 pi q[r] (q: R x 3) on orbitals orb[r] of a dims lattice."""
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 3)
+        orb = np.ascontiguousarray(orb, dtype=np.int32)
+        R = q.shape[0]
+        if orb.size != R:
+            raise ValueError("one orbital per wave vector")
+        eta = np.empty((R, M))
+        eti = np.empty((R, M)) if imag else None
+        nx, ny, nz = (int(d) for d in dims)
+        _check(lib.kpm_moments_plane_wave(self.handle, M, R, nx, ny, nz, int(norb), _p(q, _d),
+                                          _p(orb, _i32), _p(eta, _d),
+                                          _p(eti, _d) if imag else None, _stream_ptr(stream)),
+               "kpm_moments_plane_wave")
         return (eta, eti) if imag else eta
 
     # -- device-buffer calls (torch tensors)

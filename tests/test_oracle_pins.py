@@ -289,3 +289,67 @@ def test_pins_reject_transposed_operand_and_sign_flip(orc):
     assert np.max(np.abs(transposed - want)) > 1e-6 * want[0]
     flipped, _ = orc.kpm_vector(h, a, -b, M, r)
     assert np.max(np.abs(flipped - want)) > 1e-6 * want[0]
+
+
+# ------------------------------------------ local and momentum-resolved
+def bloch_matrix(q, v=0.0, t=1.0):
+    """4x4 Bloch Hamiltonian H(k) of the clean lattice of Eq. 1 at k = 2 pi q:
+    the on-site block v + 2 Gamma^1 plus every hopping block times
+    exp(i k . d) (a Bloch wave on orbital b is mapped into the span of the
+    four Bloch waves of the same k)."""
+    g1 = ham.dirac_matrices()[1]
+    hk = v * np.eye(4) + 2.0 * g1
+    for d, blk in ham.ti_blocks(t).items():
+        hk = hk + blk * np.exp(2j * np.pi * np.dot(q, d))
+    return hk
+
+
+def matrix_cheb_diag(hk, a, b, M):
+    """[T_n(a (H(k) - b))]_{alpha alpha}, n < M, from the 4x4 eigendecomposition."""
+    lam, U = np.linalg.eigh(hk)
+    x = a * (lam - b)
+    w = np.abs(U) ** 2  # w[alpha, band]
+    return np.array([w @ cheb(n, x) for n in range(M)])  # [M][4]
+
+
+def test_plane_wave_moments_bloch_closed_form(orc):
+    # a Bloch wave of the clean lattice on orbital alpha: its moments are the
+    # diagonal entries of T_n of the 4x4 Bloch matrix (the A(k, E) of Fig. 2
+    # restricted to one orbital)
+    dims, v = (4, 5, 3), 0.2
+    h = ham.ti_hamiltonian(*dims, potential=np.full(int(np.prod(dims)), v))
+    a, b = orc.scale_from_bounds(*orc.gershgorin(h), 0.01)
+    M = 48
+    qs = np.array([[0, 0, 0], [1 / 4, 2 / 5, 1 / 3], [3 / 4, 1 / 5, 2 / 3], [1 / 2, 3 / 5, 0]])
+    for q in qs:
+        er, _ = orc.moments_v0(h, a, b, M, vectors.plane_wave_block(dims, 4, [q] * 4, range(4)))
+        want = matrix_cheb_diag(bloch_matrix(q, v), a, b, M)
+        for alpha in range(4):
+            mu = orc.eta_to_mu(er[alpha:alpha + 1])
+            np.testing.assert_allclose(mu, want[:, alpha], rtol=0, atol=1e-12)
+
+
+def test_ldos_clean_lattice_equals_bloch_dos(orc):
+    # translation invariance: every site's local DOS (its four orbitals) is
+    # the DOS of the clean lattice
+    dims, v = (4, 3, 5), -0.4
+    h = ham.ti_hamiltonian(*dims, potential=np.full(int(np.prod(dims)), v))
+    a, b = orc.scale_from_bounds(*orc.gershgorin(h), 0.01)
+    M = 40
+    E = bloch_spectrum(*dims, v=v)
+    want = np.array([np.mean(cheb(k, a * (E - b))) for k in range(M)])
+    for site in (0, 7, 59):
+        er, _ = orc.moments_v0(h, a, b, M, vectors.rows_block(h["n"], range(4 * site, 4 * site + 4)))
+        np.testing.assert_allclose(orc.eta_to_mu(er), want, rtol=0, atol=1e-12)
+
+
+def test_ldos_diagonal_matrix_is_scalar_chebyshev(orc):
+    lam = np.linspace(-2.5, 3.0, 23)
+    h = ham.diagonal_matrix(lam)
+    a, b = orc.scale_from_bounds(*orc.gershgorin(h), 0.01)
+    M = 32
+    rows = [0, 5, 22]
+    er, _ = orc.moments_v0(h, a, b, M, vectors.rows_block(h["n"], rows))
+    for k, i in enumerate(rows):
+        np.testing.assert_allclose(orc.eta_to_mu(er[k:k + 1]),
+                                   [cheb(n, a * (lam[i] - b)) for n in range(M)], rtol=0, atol=1e-13)
