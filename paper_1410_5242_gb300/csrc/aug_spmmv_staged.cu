@@ -1,5 +1,6 @@
 // The aug_spmmv sweep of Fig. 5 with the gathered V rows staged in shared
-// memory by the bulk-copy (TMA) engine, for complex float storage.
+// memory by the bulk-copy (TMA) engine, for complex float and complex double
+// storage.
 //
 // Why: in the register-path kernel every entry's gather of R complex values
 // is a load into registers, so the bytes a streaming multiprocessor can
@@ -26,11 +27,15 @@
 // tile sequence moves on to the next problem.  A single problem is a table
 // of one.
 //
-// Lane/column ownership is that of aug_spmmv.cuh; the products are
-// accumulated with paired FMAs (real and imaginary parts of h times a column
-// in two packed sums), so W agrees with the register path to
+// Lane/column ownership is that of aug_spmmv.cuh.  Complex float: the
+// products are accumulated with paired FMAs (real and imaginary parts of h
+// times a column in two packed sums), so W agrees with the register path to
 // single-precision rounding, and eta (packed 8-row partials folded into
-// TwoSum pairs, StagedEta) is reproducible run to run.
+// TwoSum pairs, StagedEta) is reproducible run to run.  Complex double: four
+// FMAs per entry and column, or two in the half-complex form (every stored
+// entry purely real or purely imaginary: the host stores operand pairs and
+// marks imaginary entries in bit 15 of the local index), the FP64 pipe
+// being this form's bound on GB300; eta in plain FMA chains (StagedEta64).
 //
 // Every wait is bounded (about two seconds of SM clock): on expiry the
 // thread records KPM_DEVERR_TIMEOUT in *err, raises the block's abort flag
