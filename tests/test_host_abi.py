@@ -332,3 +332,21 @@ def test_gather_build_rejects_small_chunks(kpm):
     with pytest.raises(kpm.KPMError) as e:
         kpm.gather_build(h, 0.1, 0.0, C=4, sigma=1)
     assert e.value.status == kpm.KPM_EINVAL
+
+
+def test_local_and_plane_wave_calls_reject_missing_arguments(kpm):
+    # argument checks that need no context run before any device call
+    import ctypes
+    import numpy as np
+    eta = np.empty(16)
+    rows = np.zeros(2, dtype=np.int64)
+    q = np.zeros(6)
+    orb = np.zeros(2, dtype=np.int32)
+    pd = eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    lib = kpm.lib
+    assert lib.kpm_moments_local(None, 8, 2, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 pd, None, None) == kpm.KPM_EINVAL
+    assert lib.kpm_moments_plane_wave(None, 8, 2, 2, 2, 2, 4,
+                                      q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), pd, None,
+                                      None) == kpm.KPM_EINVAL
