@@ -82,9 +82,10 @@ def kernel_name(prec, launch, half=False):
     return "aug_spmmv_kernel<%s,%d,%d>" % (real, launch["lanes_per_row"], launch["cols_per_lane"])
 
 
-def measured_traffic(form):
-    """DRAM bytes per launch of the form's sweep kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+def measured_counter(form, name):
+    """A per-launch counter of the form's sweep kernel from the committed ncu
+    summary (profiles/aug_spmmv_traffic.txt), if it was taken on the current
+    kernel sources (else None)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     vals = {}
@@ -94,8 +95,13 @@ def measured_traffic(form):
             vals[parts[0]] = parts[1]
     if vals.get(form + "_kernel_hash") != kernel_hash(form):
         return None
-    v = vals.get(form + "_dram_bytes_per_launch")
+    v = vals.get(form + "_" + name)
     return float(v) if v is not None else None
+
+
+def measured_traffic(form):
+    """DRAM bytes (read + write) per launch of the form's sweep kernel."""
+    return measured_counter(form, "dram_bytes_per_launch")
 
 
 def peaks():
@@ -393,6 +399,10 @@ def bench_ours(args, world, rank, local):
             "bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
             "traffic": traffic,
+            # the FP64 pipe's busy fraction in the same ncu capture (the flop
+            # count above leaves out the old-W subtraction and the 1/2 of the
+            # initial sweep)
+            "fp64_pipe_active_ncu": measured_counter("fp64", "fp64_pipe_active"),
             "kernel": kernel_name("fp64", launch_shape, half),
             "half_complex": half,
             "avg_launch_ms": round(t_k * 1e3, 4),
