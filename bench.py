@@ -592,8 +592,7 @@ def e2e_rate(kpm, h, a, b, cfg, M, R, seed, dev, steps, world):
     torch.cuda.synchronize()
     t = (time.perf_counter() - t0) / steps
     t = max_over_ranks(t, world)
-    nch = info["n_chunks"]
-    h2d = info["matrix_bytes"] + 8 * (nch + 1) + 4 * nch + 4 * info["n_pad"]
+    h2d = info["upload_bytes"]
     return {"value": round(world * run_bytes(h["n"], info["nnz"], R, M, 16) / t / 1e9, 2),
             "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(M * R * 8),
             "steps": steps, "ms_per_step": round(t * 1e3, 1)}

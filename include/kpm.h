@@ -321,6 +321,8 @@ typedef struct kpm_info {
     int32_t gather_lists;    /* 1: the staged kernel's gather lists were built */
     int32_t half_complex;    /* 1: complex double, every stored entry purely real or
                                 purely imaginary (the staged kernel's two-FMA form) */
+    int64_t upload_bytes;    /* host -> device bytes kpm_create copied (matrix, indices,
+                                gather lists and records, half-complex operands) */
 } kpm_info;
 
 int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);

@@ -660,6 +660,9 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
             cudaSuccess)
             return fail(KPM_ECUDA);
     }
+    c->upload_bytes = (int64_t)sizeof(int64_t) * (sell.n_chunks + 1) +
+                      (int64_t)sizeof(int32_t) * (sell.n_chunks + sell.n_stored + sell.n_pad) +
+                      (int64_t)c->sdc * sell.n_stored;
     // complex double with every stored entry purely real or purely
     // imaginary: the staged kernel's two-FMA form
     bool half = c->precision == KPM_PREC_FP64;
@@ -730,6 +733,7 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                     kpm_gather_release(&g);
                     return fail(KPM_ECUDA);
                 }
+                c->upload_bytes += 16 * sell.n_stored;
             }
             c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sell.n_stored);
             c->d_rec = (int2 *)dev_alloc(c, sizeof(int2) * rec.size());
@@ -750,6 +754,8 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                 return fail(alloc_ok ? KPM_ECUDA : KPM_ENOMEM);
             c->gather_ok = true;
             c->half_ok = half;
+            c->upload_bytes += (int64_t)sizeof(uint16_t) * sell.n_stored +
+                               (int64_t)sizeof(int2) * (int64_t)(rec.size() + ovf.size());
             // complex double: the staged kernel's widest block is 32 columns
             // (wider rows would leave room for one stage only), and two
             // 32-wide staged sweeps beat one 64-wide register-path sweep
@@ -826,6 +832,7 @@ int kpm_get_info(const kpm_ctx *c, kpm_info *out)
     out->matrix_bytes = c->n_stored * ((int64_t)c->sdc + 4);
     out->gather_lists = c->gather_ok ? 1 : 0;
     out->half_complex = c->half_ok ? 1 : 0;
+    out->upload_bytes = c->upload_bytes;
     out->kernel_launches = c->launches;
     return KPM_OK;
 }

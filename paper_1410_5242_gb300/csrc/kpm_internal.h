@@ -194,6 +194,7 @@ struct kpm_ctx {
     // array and bit 15 of d_lidx marking the imaginary entries)
     bool half_ok = false;
     void *d_val_half = nullptr;  // [n_stored] (a, b) operand pairs
+    int64_t upload_bytes = 0;    // host -> device bytes kpm_create copied
     uint16_t *d_lidx = nullptr;  // [n_stored] local positions (SELL order)
     int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;

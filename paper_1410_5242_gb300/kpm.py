@@ -53,7 +53,7 @@ class Info(ctypes.Structure):
                 ("sigma", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("matrix_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("gather_lists", ctypes.c_int32),
-                ("half_complex", ctypes.c_int32)]
+                ("half_complex", ctypes.c_int32), ("upload_bytes", ctypes.c_int64)]
 
 
 class BatchInfo(ctypes.Structure):
