@@ -45,7 +45,7 @@ def _compile(src, extra):
         cmd = [nvcc, ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                "-I" + INCLUDE, "-I" + CSRC, "-c", path, "-o", obj] + extra
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I" + INCLUDE, "-I" + CSRC,
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I" + INCLUDE, "-I" + CSRC,
                "-I" + os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include"),
                "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,7 +68,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
     tmp = LIB + ".%d.tmp" % os.getpid()
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "lib64")
     cmd = [_nvcc(), ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results] + \
-        ["-L" + cuda_lib, "-lcusparse", "-lcublas", "-Xlinker", "-rpath=" + cuda_lib]
+        ["-L" + cuda_lib, "-lcusparse", "-lcublas", "-lpthread", "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("linking libkpm.so failed:\n%s" % r.stderr)

@@ -2,15 +2,69 @@
 // rescaling, the CSR -> SELL-C-sigma converter, and the reconstruction
 // eta -> mu -> Jackson DOS.  None of these needs a GPU.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "kpm_internal.h"
 
 namespace kpm {
+
+// Host threads for the conversions of large inputs: KPM_HOST_THREADS if set
+// (>= 1), else the hardware concurrency, at most 64.
+int host_threads()
+{
+    const char *env = std::getenv("KPM_HOST_THREADS");
+    if (env && *env) {
+        const long v = std::strtol(env, nullptr, 10);
+        if (v >= 1)
+            return (int)std::min<long>(v, 64);
+    }
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw ? (int)std::min<unsigned>(hw, 64) : 1;
+}
+
+// Calls f(begin, end, part) on contiguous parts of [0, n), part p covering
+// the p-th range in order, on up to host_threads() threads with at least
+// `grain` items each; the calling thread takes part 0.  Returns the number
+// of parts.  If a thread cannot be started its part runs on the caller.
+template <typename F>
+int parallel_parts(int64_t n, int64_t grain, F &&f)
+{
+    const int64_t want = grain > 0 ? (n + grain - 1) / grain : 1;
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), want));
+    auto range = [&](int p, int64_t &b, int64_t &e) {
+        b = n * p / parts;
+        e = n * (p + 1) / parts;
+    };
+    std::vector<std::thread> pool;
+    std::vector<int> inline_parts;
+    for (int p = 1; p < parts; p++) {
+        int64_t b, e;
+        range(p, b, e);
+        try {
+            pool.emplace_back([&f, b, e, p]() { f(b, e, p); });
+        } catch (...) {
+            inline_parts.push_back(p);
+        }
+    }
+    int64_t b0, e0;
+    range(0, b0, e0);
+    f(b0, e0, 0);
+    for (int p : inline_parts) {
+        int64_t b, e;
+        range(p, b, e);
+        f(b, e, p);
+    }
+    for (std::thread &t : pool)
+        t.join();
+    return parts;
+}
 
 int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri)
 {
@@ -18,24 +72,41 @@ int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
         return KPM_EINVAL;
     if (row_ptr[0] != 0)
         return KPM_EINVAL;
-    for (int64_t i = 0; i < n; i++)
-        if (row_ptr[i + 1] < row_ptr[i])
-            return KPM_EINVAL;
+    std::atomic<bool> bad(false);
+    parallel_parts(n, 1 << 16, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; i++)
+            if (row_ptr[i + 1] < row_ptr[i]) {
+                bad = true;
+                return;
+            }
+    });
+    if (bad)
+        return KPM_EINVAL;
     const int64_t nnz = row_ptr[n];
     if (nnz > 0 && (!col || !val_ri))
         return KPM_EINVAL;
-    for (int64_t i = 0; i < n; i++) {
-        int64_t prev = -1;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-            if (col[k] < 0 || col[k] >= n || col[k] <= prev)
-                return KPM_EINVAL;
-            prev = col[k];
+    parallel_parts(n, 1 << 14, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; i++) {
+            int64_t prev = -1;
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+                if (col[k] < 0 || col[k] >= n || col[k] <= prev) {
+                    bad = true;
+                    return;
+                }
+                prev = col[k];
+            }
         }
-    }
-    for (int64_t k = 0; k < 2 * nnz; k++)
-        if (!std::isfinite(val_ri[k]))
-            return KPM_EINVAL;
-    return KPM_OK;
+    });
+    if (bad)
+        return KPM_EINVAL;
+    parallel_parts(2 * nnz, 1 << 18, [&](int64_t b, int64_t e, int) {
+        for (int64_t k = b; k < e; k++)
+            if (!std::isfinite(val_ri[k])) {
+                bad = true;
+                return;
+            }
+    });
+    return bad ? KPM_EINVAL : KPM_OK;
 }
 
 int check_hermitian(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
@@ -344,12 +415,14 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
     // Fold H' = 2a (H - b 1): row lengths after adding missing diagonals.
     std::vector<int32_t> len(n);
     std::vector<uint8_t> has_diag(n, 0);
-    for (int64_t i = 0; i < n; i++) {
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++)
-            if (col[k] == i)
-                has_diag[i] = 1;
-        len[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]) + ((!has_diag[i] && b != 0.0) ? 1 : 0);
-    }
+    parallel_parts(n, 1 << 14, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t i = lo; i < hi; i++) {
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++)
+                if (col[k] == i)
+                    has_diag[i] = 1;
+            len[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]) + ((!has_diag[i] && b != 0.0) ? 1 : 0);
+        }
+    });
 
     const int64_t n_chunks = (n + C - 1) / C;
     const int64_t n_pad = n_chunks * C;
@@ -368,15 +441,23 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
         }
     }
     if (sigma > 1) {
-        for (int64_t w = 0; w < n; w += sigma) {
-            const int64_t e = std::min<int64_t>(n, w + sigma);
-            std::stable_sort(perm.begin() + w, perm.begin() + e,
-                             [&](int32_t x, int32_t y) { return len[x] > len[y]; });
-        }
+        // windows are sorted independently: split them among the threads
+        const int64_t n_win = (n + sigma - 1) / sigma;
+        parallel_parts(n_win, std::max<int64_t>(1, (1 << 14) / sigma), [&](int64_t lo, int64_t hi,
+                                                                          int) {
+            for (int64_t wi = lo; wi < hi; wi++) {
+                const int64_t w = wi * sigma;
+                const int64_t e = std::min<int64_t>(n, w + sigma);
+                std::stable_sort(perm.begin() + w, perm.begin() + e,
+                                 [&](int32_t x, int32_t y) { return len[x] > len[y]; });
+            }
+        });
     }
     std::vector<int32_t> iperm(n);
-    for (int64_t p = 0; p < n; p++)
-        iperm[perm[p]] = (int32_t)p;
+    parallel_parts(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t p = lo; p < hi; p++)
+            iperm[perm[p]] = (int32_t)p;
+    });
 
     int64_t *chunk_ptr = (int64_t *)std::malloc(sizeof(int64_t) * (n_chunks + 1));
     int32_t *chunk_len = (int32_t *)std::malloc(sizeof(int32_t) * (n_chunks ? n_chunks : 1));
@@ -386,19 +467,22 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
         return KPM_ENOMEM;
     }
     chunk_ptr[0] = 0;
-    int64_t nnz = 0;
-    for (int64_t c = 0; c < n_chunks; c++) {
-        int32_t m = 0;
-        for (int64_t r = 0; r < C; r++) {
-            const int64_t p = c * C + r;
-            if (p < n) {
-                m = std::max(m, len[perm[p]]);
-                nnz += len[perm[p]];
+    parallel_parts(n_chunks, 1 << 10, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; c++) {
+            int32_t m = 0;
+            for (int64_t r = 0; r < C; r++) {
+                const int64_t p = c * C + r;
+                if (p < n)
+                    m = std::max(m, len[perm[p]]);
             }
+            chunk_len[c] = m;
         }
-        chunk_len[c] = m;
-        chunk_ptr[c + 1] = chunk_ptr[c] + (int64_t)m * C;
-    }
+    });
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < n; i++)
+        nnz += len[i];
+    for (int64_t c = 0; c < n_chunks; c++)
+        chunk_ptr[c + 1] = chunk_ptr[c] + (int64_t)chunk_len[c] * C;
     const int64_t n_stored = chunk_ptr[n_chunks];
     int32_t *scol = (int32_t *)std::malloc(sizeof(int32_t) * (n_stored ? n_stored : 1));
     double *sval = (double *)std::malloc(sizeof(double) * 2 * (n_stored ? n_stored : 1));
@@ -408,44 +492,46 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
         return KPM_ENOMEM;
     }
     const double two_a = 2.0 * a;
-    for (int64_t c = 0; c < n_chunks; c++) {
-        const int64_t base = chunk_ptr[c];
-        const int32_t clen = chunk_len[c];
-        for (int64_t r = 0; r < C; r++) {
-            const int64_t p = c * C + r;
-            int32_t j = 0;
-            auto put = [&](int32_t newcol, double re, double im) {
-                const int64_t e = base + (int64_t)j * C + r;
-                scol[e] = newcol;
-                sval[2 * e] = re;
-                sval[2 * e + 1] = im;
-                j++;
-            };
-            if (p < n) {
-                const int64_t i = perm[p];
-                bool diag_done = has_diag[i] || b == 0.0;
-                for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-                    if (!diag_done && col[k] > i) {
-                        put((int32_t)p, -two_a * b, 0.0);
-                        diag_done = true;
+    // every chunk writes its own entries [chunk_ptr[c], chunk_ptr[c+1])
+    parallel_parts(n_chunks, 1 << 9, [&](int64_t lo_c, int64_t hi_c, int) {
+        for (int64_t c = lo_c; c < hi_c; c++) {
+            const int64_t base = chunk_ptr[c];
+            const int32_t clen = chunk_len[c];
+            for (int64_t r = 0; r < C; r++) {
+                const int64_t p = c * C + r;
+                int32_t j = 0;
+                auto put = [&](int32_t newcol, double re, double im) {
+                    const int64_t e = base + (int64_t)j * C + r;
+                    scol[e] = newcol;
+                    sval[2 * e] = re;
+                    sval[2 * e + 1] = im;
+                    j++;
+                };
+                if (p < n) {
+                    const int64_t i = perm[p];
+                    bool diag_done = has_diag[i] || b == 0.0;
+                    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+                        if (!diag_done && col[k] > i) {
+                            put((int32_t)p, -two_a * b, 0.0);
+                            diag_done = true;
+                        }
+                        double re = val_ri[2 * k], im = val_ri[2 * k + 1];
+                        if (col[k] == i)
+                            re = two_a * (re - b), im = two_a * im;
+                        else
+                            re = two_a * re, im = two_a * im;
+                        put(iperm[col[k]], re, im);
                     }
-                    double re = val_ri[2 * k], im = val_ri[2 * k + 1];
-                    if (col[k] == i)
-                        re = two_a * (re - b), im = two_a * im;
-                    else
-                        re = two_a * re, im = two_a * im;
-                    put(iperm[col[k]], re, im);
+                    if (!diag_done)
+                        put((int32_t)p, -two_a * b, 0.0);
                 }
-                if (!diag_done)
-                    put((int32_t)p, -two_a * b, 0.0);
+                // padding: zero value, the row's own index (its V row is read anyway)
+                while (j < clen)
+                    put((int32_t)p, 0.0, 0.0);
             }
-            // padding: zero value, the row's own index (its V row is read anyway)
-            while (j < clen)
-                put((int32_t)p, 0.0, 0.0);
         }
-    }
-    for (int64_t p = 0; p < n_pad; p++)
-        perm_out[p] = perm[p];
+    });
+    std::memcpy(perm_out, perm.data(), sizeof(int32_t) * n_pad);
 
     out->n = n;
     out->n_pad = n_pad;
@@ -496,64 +582,98 @@ int kpm_gather_build(const kpm_sell *s, kpm_gather *out)
         std::free(run_ptr);
         return KPM_ENOMEM;
     }
-    std::vector<int32_t> runs;
-    std::vector<int32_t> others;
-    int32_t u_max = 0, l_max = 0;
-    run_ptr[0] = 0;
-    for (int64_t c = 0; c < n_chunks; c++) {
-        const int64_t r0 = c * C;
-        const int64_t e0 = s->chunk_ptr[c];
-        const int64_t cnt = (int64_t)s->chunk_len[c] * C;
-        l_max = std::max(l_max, s->chunk_len[c]);
-        others.clear();
-        for (int64_t e = e0; e < e0 + cnt; e++) {
-            const int64_t j = s->col[e];
-            if (j < r0 || j >= r0 + C)
-                others.push_back((int32_t)j);
-        }
-        std::sort(others.begin(), others.end());
-        others.erase(std::unique(others.begin(), others.end()), others.end());
-        const int64_t u = C + (int64_t)others.size();
-        if (u > 65535) {
-            std::free(lidx);
-            std::free(run_ptr);
-            return KPM_EUNSUPPORTED;
-        }
-        u_max = std::max<int32_t>(u_max, (int32_t)u);
-        // own rows, then the others; a row that continues the last run joins it
-        runs.push_back((int32_t)r0);
-        runs.push_back((int32_t)C);
-        for (int32_t j : others) {
-            const size_t last = runs.size() - 2;
-            if ((int64_t)runs[last] + runs[last + 1] == j)
-                runs[last + 1]++;
-            else {
-                runs.push_back(j);
-                runs.push_back(1);
+    // chunks are independent: each part of the chunk range builds its runs
+    // (pairs) and per-chunk run counts, written to lidx directly; the parts'
+    // runs are then concatenated in order
+    const int max_parts = std::max(1, host_threads());
+    std::vector<std::vector<int32_t>> part_runs(max_parts);
+    std::vector<int32_t> part_umax(max_parts, 0), part_lmax(max_parts, 0);
+    std::atomic<bool> too_long(false), no_mem(false);
+    std::vector<int64_t> run_cnt(n_chunks, 0);
+    const int parts = parallel_parts(n_chunks, 1 << 9, [&](int64_t lo, int64_t hi, int part) {
+        try {
+            std::vector<int32_t> &runs = part_runs[part];
+            std::vector<int32_t> others;
+            int32_t u_max = 0, l_max = 0;
+            for (int64_t c = lo; c < hi && !too_long; c++) {
+                const int64_t r0 = c * C;
+                const int64_t e0 = s->chunk_ptr[c];
+                const int64_t cnt = (int64_t)s->chunk_len[c] * C;
+                l_max = std::max(l_max, s->chunk_len[c]);
+                others.clear();
+                for (int64_t e = e0; e < e0 + cnt; e++) {
+                    const int64_t j = s->col[e];
+                    if (j < r0 || j >= r0 + C)
+                        others.push_back((int32_t)j);
+                }
+                std::sort(others.begin(), others.end());
+                others.erase(std::unique(others.begin(), others.end()), others.end());
+                const int64_t u = C + (int64_t)others.size();
+                if (u > 65535) {
+                    too_long = true;
+                    return;
+                }
+                u_max = std::max<int32_t>(u_max, (int32_t)u);
+                // own rows, then the others; a row that continues the last run joins it
+                const size_t first = runs.size();
+                runs.push_back((int32_t)r0);
+                runs.push_back((int32_t)C);
+                for (int32_t j : others) {
+                    const size_t last = runs.size() - 2;
+                    if ((int64_t)runs[last] + runs[last + 1] == j)
+                        runs[last + 1]++;
+                    else {
+                        runs.push_back(j);
+                        runs.push_back(1);
+                    }
+                }
+                run_cnt[c] = (int64_t)(runs.size() - first) / 2;
+                for (int64_t e = e0; e < e0 + cnt; e++) {
+                    const int64_t j = s->col[e];
+                    int64_t pos;
+                    if (j >= r0 && j < r0 + C)
+                        pos = j - r0;
+                    else
+                        pos = C + (std::lower_bound(others.begin(), others.end(), (int32_t)j) -
+                                   others.begin());
+                    lidx[e] = (uint16_t)pos;
+                }
             }
+            part_umax[part] = u_max;
+            part_lmax[part] = l_max;
+        } catch (const std::bad_alloc &) {
+            no_mem = true;
         }
-        for (int64_t e = e0; e < e0 + cnt; e++) {
-            const int64_t j = s->col[e];
-            int64_t pos;
-            if (j >= r0 && j < r0 + C)
-                pos = j - r0;
-            else
-                pos = C + (std::lower_bound(others.begin(), others.end(), (int32_t)j) -
-                           others.begin());
-            lidx[e] = (uint16_t)pos;
-        }
-        run_ptr[c + 1] = (int64_t)runs.size() / 2;
+    });
+    if (too_long || no_mem) {
+        std::free(lidx);
+        std::free(run_ptr);
+        return too_long ? KPM_EUNSUPPORTED : KPM_ENOMEM;
     }
-    int32_t *runs_out = (int32_t *)std::malloc(sizeof(int32_t) * (runs.empty() ? 1 : runs.size()));
+    int32_t u_max = 0, l_max = 0;
+    size_t total = 0;
+    for (int p = 0; p < parts; p++) {
+        u_max = std::max(u_max, part_umax[p]);
+        l_max = std::max(l_max, part_lmax[p]);
+        total += part_runs[p].size();
+    }
+    run_ptr[0] = 0;
+    for (int64_t c = 0; c < n_chunks; c++)
+        run_ptr[c + 1] = run_ptr[c] + run_cnt[c];
+    int32_t *runs_out = (int32_t *)std::malloc(sizeof(int32_t) * (total ? total : 1));
     if (!runs_out) {
         std::free(lidx);
         std::free(run_ptr);
         return KPM_ENOMEM;
     }
-    if (!runs.empty())
-        std::memcpy(runs_out, runs.data(), sizeof(int32_t) * runs.size());
+    size_t at = 0;
+    for (int p = 0; p < parts; p++) {
+        if (!part_runs[p].empty())
+            std::memcpy(runs_out + at, part_runs[p].data(), sizeof(int32_t) * part_runs[p].size());
+        at += part_runs[p].size();
+    }
     out->n_chunks = n_chunks;
-    out->n_runs = (int64_t)runs.size() / 2;
+    out->n_runs = (int64_t)total / 2;
     out->u_max = u_max;
     out->l_max = l_max;
     out->lidx = lidx;

@@ -350,3 +350,45 @@ def test_local_and_plane_wave_calls_reject_missing_arguments(kpm):
                                       q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), pd, None,
                                       None) == kpm.KPM_EINVAL
+
+
+@pytest.mark.parametrize("C,sigma", [(32, 256), (8, 64)])
+def test_conversions_do_not_depend_on_the_host_thread_count(kpm, monkeypatch, C, sigma):
+    """kpm_sell_build and kpm_gather_build split rows, sorting windows and
+    chunks among host threads (KPM_HOST_THREADS caps them): the layout and
+    the gather lists must be identical for 1, 3 and 16 threads, on a lattice
+    large enough for several parts and with ragged rows (open boundaries)."""
+    h = ham.ti_hamiltonian(36, 30, 24, gamma=0.7, seed=5, periodic=(False, True, False))
+    a, b = 0.11, 0.07
+    got = []
+    for t in ("1", "3", "16"):
+        monkeypatch.setenv("KPM_HOST_THREADS", t)
+        got.append(kpm.gather_build(h, a, b, C=C, sigma=sigma))
+    (s0, g0) = got[0]
+    assert not np.array_equal(s0["perm"][:s0["n"]], np.arange(s0["n"]))  # the sort moved rows
+    for s1, g1 in got[1:]:
+        for k in ("chunk_ptr", "chunk_len", "col", "val", "perm"):
+            np.testing.assert_array_equal(s1[k], s0[k], err_msg=k)
+        assert (s1["nnz"], s1["n_stored"]) == (s0["nnz"], s0["n_stored"])
+        for k in ("lidx", "run_ptr", "runs"):
+            np.testing.assert_array_equal(g1[k], g0[k], err_msg=k)
+        assert (g1["u_max"], g1["l_max"]) == (g0["u_max"], g0["l_max"])
+
+
+def test_invalid_input_is_rejected_in_any_part(kpm, monkeypatch):
+    # errors placed near the end of large inputs, where a later thread's part
+    # finds them
+    monkeypatch.setenv("KPM_HOST_THREADS", "8")
+    h = ham.ti_hamiltonian(32, 32, 32)
+    n = h["n"]
+    col = h["col"].copy()
+    k = h["row_ptr"][n - 2]
+    col[[k, k + 1]] = col[[k + 1, k]]
+    val = h["val"].copy()
+    val[-3] = np.inf
+    rp = h["row_ptr"].copy()
+    rp[n - 1] = rp[n - 2] - 1
+    for bad in (_bad(h, col=col), _bad(h, val=val), _bad(h, row_ptr=rp)):
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.sell_build(bad, 0.1, 0.0)
+        assert e.value.status == kpm.KPM_EINVAL
