@@ -88,7 +88,11 @@ void kpm_default_options(kpm_options *opt);
 const char *kpm_status_string(int status);
 
 /* ======================================================= host-only calls
- * These run on the CPU and need no GPU. */
+ * These run on the CPU and need no GPU.  Large inputs are split among host
+ * threads (CSR validation, Gershgorin bounds, the SELL-C-sigma build, the
+ * gather lists; kpm_create uses the same code): at most the environment
+ * variable KPM_HOST_THREADS if set, else the hardware concurrency (<= 64).
+ * The results do not depend on the thread count. */
 
 /* Spectral bounds of a Hermitian CSR matrix by Gershgorin's circle theorem
  * (Sec. "Problem Description": a, b are found "with Gershgorin's circle

@@ -16,17 +16,19 @@
 namespace kpm {
 
 // Host threads for the conversions of large inputs: KPM_HOST_THREADS if set
-// (>= 1), else the hardware concurrency, at most 64.
+// (>= 1), else the hardware concurrency, at most kMaxHostThreads.
+constexpr int kMaxHostThreads = 64;
+
 int host_threads()
 {
     const char *env = std::getenv("KPM_HOST_THREADS");
     if (env && *env) {
         const long v = std::strtol(env, nullptr, 10);
         if (v >= 1)
-            return (int)std::min<long>(v, 64);
+            return (int)std::min<long>(v, kMaxHostThreads);
     }
     const unsigned hw = std::thread::hardware_concurrency();
-    return hw ? (int)std::min<unsigned>(hw, 64) : 1;
+    return hw ? (int)std::min<unsigned>(hw, kMaxHostThreads) : 1;
 }
 
 // Calls f(begin, end, part) on contiguous parts of [0, n), part p covering
@@ -174,17 +176,29 @@ int kpm_gershgorin(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
     int rc = validate_csr(n, row_ptr, col, val_ri);
     if (rc)
         return rc;
-    double lo = INFINITY, hi = -INFINITY;
-    for (int64_t i = 0; i < n; i++) {
-        double centre = 0.0, radius = 0.0;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-            if (col[k] == i)
-                centre = val_ri[2 * k];
-            else
-                radius += std::hypot(val_ri[2 * k], val_ri[2 * k + 1]);
+    // rows are independent and min/max do not depend on the order: each
+    // part reduces its rows, the parts are reduced at the end
+    std::vector<double> part_lo(kMaxHostThreads, INFINITY), part_hi(kMaxHostThreads, -INFINITY);
+    const int parts = parallel_parts(n, 1 << 14, [&](int64_t b, int64_t e, int part) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int64_t i = b; i < e; i++) {
+            double centre = 0.0, radius = 0.0;
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+                if (col[k] == i)
+                    centre = val_ri[2 * k];
+                else
+                    radius += std::hypot(val_ri[2 * k], val_ri[2 * k + 1]);
+            }
+            lo = std::min(lo, centre - radius);
+            hi = std::max(hi, centre + radius);
         }
-        lo = std::min(lo, centre - radius);
-        hi = std::max(hi, centre + radius);
+        part_lo[part] = lo;
+        part_hi[part] = hi;
+    });
+    double lo = INFINITY, hi = -INFINITY;
+    for (int p = 0; p < parts; p++) {
+        lo = std::min(lo, part_lo[p]);
+        hi = std::max(hi, part_hi[p]);
     }
     *emin = lo;
     *emax = hi;
@@ -585,9 +599,8 @@ int kpm_gather_build(const kpm_sell *s, kpm_gather *out)
     // chunks are independent: each part of the chunk range builds its runs
     // (pairs) and per-chunk run counts, written to lidx directly; the parts'
     // runs are then concatenated in order
-    const int max_parts = std::max(1, host_threads());
-    std::vector<std::vector<int32_t>> part_runs(max_parts);
-    std::vector<int32_t> part_umax(max_parts, 0), part_lmax(max_parts, 0);
+    std::vector<std::vector<int32_t>> part_runs(kMaxHostThreads);
+    std::vector<int32_t> part_umax(kMaxHostThreads, 0), part_lmax(kMaxHostThreads, 0);
     std::atomic<bool> too_long(false), no_mem(false);
     std::vector<int64_t> run_cnt(n_chunks, 0);
     const int parts = parallel_parts(n_chunks, 1 << 9, [&](int64_t lo, int64_t hi, int part) {

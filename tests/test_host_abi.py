@@ -392,3 +392,12 @@ def test_invalid_input_is_rejected_in_any_part(kpm, monkeypatch):
         with pytest.raises(kpm.KPMError) as e:
             kpm.sell_build(bad, 0.1, 0.0)
         assert e.value.status == kpm.KPM_EINVAL
+
+
+def test_gershgorin_does_not_depend_on_the_host_thread_count(kpm, monkeypatch):
+    h = ham.ti_hamiltonian(40, 30, 20, gamma=1.3, seed=9)
+    got = []
+    for t in ("1", "5", "16"):
+        monkeypatch.setenv("KPM_HOST_THREADS", t)
+        got.append(kpm.gershgorin(h))
+    assert got[1] == got[0] and got[2] == got[0]
