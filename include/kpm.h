@@ -50,9 +50,11 @@ extern "C" {
  *   arithmetic in IEEE double.
  * KPM_PREC_FP32: H' and the vector blocks stored as complex float (half the
  *   bytes of the bandwidth-bound sweep), the sparse product in single
- *   precision; the eta scalar products are accumulated with compensated
- *   (error-free TwoSum) single-precision pairs and reduced across threads
- *   and blocks in double.  a, b, the fold H' = 2a(H - b 1) and the
+ *   precision.  The eta scalar products: each thread's products of at most
+ *   8 rows per column are summed in single precision, the partial sums of
+ *   the rows of one warp are added in single precision (at most 32 rows in
+ *   all), and every such partial is accumulated in double, as are the sums
+ *   across warps and blocks.  a, b, the fold H' = 2a(H - b 1) and the
  *   moment-to-DOS steps stay double in both forms. */
 #define KPM_PREC_FP64 0
 #define KPM_PREC_FP32 1
@@ -204,6 +206,66 @@ typedef struct kpm_gather {
 int kpm_gather_build(const kpm_sell *s, kpm_gather *out);
 void kpm_gather_release(kpm_gather *g);
 
+/* Entry arrays of the staged sweep (host view, for inspection and tests;
+ * kpm_create builds the same arrays for the device).  The staged kernel
+ * reads a chunk's entries from arrays of its own, derived from a kpm_sell
+ * and its kpm_gather.  Fig. 5's sweep needs <V|V> per row, and the kernel
+ * takes the row's own V operand from the row's last entry, so:
+ *   - The "own" entry of a row is its last SELL entry that reads the row's
+ *     own V row (its diagonal, or a padding entry); it is stored last.
+ *     Where a row has none, a zero entry on the row's own index stands in.
+ *   - Forms 0-2: a row's entries are its SELL entries except the own one,
+ *     in SELL order, then the own entry.  In a chunk where some row has no
+ *     own entry, every row gets one more entry (value 0, own index: the own
+ *     entry of the rows without one, a filler before the own entry of the
+ *     others).  chunk_len[c] = len >= 1 is the resulting length.
+ *   - Form 3: a row's real entries except the own one first (region A,
+ *     chunk_nre[c] entries), then its imaginary entries (region B), in SELL
+ *     order, each region filled up to the chunk's largest count with zero
+ *     entries on the row's own index, then the own entry (which must be
+ *     real); len = chunk_nre[c] + (imaginary count) + 1.
+ *   - Local indices (lidx, 16-bit positions in the chunk's gather list, the
+ *     row's own position being r) and, for form 3, values: a region of n
+ *     entries per row is stored in groups of 8 entries, then one group each
+ *     of 4, 2 and 1 entries for the binary digits of n mod 8, high to low;
+ *     a group of g entries starting at entry j of the region holds row r's
+ *     entries at (region start) + C*j + g*r, so one 16-, 8- or 4-byte load
+ *     per row reads a whole group.  Forms 0-2 have one region, the first
+ *     nm = len - 1 entries; form 3 has region A at the chunk's start and
+ *     region B at C*chunk_nre[c].  The own entry sits at C*(len - 1) + r.
+ *   - Values of forms 0-2: form 1 (complex float) stores entries j, j+1 of
+ *     row r together at complex offset chunk_ptr[c] + C*j + 2r for even
+ *     j < (nm & ~1), the others at chunk_ptr[c] + C*j + r; forms 0 and 2
+ *     (complex double) store entry j at chunk_ptr[c] + C*j + r.  Form 2 is
+ *     the half-complex form of complex double matrices whose every stored
+ *     entry is purely real or purely imaginary: a real entry h stores the
+ *     operand pair (h, h), an imaginary entry i*m stores (-m, m) and has bit
+ *     15 of its local index set (the kernel reads the V row's two halves in
+ *     swapped order for it).  Form 3, the half-complex form of complex float
+ *     matrices of that kind, stores one float per entry: h of a real entry,
+ *     m of an imaginary one (the region says which).  A zero entry counts as
+ *     real.
+ * form: 0 complex double, 1 complex float (values rounded to float), 2
+ * half-complex double, 3 half-complex float.  KPM_EINVAL for another form;
+ * for forms 2 and 3 if an entry has both parts nonzero; for form 2 if a
+ * gather list is longer than 32768 rows (bit 15 is taken); for form 3 if an
+ * own entry is imaginary.  Host only; free with kpm_staged_release. */
+typedef struct kpm_staged {
+    int64_t n_chunks;
+    int64_t n_stored;    /* C * sum of chunk_len */
+    int32_t l_max;       /* largest chunk_len */
+    int32_t form;
+    int64_t *chunk_ptr;  /* [n_chunks + 1] first entry of each chunk */
+    int32_t *chunk_len;  /* [n_chunks] */
+    int32_t *chunk_nre;  /* form 3: [n_chunks] real-region length; otherwise NULL */
+    uint16_t *lidx;      /* [n_stored] */
+    double *val;         /* forms 0, 2: double[2 * n_stored]; otherwise NULL */
+    float *valf;         /* form 1: float[2 * n_stored]; form 3: float[n_stored];
+                            otherwise NULL */
+} kpm_staged;
+int kpm_staged_build(const kpm_sell *s, const kpm_gather *g, int32_t form, kpm_staged *out);
+void kpm_staged_release(kpm_staged *st);
+
 /* ============================================================ GPU calls */
 
 /* Creates a context on opt->device: validates the CSR (and, if asked,
@@ -323,8 +385,10 @@ typedef struct kpm_info {
     int64_t matrix_bytes;   /* device bytes of values + column indices */
     int64_t kernel_launches; /* kernels this context has launched so far */
     int32_t gather_lists;    /* 1: the staged kernel's gather lists were built */
-    int32_t half_complex;    /* 1: complex double, every stored entry purely real or
-                                purely imaginary (the staged kernel's two-FMA form) */
+    int32_t half_complex;    /* 1: every stored entry purely real or purely imaginary (and,
+                                for complex float, every row's own entry real): the staged
+                                kernel's half-complex form, two real FMAs per entry and
+                                column instead of four */
     int64_t upload_bytes;    /* host -> device bytes kpm_create copied (matrix, indices,
                                 gather lists and records, half-complex operands) */
 } kpm_info;
@@ -343,8 +407,10 @@ int kpm_check_device_error(kpm_ctx *ctx);
  * block, so the consumers' waits for the next stage expire (after about two
  * seconds of SM clock), the launch records a timeout in the device error word
  * (kpm_check_device_error then returns KPM_ETIMEOUT) and its results are
- * invalid; the context stays usable.  -1 switches the hook off.  KPM_EINVAL
- * for values below -1. */
+ * invalid; the context stays usable.  A batch (kpm_batch_create) built while
+ * the hook is set on its first context stalls the same way in each of its
+ * staged launches; kpm_batch_eta then returns KPM_ETIMEOUT.  -1 switches the
+ * hook off.  KPM_EINVAL for values below -1. */
 int kpm_test_stall_staged(kpm_ctx *ctx, int64_t chunks_per_block);
 
 /* Bytes of one device vector block of width R in the context's layout:
@@ -443,11 +509,12 @@ void kpm_naive_destroy(kpm_naive *nv);
  * lane) or 8..32 (complex double, 2 columns per lane) and two stages fit in
  * shared memory; everything else runs the register-path kernel.  Complex
  * double contexts with gather lists split R into blocks of at most 32
- * columns (kpm_get_max_block_width).  For a complex double matrix whose
- * every stored entry is purely real or purely imaginary (the topological
- * insulator, Sec. "Application Scenario"), the staged kernel multiplies
- * with two real FMAs per entry and column instead of four (the skipped
- * products are exact zeros, so W is the same). */
+ * columns (kpm_get_max_block_width).  For a matrix whose every stored
+ * entry is purely real or purely imaginary (the topological insulator,
+ * Sec. "Application Scenario"), the staged kernel multiplies with two real
+ * FMAs per entry and column instead of four in both forms (the skipped
+ * products are exact zeros, so W is the same); complex float then stores
+ * one float per entry. */
 typedef struct kpm_launch {
     int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
     int32_t stages;  /* 0: register-path kernel (block_threads per block, tile_groups);

@@ -181,14 +181,16 @@ def diagonal_matrix(diag):
     }
 
 
-def random_hermitian(n, avg_offdiag, seed, empty_rows=0.0, scale=1.0):
+def random_hermitian(n, avg_offdiag, seed, empty_rows=0.0, scale=1.0, diag=True):
     """Random sparse Hermitian matrix with ragged rows.
 
     Off-diagonal pairs (i, j), i < j, are drawn with probability
     avg_offdiag / n; values are complex, diagonal real.  A fraction
     ``empty_rows`` of rows (and their columns) is left without any entry,
     which exercises zero-length rows and chunks in the sparse converter.
-    Uses the numpy Generator seeded with ``seed`` (inputs only).
+    ``diag=False`` stores no diagonal at all (rows whose own entry the
+    converter must supply).  Uses the numpy Generator seeded with ``seed``
+    (inputs only).
     """
     g = np.random.default_rng(seed)
     p = min(1.0, avg_offdiag / max(n, 1))
@@ -200,7 +202,7 @@ def random_hermitian(n, avg_offdiag, seed, empty_rows=0.0, scale=1.0):
     empty = g.random(n) < empty_rows
     keep = ~(empty[iu] | empty[ju])
     iu, ju, vo = iu[keep], ju[keep], vo[keep]
-    di = np.nonzero(~empty)[0]
+    di = np.nonzero(~empty)[0] if diag else np.zeros(0, dtype=np.int64)
     rows = np.concatenate([iu, ju, di])
     cols = np.concatenate([ju, iu, di])
     vals = np.concatenate([vo, vo.conj(), dv[di].astype(np.complex128)])

@@ -202,12 +202,25 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
     return d;
 }
 
-// A lane's eta terms for one column.  Each row adds |v|^2 and Re(conj(w) v)
-// as paired FMAs into packed single-precision pending sums ((v_re^2, v_im^2)
-// and (w_re v_re, w_im v_im)); every kEtaFold chunks fold() adds the pending
-// sums to (hi, lo) pairs with Knuth's TwoSum, so the running sum is carried
-// without rounding loss and only an 8-row partial is ever rounded in single
-// precision.  IMAG adds Im(conj(w) v) the same way in scalar form.
+// One 16-byte piece (one complex double) from shared memory.
+__device__ __forceinline__ void lds_piece(const double *src, double (&out)[2])
+{
+    const double2 t = *reinterpret_cast<const double2 *>(src);
+    out[0] = t.x;
+    out[1] = t.y;
+}
+
+// ------------------------------------------------------------------ eta
+// Complex float eta.  Each row adds, per column, |v|^2 and Re(conj(w) v)
+// (IMAG: also Im(conj(w) v)) to single-precision pending sums, one FMA
+// chain per value.  Every kEtaFold rows (one row per chunk) fold() sums the
+// pending values of the warp's P = 32/T rows (teams of equal lane-in-team)
+// by an xor butterfly and adds each sum, error-free, to a float-float
+// (TwoSum, Knuth) running pair held by one team: value i = q*E + k goes to
+// team i % P, slot i / P.  A single-precision partial thus never holds more
+// than kEtaFold rows of one lane plus the additions across the warp's rows,
+// and nothing here uses the FP64 pipe, which on this GPU runs at 1/64 of
+// the FP32 rate.
 constexpr int kEtaFold = 8;
 
 __device__ __forceinline__ void two_sum_pair(float &hi, float &lo, float p)
@@ -220,47 +233,64 @@ __device__ __forceinline__ void two_sum_pair(float &hi, float &lo, float p)
     lo = __fadd_rn(lo, e);
 }
 
-template <bool IMAG>
-struct StagedEta {
-    uint64_t pvv = 0ull, pwv = 0ull;
-    float pwvi = 0.f;
-    float vv_h = 0.f, vv_l = 0.f, wv_h = 0.f, wv_l = 0.f, wvi_h = 0.f, wvi_l = 0.f;
-    __device__ __forceinline__ void add(float wr, float wi, float vr, float vi)
+template <bool IMAG, int T, int E>
+struct WarpEta {
+    static constexpr int NQ = IMAG ? 3 : 2, P = 32 / T, NV = NQ * E, KH = (NV + P - 1) / P;
+    float pend[NV];
+    float hi[KH], lo[KH];
+    __device__ __forceinline__ void clear()
     {
-        const uint64_t v2 = pack2(vr, vi), w2 = pack2(wr, wi);
-        pvv = ffma2(v2, v2, pvv);
-        pwv = ffma2(w2, v2, pwv);
+#pragma unroll
+        for (int i = 0; i < NV; i++)
+            pend[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < KH; i++)
+            hi[i] = lo[i] = 0.f;
+    }
+    __device__ __forceinline__ void add(int k, float wr, float wi, float vr, float vi)
+    {
+        pend[k] = __fmaf_rn(vr, vr, pend[k]);
+        pend[k] = __fmaf_rn(vi, vi, pend[k]);
+        pend[E + k] = __fmaf_rn(wr, vr, pend[E + k]);
+        pend[E + k] = __fmaf_rn(wi, vi, pend[E + k]);
         if constexpr (IMAG) {
-            pwvi = __fmaf_rn(wr, vi, pwvi);
-            pwvi = __fmaf_rn(-wi, vr, pwvi);
+            pend[2 * E + k] = __fmaf_rn(wr, vi, pend[2 * E + k]);
+            pend[2 * E + k] = __fmaf_rn(-wi, vr, pend[2 * E + k]);
         }
     }
-    __device__ __forceinline__ void fold()
+    // all lanes of the warp take part
+    __device__ __forceinline__ void fold(int team)
     {
-        float a, b;
-        unpack2(pvv, a, b);
-        two_sum_pair(vv_h, vv_l, __fadd_rn(a, b));
-        unpack2(pwv, a, b);
-        two_sum_pair(wv_h, wv_l, __fadd_rn(a, b));
-        pvv = pwv = 0ull;
-        if constexpr (IMAG) {
-            two_sum_pair(wvi_h, wvi_l, pwvi);
-            pwvi = 0.f;
+#pragma unroll
+        for (int off = T; off < 32; off <<= 1)
+#pragma unroll
+            for (int i = 0; i < NV; i++)
+                pend[i] = __fadd_rn(pend[i], __shfl_xor_sync(0xffffffffu, pend[i], off));
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            if (team == i % P)
+                two_sum_pair(hi[i / P], lo[i / P], pend[i]);
+            pend[i] = 0.f;
         }
     }
-    // after fold()
-    __device__ __forceinline__ double get(int k) const
+    // after fold(): this lane's running sums to the warp's accumulators acc
+    // (double [3][RB], column c of quantity q at q*RB + c), then cleared
+    __device__ __forceinline__ void store(double *acc, int tl, int team)
     {
-        if (k == 0)
-            return (double)vv_h + (double)vv_l;
-        if (k == 1)
-            return (double)wv_h + (double)wv_l;
-        return IMAG ? (double)wvi_h + (double)wvi_l : 0.0;
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            if (team == i % P)
+                acc[(i / E) * (T * E) + owned_column<float, T, E>(tl, i % E)] =
+                    (double)hi[i / P] + (double)lo[i / P];
+        }
+#pragma unroll
+        for (int i = 0; i < KH; i++)
+            hi[i] = lo[i] = 0.f;
     }
 };
 
 // A lane's eta terms for one column in complex double: plain FMA chains
-// (aug_spmmv.cuh's EtaAcc); fold() has nothing to do.
+// (aug_spmmv.cuh's EtaAcc).
 template <bool IMAG>
 struct StagedEta64 {
     EtaAcc<double, IMAG> a;
@@ -268,7 +298,6 @@ struct StagedEta64 {
     {
         a.add(wr, wi, vr, vi);
     }
-    __device__ __forceinline__ void fold() {}
     __device__ __forceinline__ double get(int k) const { return a.get(k); }
 };
 
@@ -299,7 +328,7 @@ __device__ __forceinline__ int advance_problem(const StagedProblem *tab, int n_p
 // word l of the tile's record, i.e. inline run l - 3; runs past the inline
 // ones are read from the overflow array 32 at a time.  Returns the number
 // of tiles armed.
-template <int RB, int CSIZE>
+template <int RB, int CSIZE, int VSIZE>
 __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem,
                                            const StagedProblem *tab, int64_t total,
                                            volatile int *abort_flag)
@@ -340,6 +369,8 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
     const int2 *ovfp = nullptr;
     int ld = 0, col0 = 0;
     int64_t k = 0;
+    int s = 0;          // stage of tile k
+    uint32_t ph = 0;    // parity of that stage's current use
     for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         if (p.stall_after >= 0 && k >= p.stall_after)
             break;  // test hook: leave the remaining stages unarmed
@@ -369,7 +400,8 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                    ((int64_t)__shfl_sync(0xffffffffu, word.y, w) << 32);
         };
         const int64_t e0 = word64(0), ovf0 = word64(2);
-        const int len = __shfl_sync(0xffffffffu, word.x, 1);
+        const int lenw = __shfl_sync(0xffffffffu, word.x, 1);
+        const int len = lenw & 0xffff, nre = lenw >> 16;
         const int nruns = __shfl_sync(0xffffffffu, word.y, 1);
         const int n_inline = min(nruns, KPM_REC_INLINE_RUNS);
         const bool has_run = lane >= 3 && lane - 3 < n_inline;
@@ -383,8 +415,6 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             total_rows += (uint32_t)__shfl_sync(0xffffffffu, warp_incl_scan(r.y, lane), 31);
         }
 
-        const int s = (int)(k % NS);
-        const uint32_t ph = (uint32_t)((k / NS) & 1);
         const uint32_t full = full0 + 8 * s, empty = empty0 + 8 * s;
         if (k >= NS) {
             // every lane waits (and acquires); the warp leaves together
@@ -393,20 +423,19 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                 break;
         }
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
-        const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * (uint32_t)CSIZE;
+        const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * (uint32_t)VSIZE;
         const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
         const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes;
         if (lane == 0) {
             volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
-            meta[1] = pi;
-            meta[2] = (int)lt;
+            meta[1] = nre;
             mbar_arrive_expect_tx(full, bytes);
         }
         __syncwarp();
         if (len > 0) {
             if (lane == 0)
-                bulk_g2s(st + p.off_val, valb + e0 * CSIZE, val_bytes, full);
+                bulk_g2s(st + p.off_val, valb + e0 * VSIZE, val_bytes, full);
             if (lane == 1)
                 bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, lidx_bytes, full);
         }
@@ -428,6 +457,10 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                           row_bytes, full, CSIZE);
             base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
         }
+        if (++s == NS) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
     cp_async_wait<0>();
     return k;
@@ -438,24 +471,44 @@ __device__ __forceinline__ void consumer_bar(int n_cw)
     asm volatile("bar.sync 1, %0;" ::"r"(n_cw * 32) : "memory");
 }
 
-// The consumer warps' eta sums for one problem, in a fixed order: lanes of
-// equal columns by an xor butterfly, then warp after warp into red (3*RB
-// doubles), then red to the problem's partial slot.  Resets acc.
-template <typename Real, int T, int E, typename Acc>
-__device__ __forceinline__ void flush_eta(Acc (&acc)[E], double *red,
-                                          const StagedProblem &P, int64_t slot, int cw, int n_cw)
+// Complex float: one problem's eta sums from the consumer warps'
+// accumulators (acc0: n_cw blocks of [3][RB] doubles, written by
+// WarpEta::store), summed in warp order into the problem's partial slot;
+// the accumulators are cleared.
+template <int RB>
+__device__ __forceinline__ void flush_eta32(double *acc0, const StagedProblem &P, int64_t slot,
+                                            int cw, int n_cw)
+{
+    const int lane = threadIdx.x & 31;
+    consumer_bar(n_cw);
+    for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32) {
+        double s = 0.0;
+        for (int w = 0; w < n_cw; w++) {
+            s += acc0[w * 3 * RB + t];
+            acc0[w * 3 * RB + t] = 0.0;
+        }
+        P.partial[slot * P.ps + t * P.qs] = s;
+    }
+    consumer_bar(n_cw);
+}
+
+// Complex double: the consumer warps' eta sums for one problem, in a fixed
+// order: lanes of equal columns by an xor butterfly, then warp after warp
+// into red (3*RB doubles), then red to the problem's partial slot.  Resets
+// acc.
+template <int T, int E, typename Acc>
+__device__ __forceinline__ void flush_eta64(Acc (&acc)[E], double *red, const StagedProblem &P,
+                                            int64_t slot, int cw, int n_cw)
 {
     constexpr int RB = T * E;
     const int lane = threadIdx.x & 31;
     const int tl = lane % T, team = lane / T;
     double out[3 * E];
 #pragma unroll
-    for (int k = 0; k < E; k++) {
-        acc[k].fold();
+    for (int k = 0; k < E; k++)
 #pragma unroll
         for (int q = 0; q < 3; q++)
             out[q * E + k] = acc[k].get(q);
-    }
 #pragma unroll
     for (int off = T; off < 32; off <<= 1)
 #pragma unroll
@@ -467,7 +520,7 @@ __device__ __forceinline__ void flush_eta(Acc (&acc)[E], double *red,
             for (int q = 0; q < 3; q++)
 #pragma unroll
                 for (int k = 0; k < E; k++) {
-                    double &d = red[q * RB + owned_column<Real, T, E>(tl, k)];
+                    double &d = red[q * RB + owned_column<double, T, E>(tl, k)];
                     d = w == 0 ? out[q * E + k] : d + out[q * E + k];
                 }
         }
@@ -494,67 +547,467 @@ struct StagedMinBlocks {
     static constexpr int value = (E >= 4 || sizeof(Real) == 8) ? 1 : 2;
 };
 
-// One row's H' V for this lane's E columns from a stage, complex double:
-// one 16-byte piece per column and lane and four FMAs per entry and column;
-// or, with HALF (every stored entry purely real or purely imaginary), two.
-// There the value array holds operand pairs (a, b) and bit 15 of the local
-// index marks an imaginary entry: a real one, (r, r), adds (r x, r y) to
-// (re, im); an imaginary one, (-m, m), adds (-m y, m x), so the halves of v
-// are read in swapped order.  The two FMAs are the general form's nonzero
-// products in the same order (the skipped ones add exact zeros), so both
-// forms give the same W.
-template <int T, int E, bool HALF>
-__device__ __forceinline__ void row_product(const double *vb, const double2 *vals,
-                                            const uint16_t *lid, int C, int len, int rit, int tl,
-                                            double (&acc_s)[2 * E])
+// Visits the index groups of a row's first nm entries in a stage (layout of
+// kpm_staged in kpm.h: groups of 8, then of 4, 2 and 1 entries; one load per
+// group): pair(j, u_j, u_{j+1}) for the entries of the groups of two or
+// more, in pairs starting at even j, and single(j, u_j) for a group of one.
+template <typename F2, typename F1>
+__device__ __forceinline__ void walk_index_groups(const uint16_t *lid, int C, int rit, int nm,
+                                                  F2 &&pair, F1 &&single)
 {
-    constexpr int RB = T * E;
+    int j = 0;
+    for (; j + 8 <= nm; j += 8) {
+        const uint4 g = *reinterpret_cast<const uint4 *>(lid + C * j + 8 * rit);
+        pair(j, g.x & 0xffffu, g.x >> 16);
+        pair(j + 2, g.y & 0xffffu, g.y >> 16);
+        pair(j + 4, g.z & 0xffffu, g.z >> 16);
+        pair(j + 6, g.w & 0xffffu, g.w >> 16);
+    }
+    if (nm - j >= 4) {
+        const uint2 g = *reinterpret_cast<const uint2 *>(lid + C * j + 4 * rit);
+        pair(j, g.x & 0xffffu, g.x >> 16);
+        pair(j + 2, g.y & 0xffffu, g.y >> 16);
+        j += 4;
+    }
+    if (nm - j >= 2) {
+        const uint32_t g = *reinterpret_cast<const uint32_t *>(lid + C * j + 2 * rit);
+        pair(j, g & 0xffffu, g >> 16);
+        j += 2;
+    }
+    if (nm - j >= 1)
+        single(j, (uint32_t)lid[C * j + rit]);
+}
+
+// Visits entries [j0, j0 + n) of a row whose indices and one-float values
+// share the grouped layout of a region (groups of 8, 4, 2, 1 entries; one
+// load per group for the indices and one or two for the values):
+// f(u_j, s_j) for each entry in order.
+template <typename F>
+__device__ __forceinline__ void walk_region(const uint16_t *lid, const float *hv, int C, int rit,
+                                            int j0, int n, F &&f)
+{
+    const uint16_t *L = lid + C * j0;
+    const float *H = hv + C * j0;
+    int j = 0;
+    for (; j + 8 <= n; j += 8) {
+        const uint4 g = *reinterpret_cast<const uint4 *>(L + C * j + 8 * rit);
+        const float4 h0 = *reinterpret_cast<const float4 *>(H + C * j + 8 * rit);
+        const float4 h1 = *reinterpret_cast<const float4 *>(H + C * j + 8 * rit + 4);
+        f(g.x & 0xffffu, h0.x);
+        f(g.x >> 16, h0.y);
+        f(g.y & 0xffffu, h0.z);
+        f(g.y >> 16, h0.w);
+        f(g.z & 0xffffu, h1.x);
+        f(g.z >> 16, h1.y);
+        f(g.w & 0xffffu, h1.z);
+        f(g.w >> 16, h1.w);
+    }
+    if (n - j >= 4) {
+        const uint2 g = *reinterpret_cast<const uint2 *>(L + C * j + 4 * rit);
+        const float4 h = *reinterpret_cast<const float4 *>(H + C * j + 4 * rit);
+        f(g.x & 0xffffu, h.x);
+        f(g.x >> 16, h.y);
+        f(g.y & 0xffffu, h.z);
+        f(g.y >> 16, h.w);
+        j += 4;
+    }
+    if (n - j >= 2) {
+        const uint32_t g = *reinterpret_cast<const uint32_t *>(L + C * j + 2 * rit);
+        const float2 h = *reinterpret_cast<const float2 *>(H + C * j + 2 * rit);
+        f(g & 0xffffu, h.x);
+        f(g >> 16, h.y);
+        j += 2;
+    }
+    if (n - j >= 1)
+        f((uint32_t)L[C * j + rit], H[C * j + rit]);
+}
+
+// The problem a consumer warp's tile belongs to, with the fields the
+// consumers use.  Every consumer warp derives it from the tile number and
+// the problem table alone (never from what the producer wrote), so all of
+// them see the same sequence of problems.
+struct ConsumerProblem {
+    int pi = 0, cur = -1;
+    int64_t slot = 0;
+    void *W = nullptr;
+    int ld = 0, col0 = 0;
+};
+
+// Complex float consumer warp.  Per chunk: the row's old W is loaded into
+// registers one chunk ahead, when the previous chunk is done, so its latency
+// passes while the entries are summed; the entries are read from the stage
+// group by group (one 16-byte load per 8 indices, one per 2 values); each
+// entry adds its products with Re h and Im h to two packed (re, im) sums
+// per column with paired FMAs, and H'V - W = (a.re - b.im - w.re,
+// a.im + b.re - w.im); the last entry reads the row's own V row, whose
+// operand stays in registers for the scalar products.  HALF (every entry
+// purely real or purely imaginary, one float per entry, real entries before
+// imaginary ones): a real entry r adds (r, r) * (v.re, v.im) to a, an
+// imaginary one i*m adds (m, m) * (v.re, v.im) to b -- the nonzero products
+// of the general form, so W is the same -- with one paired FMA per column.
+//
+// Abort safety: the only barriers among consumer warps are in flush_eta32.
+// Every consumer warp walks the same tiles (blockIdx.x, + gridDim.x, ...)
+// and derives each tile's problem from the table, so every consumer warp
+// calls flush_eta32 at the same tiles whatever happens to its waits.  A
+// warp whose wait fails (timeout, or the block's abort flag) sets `failed`
+// and skips the work and the waits of its remaining tiles, but not the
+// flushes: the barrier counts always match.
+template <int T, int E, bool IMAG, bool HALF>
+__device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *smem,
+                                          const StagedProblem *tab, int64_t total,
+                                          volatile int *abort_flag)
+{
+    constexpr int P = 32 / T, RB = T * E;
+    constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
+    static_assert(EV == 2, "two complex floats per 16-byte piece");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cw = warp - 1, n_cw = (blockDim.x >> 5) - 1;
+    const int tl = lane % T, team = lane / T;
+    const int rit = cw * P + team;  // row within the chunk
+    const int C = p.C, NS = p.stages;
+    const int64_t G = gridDim.x;
+    const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
+    double *acc0 = reinterpret_cast<double *>(smem + p.off_aux);
+    double *accw = acc0 + cw * 3 * RB;
+    for (int i = lane; i < 3 * RB; i += 32)
+        accw[i] = 0.0;
+    __syncwarp();
+
+    WarpEta<IMAG, T, E> pe;
+    pe.clear();
+    int nfold = 0;
+    uint64_t pa[E], pb[E];
+    float4 wo[NP];  // the row's old W pieces
+    // the old W of the row of tile gt (problem q) into wo
+    auto load_w = [&](int64_t gt, int q) {
+        const StagedProblem &Q = tab[q];
+        const float *Wq = static_cast<const float *>(Q.buf[p.parity ^ 1]);
+        const int64_t row = (gt - Q.tile0) * (int64_t)C + rit;
+        const int64_t wb = row * Q.ld + Q.col0 + tl * EV;
 #pragma unroll
-    for (int q = 0; q < 2 * E; q++)
-        acc_s[q] = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < len; j++) {
-        const int l = lid[j * C + rit];
-        const double2 h = vals[j * C + rit];
-        if constexpr (HALF) {
-            const int sw = l >> 15;
-            const double *vr = vb + (size_t)(l & 0x7fff) * 2 * RB + 2 * tl;
-            const double *v0 = vr + sw, *v1 = vr + (sw ^ 1);
-#pragma unroll
-            for (int k = 0; k < E; k++) {
-                acc_s[2 * k] = fma(h.x, v0[2 * k * T], acc_s[2 * k]);
-                acc_s[2 * k + 1] = fma(h.y, v1[2 * k * T], acc_s[2 * k + 1]);
+        for (int q2 = 0; q2 < NP; q2++)
+            wo[q2] = __ldcg(reinterpret_cast<const float4 *>(Wq + 2 * (wb + q2 * T * EV)));
+    };
+    ConsumerProblem cp;
+    bool failed = false, have_w = false;
+    int64_t k = 0;
+    int s_next = 0;          // stage of the next tile
+    uint32_t ph_next = 0;    // parity of that stage's current use
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
+        const int s = s_next;
+        const uint32_t ph = ph_next;
+        if (++s_next == NS) {
+            s_next = 0;
+            ph_next ^= 1u;
+        }
+        cp.pi = advance_problem(tab, p.n_probs, cp.pi, gt);
+        const int64_t lt = gt - tab[cp.pi].tile0;
+        if (cp.pi != cp.cur) {
+            if (cp.cur >= 0 && p.dots) {
+                pe.fold(team);
+                pe.store(accw, tl, team);
+                nfold = 0;
+                flush_eta32<RB>(acc0, tab[cp.cur], cp.slot, cw, n_cw);
             }
-        } else {
-            const double *vr = vb + (size_t)l * 2 * RB;
+            cp.cur = cp.pi;
+            cp.slot = lt;
+            cp.W = tab[cp.pi].buf[p.parity ^ 1];
+            cp.ld = tab[cp.pi].ld;
+            cp.col0 = tab[cp.pi].col0;
+        }
+        if (failed)
+            continue;
+        if (!p.init && !have_w)
+            load_w(gt, cp.pi);
+        const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
+        if (!__all_sync(0xffffffffu, ok)) {
+            failed = true;
+            continue;
+        }
+        const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
+        const volatile int *meta = reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
+        const int len = meta[0];
+        const float *vb = reinterpret_cast<const float *>(st);
+        const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
 #pragma unroll
-            for (int k = 0; k < E; k++) {
-                const double2 v = *reinterpret_cast<const double2 *>(vr + 2 * (k * T + tl));
-                acc_s[2 * k] = fma(h.x, v.x, acc_s[2 * k]);
-                acc_s[2 * k] = fma(-h.y, v.y, acc_s[2 * k]);
-                acc_s[2 * k + 1] = fma(h.x, v.y, acc_s[2 * k + 1]);
-                acc_s[2 * k + 1] = fma(h.y, v.x, acc_s[2 * k + 1]);
+        for (int c = 0; c < E; c++)
+            pa[c] = pb[c] = 0ull;
+        auto entry = [&](uint32_t u, float hx, float hy) {
+            const uint64_t hx2 = pack2(hx, hx), hy2 = pack2(hy, hy);
+            const float *vr = vb + (size_t)u * 2 * RB + 2 * tl * EV;
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                const uint64_t v0 = pack2(v4.x, v4.y), v1 = pack2(v4.z, v4.w);
+                pa[2 * q] = ffma2(hx2, v0, pa[2 * q]);
+                pb[2 * q] = ffma2(hy2, v0, pb[2 * q]);
+                pa[2 * q + 1] = ffma2(hx2, v1, pa[2 * q + 1]);
+                pb[2 * q + 1] = ffma2(hy2, v1, pb[2 * q + 1]);
+            }
+        };
+        const int nm = len - 1;
+        float hox, hoy;  // the own entry's value
+        if constexpr (HALF) {
+            const float *hv = reinterpret_cast<const float *>(st + p.off_val);
+            const int nre = meta[1];
+            auto half_entry = [&](uint64_t (&acc)[E], uint32_t u, float h) {
+                const uint64_t h2 = pack2(h, h);
+                const float *vr = vb + (size_t)u * 2 * RB + 2 * tl * EV;
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    const float4 v4 = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                    acc[2 * q] = ffma2(h2, pack2(v4.x, v4.y), acc[2 * q]);
+                    acc[2 * q + 1] = ffma2(h2, pack2(v4.z, v4.w), acc[2 * q + 1]);
+                }
+            };
+            walk_region(lid, hv, C, rit, 0, nre, [&](uint32_t u, float h) { half_entry(pa, u, h); });
+            walk_region(lid, hv, C, rit, nre, nm - nre,
+                        [&](uint32_t u, float h) { half_entry(pb, u, h); });
+            hox = hv[C * nm + rit];
+            hoy = 0.f;
+        } else {
+            const float2 *vals = reinterpret_cast<const float2 *>(st + p.off_val);
+            walk_index_groups(
+                lid, C, rit, nm,
+                [&](int j, uint32_t u0, uint32_t u1) {
+                    const float4 h = *reinterpret_cast<const float4 *>(vals + C * j + 2 * rit);
+                    entry(u0, h.x, h.y);
+                    entry(u1, h.z, h.w);
+                },
+                [&](int j, uint32_t u) {
+                    const float2 h = vals[C * j + rit];
+                    entry(u, h.x, h.y);
+                });
+            const float2 h = vals[C * nm + rit];
+            hox = h.x;
+            hoy = h.y;
+        }
+        // the own entry: local position rit; its V operand stays for eta
+        float4 vo[NP];
+        {
+            const uint64_t hx2 = pack2(hox, hox), hy2 = pack2(hoy, hoy);
+            const float *vr = vb + (size_t)rit * 2 * RB + 2 * tl * EV;
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                vo[q] = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                const uint64_t v0 = pack2(vo[q].x, vo[q].y), v1 = pack2(vo[q].z, vo[q].w);
+                pa[2 * q] = ffma2(hx2, v0, pa[2 * q]);
+                pa[2 * q + 1] = ffma2(hx2, v1, pa[2 * q + 1]);
+                if constexpr (!HALF) {
+                    pb[2 * q] = ffma2(hy2, v0, pb[2 * q]);
+                    pb[2 * q + 1] = ffma2(hy2, v1, pb[2 * q + 1]);
+                }
             }
         }
+        float w[2 * E];
+#pragma unroll
+        for (int c = 0; c < E; c++) {
+            float ar, ai, br, bi;
+            unpack2(pa[c], ar, ai);
+            unpack2(pb[c], br, bi);
+            w[2 * c] = ar - bi;
+            w[2 * c + 1] = ai + br;
+        }
+        if (p.init) {
+#pragma unroll
+            for (int i = 0; i < 2 * E; i++)
+                w[i] *= 0.5f;
+        } else {
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                w[4 * q] -= wo[q].x;
+                w[4 * q + 1] -= wo[q].y;
+                w[4 * q + 2] -= wo[q].z;
+                w[4 * q + 3] -= wo[q].w;
+            }
+        }
+        const int64_t wbase = (lt * (int64_t)C + rit) * cp.ld + cp.col0 + tl * EV;
+        store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, w);
+        // the next tile's old W, while this one's scalar products are added
+        have_w = false;
+        if (!p.init && gt + G < total) {
+            load_w(gt + G, advance_problem(tab, p.n_probs, cp.pi, gt + G));
+            have_w = true;
+        }
+        if (p.dots) {
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                pe.add(2 * q, w[4 * q], w[4 * q + 1], vo[q].x, vo[q].y);
+                pe.add(2 * q + 1, w[4 * q + 2], w[4 * q + 3], vo[q].z, vo[q].w);
+            }
+            if (++nfold == kEtaFold) {
+                pe.fold(team);
+                nfold = 0;
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(empty0 + 8 * s);
+    }
+    if (!p.dots)
+        return;
+    if (cp.cur >= 0) {
+        pe.fold(team);
+        pe.store(accw, tl, team);
+        flush_eta32<RB>(acc0, tab[cp.cur], cp.slot, cw, n_cw);
+    } else if (p.probs == nullptr) {
+        // a single problem's partials are read for every block: a block
+        // without chunks contributes zeros
+        for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
+            tab[0].partial[(int64_t)blockIdx.x * tab[0].ps + t * tab[0].qs] = 0.0;
     }
 }
 
-// One 16-byte piece (two complex floats or one complex double) from
-// shared memory.
-__device__ __forceinline__ void lds_piece(const float *src, float (&out)[4])
+// Complex double consumer warp (the FP64 pipe is this form's bound): the
+// old W row is fetched with cp.async into the block's W buffer while the
+// entry loop runs; per entry and column four FMAs on one 16-byte V piece,
+// or, HALF (every stored entry purely real or purely imaginary), two on its
+// 8-byte halves: the value array holds operand pairs (a, b) and bit 15 of
+// the local index marks an imaginary entry -- a real one, (r, r), adds
+// (r x, r y) to (re, im); an imaginary one, (-m, m), adds (-m y, m x), so
+// the halves are read in swapped order.  The two FMAs are the general
+// form's nonzero products in the same order (the skipped ones add exact
+// zeros), so both forms give the same W.  Eta in plain FMA chains.  Abort
+// safety as in consume32.
+template <int T, int E, bool IMAG, bool HALF>
+__device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *smem,
+                                          const StagedProblem *tab, int64_t total,
+                                          volatile int *abort_flag)
 {
-    const float4 t = *reinterpret_cast<const float4 *>(src);
-    out[0] = t.x;
-    out[1] = t.y;
-    out[2] = t.z;
-    out[3] = t.w;
-}
+    constexpr int P = 32 / T, RB = T * E;
+    constexpr int EV = Pieces<double, E>::EV, NP = Pieces<double, E>::NP;
+    static_assert(EV == 1, "one complex double per 16-byte piece");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cw = warp - 1, n_cw = (blockDim.x >> 5) - 1;
+    const int tl = lane % T, team = lane / T;
+    const int rit = cw * P + team;
+    const int C = p.C, NS = p.stages;
+    const int64_t G = gridDim.x;
+    const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
+    double *red = reinterpret_cast<double *>(smem + kRedOffset);
+    StagedEta64<IMAG> acc[E];
+    ConsumerProblem cp;
+    bool failed = false;
+    int64_t k = 0;
+    int s_next = 0;          // stage of the next tile
+    uint32_t ph_next = 0;    // parity of that stage's current use
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
+        const int s = s_next;
+        const uint32_t ph = ph_next;
+        if (++s_next == NS) {
+            s_next = 0;
+            ph_next ^= 1u;
+        }
+        cp.pi = advance_problem(tab, p.n_probs, cp.pi, gt);
+        const int64_t lt = gt - tab[cp.pi].tile0;
+        if (cp.pi != cp.cur) {
+            if (cp.cur >= 0 && p.dots)
+                flush_eta64<T, E>(acc, red, tab[cp.cur], cp.slot, cw, n_cw);
+            cp.cur = cp.pi;
+            cp.slot = lt;
+            cp.W = tab[cp.pi].buf[p.parity ^ 1];
+            cp.ld = tab[cp.pi].ld;
+            cp.col0 = tab[cp.pi].col0;
+        }
+        if (failed)
+            continue;
+        const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
+        if (!__all_sync(0xffffffffu, ok)) {
+            failed = true;
+            continue;
+        }
+        const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
+        const int len = *reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
+        const double *vb = reinterpret_cast<const double *>(st);
+        const double2 *vals = reinterpret_cast<const double2 *>(st + p.off_val);
+        const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
+        double *Wp = static_cast<double *>(cp.W);
 
-__device__ __forceinline__ void lds_piece(const double *src, double (&out)[2])
-{
-    const double2 t = *reinterpret_cast<const double2 *>(src);
-    out[0] = t.x;
-    out[1] = t.y;
+        // the old W row is requested first (the producer asked L2 for it):
+        // this lane's 16-byte pieces go to the row's slot of the W buffer
+        // (written and read by this lane only) with cp.async
+        const int64_t wbase = (lt * (int64_t)C + rit) * cp.ld + cp.col0 + tl * EV;
+        double *wsm = reinterpret_cast<double *>(smem + p.off_aux) + rit * 2 * RB;
+        if (!p.init) {
+#pragma unroll
+            for (int q = 0; q < NP; q++)
+                cp_async16(smem_u32(wsm + 2 * (q * T * EV + tl * EV)),
+                           Wp + 2 * (wbase + (int64_t)q * T * EV));
+            cp_async_commit();
+        }
+        double a[2 * E];
+#pragma unroll
+        for (int q = 0; q < 2 * E; q++)
+            a[q] = 0.0;
+        auto entry = [&](uint32_t l, const double2 h) {
+            if constexpr (HALF) {
+                const int sw = (int)(l >> 15);
+                const double *vr = vb + (size_t)(l & 0x7fffu) * 2 * RB + 2 * tl;
+                const double *v0 = vr + sw, *v1 = vr + (sw ^ 1);
+#pragma unroll
+                for (int c = 0; c < E; c++) {
+                    a[2 * c] = fma(h.x, v0[2 * c * T], a[2 * c]);
+                    a[2 * c + 1] = fma(h.y, v1[2 * c * T], a[2 * c + 1]);
+                }
+            } else {
+                const double *vr = vb + (size_t)l * 2 * RB;
+#pragma unroll
+                for (int c = 0; c < E; c++) {
+                    const double2 v = *reinterpret_cast<const double2 *>(vr + 2 * (c * T + tl));
+                    a[2 * c] = fma(h.x, v.x, a[2 * c]);
+                    a[2 * c] = fma(-h.y, v.y, a[2 * c]);
+                    a[2 * c + 1] = fma(h.x, v.y, a[2 * c + 1]);
+                    a[2 * c + 1] = fma(h.y, v.x, a[2 * c + 1]);
+                }
+            }
+        };
+        const int nm = len - 1;
+        walk_index_groups(
+            lid, C, rit, nm,
+            [&](int j, uint32_t u0, uint32_t u1) {
+                entry(u0, vals[C * j + rit]);
+                entry(u1, vals[C * (j + 1) + rit]);
+            },
+            [&](int j, uint32_t u) { entry(u, vals[C * j + rit]); });
+        entry((uint32_t)lid[C * nm + rit], vals[C * nm + rit]);
+        if (p.init) {
+#pragma unroll
+            for (int q = 0; q < 2 * E; q++)
+                a[q] *= 0.5;
+        } else {
+            cp_async_wait<0>();
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                double wo[2];
+                lds_piece(wsm + 2 * (q * T * EV + tl * EV), wo);
+                a[2 * q] -= wo[0];
+                a[2 * q + 1] -= wo[1];
+            }
+        }
+        store_owned<double, T, E>(Wp, wbase, a);
+        if (p.dots) {
+            // the row's own V entries: local position rit of the list
+            const double *ov = vb + (size_t)rit * 2 * RB;
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                double v[2];
+                lds_piece(ov + 2 * (q * T * EV + tl * EV), v);
+                acc[q].add(a[2 * q], a[2 * q + 1], v[0], v[1]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(empty0 + 8 * s);
+    }
+    if (!p.dots)
+        return;
+    if (cp.cur >= 0) {
+        flush_eta64<T, E>(acc, red, tab[cp.cur], cp.slot, cw, n_cw);
+    } else if (p.probs == nullptr) {
+        for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
+            tab[0].partial[(int64_t)blockIdx.x * tab[0].ps + t * tab[0].qs] = 0.0;
+    }
 }
 
 template <typename Real, int T, int E, bool IMAG, bool HALF>
@@ -562,18 +1015,16 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
     aug_spmmv_staged_kernel(const StagedParams p)
 {
     static_assert(T >= 1 && T <= 32 && (32 % T) == 0, "team size divides the warp");
-    static_assert(!HALF || sizeof(Real) == 8, "the half-complex form is complex double only");
-    constexpr int P = 32 / T;
     constexpr int RB = T * E;
     constexpr int CSIZE = 2 * (int)sizeof(Real);
-    constexpr int EV = Pieces<Real, E>::EV, NP = Pieces<Real, E>::NP;
-    static_assert(2 * EV * sizeof(Real) == 16, "16-byte pieces");
-    using Acc = typename std::conditional<sizeof(Real) == 4, StagedEta<IMAG>,
-                                          StagedEta64<IMAG>>::type;
-    // [full[NS], empty[NS] | abort flag at 128 | stage metadata at
+    // bytes of one staged value: a complex number, an operand pair (complex
+    // double half form) or one float (complex float half form)
+    constexpr int VSIZE = (sizeof(Real) == 4 && HALF) ? 4 : CSIZE;
+    // [full[NS], empty[NS] | abort flag at 128 | stage chunk lengths at
     //  kMetaOffset | record ring at kRingOffset | eta sum at kRedOffset |
-    //  problem table at kTableOffset | stages from bar_bytes on | W buffer
-    //  at off_wbuf]
+    //  problem table at kTableOffset | stages from bar_bytes on | at
+    //  off_aux: the W buffer (complex double) or the consumer warps' eta
+    //  accumulators (complex float)]
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -582,7 +1033,6 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
     const int n_cw = (blockDim.x >> 5) - 1;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);
     StagedProblem *tab = reinterpret_cast<StagedProblem *>(smem + kTableOffset);
-    double *red = reinterpret_cast<double *>(smem + kRedOffset);
     if (threadIdx.x == 0) {
         *abort_flag = 0;
         for (int s = 0; s < NS; s++) {
@@ -601,7 +1051,7 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
     const int64_t total = tab[p.n_probs - 1].tile0 + tab[p.n_probs - 1].n_tiles;
 
     if (warp == 0) {
-        const int64_t armed = produce<RB, CSIZE>(p, smem, tab, total, abort_flag);
+        const int64_t armed = produce<RB, CSIZE, VSIZE>(p, smem, tab, total, abort_flag);
         // the copies of the last armed stages must land before the block's
         // shared memory is released
         if (lane == 0)
@@ -609,147 +1059,10 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
                 mbar_wait_bounded(full0 + 8 * (uint32_t)(k % NS), (uint32_t)((k / NS) & 1),
                                   abort_flag, p.err, false);
         __syncwarp();
+    } else if constexpr (sizeof(Real) == 4) {
+        consume32<T, E, IMAG, HALF>(p, smem, tab, total, abort_flag);
     } else {
-        const int cw = warp - 1;
-        const int tl = lane % T, team = lane / T;
-        const int rit = cw * P + team;  // row within the chunk
-        const int C = p.C;
-        Acc acc[E];
-        int cur = -1;        // problem whose eta terms acc holds
-        int64_t slot = 0;    // its partial slot: this block's first chunk of it
-        Real *Wp = nullptr;  // its W block, row length and first column
-        int ldw = 0, col0 = 0;
-        int64_t k = 0;
-        for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, k++) {
-            const int s = (int)(k % NS);
-            const uint32_t ph = (uint32_t)((k / NS) & 1);
-            const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
-            if (!__all_sync(0xffffffffu, ok))
-                break;
-            const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
-            const volatile int *meta =
-                reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
-            const int len = meta[0], pi = meta[1];
-            const int64_t lt = meta[2];
-            if (pi != cur) {
-                if (cur >= 0 && p.dots)
-                    flush_eta<Real, T, E>(acc, red, tab[cur], slot, cw, n_cw);
-                cur = pi;
-                slot = lt;
-                Wp = static_cast<Real *>(tab[pi].buf[p.parity ^ 1]);
-                ldw = tab[pi].ld;
-                col0 = tab[pi].col0;
-            }
-            using Real2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
-            const Real *vb = reinterpret_cast<const Real *>(st);
-            const Real2 *vals = reinterpret_cast<const Real2 *>(st + p.off_val);
-            const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
-
-            // The old W row is requested from global memory first (the
-            // producer asked L2 for it when it armed the stage): this lane's
-            // 16-byte pieces go to the block's W buffer (the row's slot,
-            // written and read by this lane only) with cp.async, and the
-            // entry loop hides their latency.
-            const int64_t row = lt * (int64_t)C + rit;
-            const int64_t wbase = row * ldw + col0 + tl * EV;
-            Real *wsm = reinterpret_cast<Real *>(smem + p.off_wbuf) + rit * 2 * RB;
-            if (!p.init) {
-#pragma unroll
-                for (int q = 0; q < NP; q++)
-                    cp_async16(smem_u32(wsm + 2 * (q * T * EV + tl * EV)),
-                               Wp + 2 * (wbase + (int64_t)q * T * EV));
-                cp_async_commit();
-            }
-            Real acc_s[2 * E];
-            if constexpr (sizeof(Real) == 4) {
-                // complex float: two packed (re, im) accumulators per
-                // column, a = sum_j Re(h_j) v_j and b = sum_j Im(h_j) v_j, so
-                // each entry costs two paired FMAs per column; then
-                // H' V = (a.re - b.im, a.im + b.re)
-                uint64_t pa[E], pb[E];
-#pragma unroll
-                for (int c = 0; c < E; c++)
-                    pa[c] = pb[c] = 0ull;
-#pragma unroll 4
-                for (int j = 0; j < len; j++) {
-                    const int u = lid[j * C + rit];
-                    const float2 h = vals[j * C + rit];
-                    const uint64_t hx2 = pack2(h.x, h.x), hy2 = pack2(h.y, h.y);
-                    const float *vr = vb + (size_t)u * 2 * RB;
-#pragma unroll
-                    for (int q = 0; q < NP; q++) {
-                        const float4 v4 =
-                            *reinterpret_cast<const float4 *>(vr + 2 * (q * T * EV + tl * EV));
-                        const uint64_t v0 = pack2(v4.x, v4.y);
-                        pa[q * EV] = ffma2(hx2, v0, pa[q * EV]);
-                        pb[q * EV] = ffma2(hy2, v0, pb[q * EV]);
-                        if constexpr (EV == 2) {
-                            const uint64_t v1 = pack2(v4.z, v4.w);
-                            pa[q * EV + 1] = ffma2(hx2, v1, pa[q * EV + 1]);
-                            pb[q * EV + 1] = ffma2(hy2, v1, pb[q * EV + 1]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < E; c++) {
-                    float ar, ai, br, bi;
-                    unpack2(pa[c], ar, ai);
-                    unpack2(pb[c], br, bi);
-                    acc_s[2 * c] = ar - bi;
-                    acc_s[2 * c + 1] = ai + br;
-                }
-            } else {
-                row_product<T, E, HALF>(vb, vals, lid, C, len, rit, tl, acc_s);
-            }
-            if (p.init) {
-#pragma unroll
-                for (int q = 0; q < 2 * E; q++)
-                    acc_s[q] *= Real(0.5);
-            } else {
-                cp_async_wait<0>();
-#pragma unroll
-                for (int q = 0; q < NP; q++) {
-                    Real w[2 * EV];
-                    lds_piece(wsm + 2 * (q * T * EV + tl * EV), w);
-#pragma unroll
-                    for (int i = 0; i < 2 * EV; i++)
-                        acc_s[q * 2 * EV + i] -= w[i];
-                }
-            }
-            store_owned<Real, T, E>(Wp, wbase, acc_s);
-            // the row's own V entries: local position rit of the list
-            if (p.dots) {
-                const Real *ov = vb + (size_t)rit * 2 * RB;
-#pragma unroll
-                for (int q = 0; q < NP; q++) {
-                    Real v[2 * EV];
-                    lds_piece(ov + 2 * (q * T * EV + tl * EV), v);
-#pragma unroll
-                    for (int e = 0; e < EV; e++)
-                        acc[q * EV + e].add(acc_s[q * 2 * EV + 2 * e],
-                                            acc_s[q * 2 * EV + 2 * e + 1], v[2 * e],
-                                            v[2 * e + 1]);
-                }
-                if ((k % kEtaFold) == kEtaFold - 1) {
-#pragma unroll
-                    for (int c = 0; c < E; c++)
-                        acc[c].fold();
-                }
-            }
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(empty0 + 8 * s);
-        }
-        if (!p.dots) {
-            // no scalar products: nothing to write
-        } else if (cur >= 0) {
-            flush_eta<Real, T, E>(acc, red, tab[cur], slot, cw, n_cw);
-        } else if (p.probs == nullptr) {
-            // a single problem's partials are read for every block: a block
-            // without chunks contributes zeros
-            for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
-                tab[0].partial[(int64_t)blockIdx.x * tab[0].ps + t * tab[0].qs] = 0.0;
-        }
+        consume64<T, E, IMAG, HALF>(p, smem, tab, total, abort_flag);
     }
 }
 
@@ -777,26 +1090,30 @@ bool staged_shape_supported(int T, int E, bool fp64)
     return false;
 }
 
-bool staged_layout(int C, int T, int RB, int csize, int u_max, int l_max, int stages,
+bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_max, int stages,
                    int n_probs, size_t max_smem, StagedLayout &o)
 {
     auto up = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
-    if (C < 8 || T < 1 || RB < 1 || RB > 64 || (csize != 8 && csize != 16) || u_max < C ||
+    if (C < 8 || T < 1 || RB < 1 || RB > 64 || (csize != 8 && csize != 16) ||
+        (vsize != 4 && vsize != 8 && vsize != 16) || u_max < C ||
         l_max < 0 || stages < 1 || stages > 8 || n_probs < 1 || (C * T) % 32 != 0 ||
         32 + C * T > KPM_STAGED_MAX_THREADS)
         return false;
     const uint64_t row_bytes = (uint64_t)RB * csize;
     uint64_t off = up((uint64_t)u_max * row_bytes, 128);
     o.off_val = (uint32_t)off;
-    off = up(off + (uint64_t)C * l_max * csize, 128);
+    off = up(off + (uint64_t)C * l_max * vsize, 128);
     o.off_lidx = (uint32_t)off;
     off = up(off + (uint64_t)C * l_max * 2, 128);
     o.stage_bytes = (uint32_t)off;
     o.bar_bytes = (uint32_t)up(kTableOffset + (uint64_t)n_probs * sizeof(StagedProblem), 128);
     o.stages = stages;
-    // after the stages: the block's W buffer, one slot per row of a chunk
-    o.off_wbuf = (uint32_t)(o.bar_bytes + (uint64_t)stages * o.stage_bytes);
-    o.smem = o.off_wbuf + (uint64_t)C * row_bytes;
+    // after the stages: complex double, the block's W buffer (one slot per
+    // row of a chunk); complex float, each consumer warp's eta accumulators
+    // (3 x RB doubles)
+    o.off_aux = (uint32_t)(o.bar_bytes + (uint64_t)stages * o.stage_bytes);
+    const uint64_t n_cw = (uint64_t)C * T / 32;
+    o.smem = o.off_aux + (csize == 16 ? (uint64_t)C * row_bytes : n_cw * 3 * RB * 8);
     return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 
@@ -835,12 +1152,13 @@ int launch_one_staged(const StagedParams &p, int grid, int threads, size_t smem,
 
 }  // namespace
 
-int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64)
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64, bool half)
 {
     const int threads = 32 + C * T;
 #define KPM_CASE(T_, E_) \
     if (T == T_ && E == E_) \
-        return occupancy_of<float, T_, E_, false, false>(threads, smem);
+        return half ? occupancy_of<float, T_, E_, false, true>(threads, smem) \
+                    : occupancy_of<float, T_, E_, false, false>(threads, smem);
 #define KPM_CASE64(T_, E_) \
     if (T == T_ && E == E_) \
         return occupancy_of<double, T_, E_, false, false>(threads, smem);
@@ -858,13 +1176,18 @@ int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t sm
 {
     const int threads = 32 + p.C * T;
     if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8 ||
-        p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1) || (p.half && !p.fp64))
+        p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1))
         return KPM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \
-    if (T == T_ && E == E_)                                                                    \
+    if (T == T_ && E == E_) {                                                                  \
+        if (p.half)                                                                            \
+            return p.with_imag                                                                 \
+                       ? launch_one_staged<float, T_, E_, true, true>(p, grid, threads, smem, st) \
+                       : launch_one_staged<float, T_, E_, false, true>(p, grid, threads, smem, st); \
         return p.with_imag ? launch_one_staged<float, T_, E_, true, false>(p, grid, threads, smem, st) \
-                           : launch_one_staged<float, T_, E_, false, false>(p, grid, threads, smem, st);
+                           : launch_one_staged<float, T_, E_, false, false>(p, grid, threads, smem, st); \
+    }
 #define KPM_CASE64(T_, E_)                                                                     \
     if (T == T_ && E == E_) {                                                                  \
         if (p.half)                                                                            \

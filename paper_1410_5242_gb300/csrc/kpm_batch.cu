@@ -213,7 +213,7 @@ int batch_grid(int n_sm)
 // A class whose problems run the staged kernel (complex float with gather
 // lists): its launch shape and shared-memory layout.
 struct StagedClass {
-    bool on = false;
+    bool on = false, half = false;  // half: the half-complex float form
     int T = 0, E = 4, grid = 0;
     StagedLayout L{};
 };
@@ -348,7 +348,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         int u_max = 0, l_max = 0;
         for (int i = first; i < last && ok; i++) {
             const kpm_ctx *c = ctx[order[i]];
-            ok = c->gather_ok && c->C == c0->C;
+            ok = c->gather_ok && c->C == c0->C && c->half_ok == c0->half_ok;
             u_max = std::max(u_max, c->u_max);
             l_max = std::max(l_max, c->l_max);
         }
@@ -356,16 +356,19 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         // other problems (or the problem table) do not leave room
         bool fits = false;
         for (int ns = ok ? sh.stages : 0; ns >= 1 && !fits; ns--)
-            fits = staged_layout(c0->C, sc.T, RB, 8, u_max, l_max, ns, last - first,
+            fits = staged_layout(c0->C, sc.T, RB, 8, staged_value_bytes(false, c0->half_ok), u_max,
+                                 l_max, ns, last - first,
                                  ctx[0]->max_smem, sc.L);
         ok = ok && fits;
         if (ok) {
             const int bps =
-                staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem, false);
+                staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem, false,
+                                         c0->half_ok);
             sc.grid = bps * ctx[0]->n_sm;
             ok = bps > 0;
         }
         sc.on = ok;
+        sc.half = ok && c0->half_ok;
     }
     for (int i = 0; i < count; i++) {
         int cl = 0;
@@ -420,7 +423,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             sp.rec = c->d_rec;
             sp.ovf = c->d_ovf;
             sp.lidx = c->d_lidx;
-            sp.val = c->d_val;
+            sp.val = c->d_val_staged;
             sp.buf[0] = c->d_V;
             sp.buf[1] = c->d_W;
             sp.partial = c->d_partial;  // [3*RB][slots]
@@ -503,14 +506,15 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.stages = sc.L.stages;
                 q.with_imag = 0;
                 q.init = s == 0 ? 1 : 0;
+                q.half = sc.half ? 1 : 0;
                 q.dots = 1;
-                q.stall_after = -1;
+                q.stall_after = ctx[0]->stall_after;
                 q.err = ctx[0]->d_err;
                 q.bar_bytes = sc.L.bar_bytes;
                 q.stage_bytes = sc.L.stage_bytes;
                 q.off_val = sc.L.off_val;
                 q.off_lidx = sc.L.off_lidx;
-                q.off_wbuf = sc.L.off_wbuf;
+                q.off_aux = sc.L.off_aux;
                 rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
                 if (rc != KPM_OK)
                     break;

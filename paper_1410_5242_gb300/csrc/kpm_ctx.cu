@@ -236,7 +236,8 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
     const int E = fp64 ? 2 : 4;
     if (c->gather_ok && RB >= 8 && RB % E == 0 && staged_shape_supported(RB / E, E, fp64)) {
         StagedLayout L;
-        if (staged_layout(c->C, RB / E, RB, fp64 ? 16 : 8, c->u_max, c->l_max, 2, 1,
+        if (staged_layout(c->C, RB / E, RB, fp64 ? 16 : 8, staged_value_bytes(fp64, c->half_ok),
+                          c->u_max, c->l_max, 2, 1,
                           c->max_smem, L)) {
             s.E = E;
             s.T = RB / E;
@@ -253,14 +254,16 @@ bool shape_layout(const kpm_ctx *c, const LaunchShape &s, StagedLayout &L)
     const bool fp64 = c->precision == KPM_PREC_FP64;
     if (s.stages < 1 || !c->gather_ok || !staged_shape_supported(s.T, s.E, fp64))
         return false;
-    return staged_layout(c->C, s.T, s.T * s.E, fp64 ? 16 : 8, c->u_max, c->l_max, s.stages, 1,
+    return staged_layout(c->C, s.T, s.T * s.E, fp64 ? 16 : 8, staged_value_bytes(fp64, c->half_ok),
+                         c->u_max, c->l_max, s.stages, 1,
                          c->max_smem, L);
 }
 
 // Blocks per SM of a staged shape with layout L.
 int staged_occupancy(const kpm_ctx *c, const LaunchShape &s, const StagedLayout &L)
 {
-    return staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem, c->precision == KPM_PREC_FP64);
+    return staged_max_blocks_per_sm(s.T, s.E, c->C, L.smem, c->precision == KPM_PREC_FP64,
+                                    c->half_ok);
 }
 
 int resolve_grid(kpm_ctx *c, LaunchShape &s)
@@ -388,7 +391,7 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.one.rec = c->d_rec;
         q.one.ovf = c->d_ovf;
         q.one.lidx = c->d_lidx;
-        q.one.val = c->half_ok ? c->d_val_half : c->d_val;
+        q.one.val = c->d_val_staged;
         q.one.buf[0] = const_cast<void *>(p.V);
         q.one.buf[1] = p.W;
         q.one.partial = p.partial;
@@ -407,14 +410,14 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.init = init ? 1 : 0;
         q.dots = dots ? 1 : 0;
         q.fp64 = c->precision == KPM_PREC_FP64 ? 1 : 0;
-        q.half = q.fp64 && c->half_ok ? 1 : 0;
+        q.half = c->half_ok ? 1 : 0;
         q.stall_after = c->stall_after;
         q.err = c->d_err;
         q.bar_bytes = L.bar_bytes;
         q.stage_bytes = L.stage_bytes;
         q.off_val = L.off_val;
         q.off_lidx = L.off_lidx;
-        q.off_wbuf = L.off_wbuf;
+        q.off_aux = L.off_aux;
         return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
     }
     if (c->precision == KPM_PREC_FP64)
@@ -663,19 +666,37 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
     c->upload_bytes = (int64_t)sizeof(int64_t) * (sell.n_chunks + 1) +
                       (int64_t)sizeof(int32_t) * (sell.n_chunks + sell.n_stored + sell.n_pad) +
                       (int64_t)c->sdc * sell.n_stored;
-    // complex double with every stored entry purely real or purely
-    // imaginary: the staged kernel's two-FMA form
-    bool half = c->precision == KPM_PREC_FP64;
+    // every stored entry purely real or purely imaginary: the staged
+    // kernel's two-FMA (half-complex) form
+    bool half = true;
     for (int64_t k = 0; k < sell.n_stored && half; k++)
         half = sell.val_ri[2 * k] == 0.0 || sell.val_ri[2 * k + 1] == 0.0;
     if (sell.C >= 8) {
-        // gather lists for the staged kernel; a matrix whose lists do not fit
-        // the 16-bit local indices keeps the register-path kernel only
+        // gather lists and staged entry arrays for the staged kernel; a
+        // matrix whose lists do not fit the 16-bit local indices keeps the
+        // register-path kernel only
         kpm_gather g;
         const int grc = kpm_gather_build(&sell, &g);
         if (grc == KPM_ENOMEM)
             return fail(KPM_ENOMEM);
         if (grc == KPM_OK) {
+            // complex double: the two-FMA form's operands need bit 15 of the
+            // local indices; complex float: every row's own entry real (else
+            // kpm_staged_build refuses form 3 and the general form is built)
+            const bool fp32 = c->precision == KPM_PREC_FP32;
+            half = half && (fp32 || g.u_max <= 32768);
+            int form = fp32 ? (half ? 3 : 1) : (half ? 2 : 0);
+            kpm_staged sg;
+            int src = kpm_staged_build(&sell, &g, form, &sg);
+            if (src == KPM_EINVAL && form == 3) {
+                half = false;
+                form = 1;
+                src = kpm_staged_build(&sell, &g, form, &sg);
+            }
+            if (src != KPM_OK) {
+                kpm_gather_release(&g);
+                return fail(src);
+            }
             // producer records: fixed 256-byte entries, runs past the inline
             // ones in the overflow array
             std::vector<int2> rec, ovf;
@@ -683,11 +704,14 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                 rec.assign((size_t)g.n_chunks * KPM_REC_WORDS, make_int2(0, 0));
                 for (int64_t ch = 0; ch < g.n_chunks; ch++) {
                     int2 *r = &rec[(size_t)ch * KPM_REC_WORDS];
-                    const int64_t e0 = sell.chunk_ptr[ch];
+                    const int64_t e0 = sg.chunk_ptr[ch];
                     const int64_t q0 = g.run_ptr[ch], nr = g.run_ptr[ch + 1] - q0;
                     const int64_t of = (int64_t)ovf.size();
                     r[0] = make_int2((int)(uint32_t)e0, (int)(e0 >> 32));
-                    r[1] = make_int2(sell.chunk_len[ch], (int)nr);
+                    // staged length, and (half-complex float) the real
+                    // region's length in the upper 16 bits
+                    const int nre = sg.chunk_nre ? sg.chunk_nre[ch] : 0;
+                    r[1] = make_int2(sg.chunk_len[ch] | (nre << 16), (int)nr);
                     r[2] = make_int2((int)(uint32_t)of, (int)(of >> 32));
                     for (int64_t q = 0; q < nr; q++) {
                         const int2 run = make_int2(g.runs[2 * (q0 + q)], g.runs[2 * (q0 + q) + 1]);
@@ -698,63 +722,36 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                     }
                 }
             } catch (const std::bad_alloc &) {
+                kpm_staged_release(&sg);
                 kpm_gather_release(&g);
                 return fail(KPM_ENOMEM);
             }
-            // The two-FMA form's operands: entry h = (r, 0) is stored as
-            // (r, r) and adds (r x, r y); h = (0, m) as (-m, m) with bit 15 of
-            // its local index set, and adds (-m y, m x): the kernel reads the
-            // V row's halves in swapped order for it.  Lists of more than
-            // 32768 rows keep the four-FMA form.
-            std::vector<double> hv;
-            half = half && g.u_max <= 32768;
-            if (half) {
-                try {
-                    hv.resize(2 * (size_t)sell.n_stored);
-                } catch (const std::bad_alloc &) {
-                    kpm_gather_release(&g);
-                    return fail(KPM_ENOMEM);
-                }
-                for (int64_t e = 0; e < sell.n_stored; e++) {
-                    const double re = sell.val_ri[2 * e], im = sell.val_ri[2 * e + 1];
-                    const bool imag = re == 0.0;
-                    hv[2 * e] = imag ? -im : re;
-                    hv[2 * e + 1] = imag ? im : re;
-                    if (imag)
-                        g.lidx[e] = (uint16_t)(g.lidx[e] | 0x8000u);
-                }
-                c->d_val_half = dev_alloc(c, 16 * sell.n_stored);
-                if (!c->d_val_half) {
-                    kpm_gather_release(&g);
-                    return fail(KPM_ENOMEM);
-                }
-                if (cudaMemcpy(c->d_val_half, hv.data(), 16 * sell.n_stored,
-                               cudaMemcpyHostToDevice) != cudaSuccess) {
-                    kpm_gather_release(&g);
-                    return fail(KPM_ECUDA);
-                }
-                c->upload_bytes += 16 * sell.n_stored;
-            }
-            c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sell.n_stored);
+            const size_t vbytes = (size_t)staged_value_bytes(!fp32, half) * sg.n_stored;
+            c->d_val_staged = dev_alloc(c, vbytes);
+            c->d_lidx = (uint16_t *)dev_alloc(c, sizeof(uint16_t) * sg.n_stored);
             c->d_rec = (int2 *)dev_alloc(c, sizeof(int2) * rec.size());
             c->d_ovf = (int2 *)dev_alloc(c, sizeof(int2) * (ovf.empty() ? 1 : ovf.size()));
-            const bool alloc_ok = c->d_lidx && c->d_rec && c->d_ovf;
+            const bool alloc_ok = c->d_val_staged && c->d_lidx && c->d_rec && c->d_ovf;
+            const void *vsrc = sg.valf ? (const void *)sg.valf : (const void *)sg.val;
             const bool ok =
                 alloc_ok &&
-                cudaMemcpy(c->d_lidx, g.lidx, sizeof(uint16_t) * sell.n_stored,
+                cudaMemcpy(c->d_val_staged, vsrc, vbytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                cudaMemcpy(c->d_lidx, sg.lidx, sizeof(uint16_t) * sg.n_stored,
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 cudaMemcpy(c->d_rec, rec.data(), sizeof(int2) * rec.size(),
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 (ovf.empty() || cudaMemcpy(c->d_ovf, ovf.data(), sizeof(int2) * ovf.size(),
                                            cudaMemcpyHostToDevice) == cudaSuccess);
             c->u_max = g.u_max;
-            c->l_max = g.l_max;
+            c->l_max = sg.l_max;
+            const int64_t n_staged = sg.n_stored;
+            kpm_staged_release(&sg);
             kpm_gather_release(&g);
             if (!ok)
                 return fail(alloc_ok ? KPM_ECUDA : KPM_ENOMEM);
             c->gather_ok = true;
             c->half_ok = half;
-            c->upload_bytes += (int64_t)sizeof(uint16_t) * sell.n_stored +
+            c->upload_bytes += (int64_t)vbytes + (int64_t)sizeof(uint16_t) * n_staged +
                                (int64_t)sizeof(int2) * (int64_t)(rec.size() + ovf.size());
             // complex double: the staged kernel's widest block is 32 columns
             // (wider rows would leave room for one stage only), and two
@@ -785,7 +782,7 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_eta);
     dev_free(c, c->d_eta_im);
     dev_free(c, c->d_lidx);
-    dev_free(c, c->d_val_half);
+    dev_free(c, c->d_val_staged);
     dev_free(c, c->d_aux);
     dev_free(c, c->d_rec);
     dev_free(c, c->d_ovf);

@@ -706,3 +706,258 @@ void kpm_gather_release(kpm_gather *g)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ staged entry arrays
+namespace kpm {
+namespace {
+
+// Offset (in entries) of entry j < n of row r in a region of n entries per
+// row laid out in groups of 8, then of 4, 2 and 1 entries (the binary digits
+// of n mod 8), each group row-major (see kpm_staged in kpm.h).
+int64_t group_offset(int64_t C, int n, int j, int64_t r)
+{
+    const int full = n & ~7;
+    if (j < full)
+        return C * (j & ~7) + 8 * r + (j & 7);
+    int base = full;
+    for (int g = 4; g >= 1; g >>= 1) {
+        if ((n - full) & g) {
+            if (j < base + g)
+                return C * base + g * r + (j - base);
+            base += g;
+        }
+    }
+    return -1;  // not reached for j < n
+}
+
+// Offset of the index of entry j of row r within its chunk (forms 0-2: the
+// first len - 1 entries grouped, the own entry last).
+int64_t staged_index_offset(int64_t C, int len, int j, int64_t r)
+{
+    const int nm = len - 1;
+    return j == nm ? C * nm + r : group_offset(C, nm, j, r);
+}
+
+// Offset (in complex numbers) of the value of entry j of row r: form 1
+// pairs entries j, j+1 for even j below (len - 1) rounded down to even.
+int64_t staged_value_offset(int64_t C, int len, int j, int64_t r, int form)
+{
+    if (form == 1) {
+        const int np = (len - 1) & ~1;
+        if (j < np)
+            return C * (j & ~1) + 2 * r + (j & 1);
+    }
+    return C * j + r;
+}
+
+}  // namespace
+}  // namespace kpm
+
+extern "C" {
+
+int kpm_staged_build(const kpm_sell *s, const kpm_gather *g, int32_t form, kpm_staged *out)
+{
+    if (!out)
+        return KPM_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (!s || !g || form < 0 || form > 3 || !s->chunk_ptr || !s->chunk_len || s->C < 8 ||
+        g->n_chunks != s->n_chunks || (s->n_stored > 0 && (!s->col || !s->val_ri || !g->lidx)))
+        return KPM_EINVAL;
+    if (form == 2 && g->u_max > 32768)
+        return KPM_EINVAL;
+    const int64_t C = s->C, n_chunks = s->n_chunks;
+    // the last SELL entry of row r of chunk c that reads the row's own V row
+    auto own_entry = [&](int64_t c, int64_t r) {
+        int own = -1;
+        for (int j = 0; j < s->chunk_len[c]; j++)
+            if (s->col[s->chunk_ptr[c] + (int64_t)j * C + r] == c * C + r)
+                own = j;
+        return own;
+    };
+    if (form >= 2) {
+        // every entry purely real or purely imaginary; form 3: own entries real
+        std::atomic<bool> bad(false);
+        parallel_parts(n_chunks, 1 << 10, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t c = lo; c < hi && !bad; c++)
+                for (int64_t r = 0; r < C; r++) {
+                    for (int j = 0; j < s->chunk_len[c]; j++) {
+                        const int64_t e = s->chunk_ptr[c] + (int64_t)j * C + r;
+                        if (s->val_ri[2 * e] != 0.0 && s->val_ri[2 * e + 1] != 0.0)
+                            bad = true;
+                    }
+                    const int own = own_entry(c, r);
+                    if (form == 3 && own >= 0 &&
+                        s->val_ri[2 * (s->chunk_ptr[c] + (int64_t)own * C + r) + 1] != 0.0)
+                        bad = true;
+                }
+        });
+        if (bad)
+            return KPM_EINVAL;
+    }
+    int64_t *chunk_ptr = (int64_t *)std::malloc(sizeof(int64_t) * (n_chunks + 1));
+    int32_t *chunk_len = (int32_t *)std::malloc(sizeof(int32_t) * (n_chunks ? n_chunks : 1));
+    int32_t *chunk_nre = form == 3 ? (int32_t *)std::malloc(sizeof(int32_t) * (n_chunks ? n_chunks : 1))
+                                   : nullptr;
+    if (!chunk_ptr || !chunk_len || (form == 3 && !chunk_nre)) {
+        std::free(chunk_ptr);
+        std::free(chunk_len);
+        std::free(chunk_nre);
+        return KPM_ENOMEM;
+    }
+    auto is_imag = [&](int64_t e) { return s->val_ri[2 * e] == 0.0 && s->val_ri[2 * e + 1] != 0.0; };
+    parallel_parts(n_chunks, 1 << 10, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; c++) {
+            const int len = s->chunk_len[c];
+            if (form == 3) {
+                // real region: the largest count of real entries besides the
+                // own one; imaginary region: the largest count of imaginary
+                int n_re = 0, n_im = 0;
+                for (int64_t r = 0; r < C; r++) {
+                    const int own = own_entry(c, r);
+                    int re = 0, im = 0;
+                    for (int j = 0; j < len; j++) {
+                        if (j == own)
+                            continue;
+                        if (is_imag(s->chunk_ptr[c] + (int64_t)j * C + r))
+                            im++;
+                        else
+                            re++;
+                    }
+                    n_re = std::max(n_re, re);
+                    n_im = std::max(n_im, im);
+                }
+                chunk_nre[c] = n_re;
+                chunk_len[c] = n_re + n_im + 1;
+                continue;
+            }
+            bool all_own = len > 0;
+            for (int64_t r = 0; r < C && all_own; r++)
+                all_own = own_entry(c, r) >= 0;
+            chunk_len[c] = len + (all_own ? 0 : 1);
+        }
+    });
+    chunk_ptr[0] = 0;
+    int32_t l_max = 0;
+    for (int64_t c = 0; c < n_chunks; c++) {
+        chunk_ptr[c + 1] = chunk_ptr[c] + C * chunk_len[c];
+        l_max = std::max(l_max, chunk_len[c]);
+    }
+    const int64_t n_stored = chunk_ptr[n_chunks];
+    const int64_t nv = form == 3 ? n_stored : 2 * n_stored;  // value words
+    uint16_t *lidx = (uint16_t *)std::malloc(sizeof(uint16_t) * (n_stored ? n_stored : 1));
+    double *val = (form == 0 || form == 2) ? (double *)std::malloc(sizeof(double) * (nv ? nv : 1))
+                                           : nullptr;
+    float *valf = (form == 1 || form == 3) ? (float *)std::malloc(sizeof(float) * (nv ? nv : 1))
+                                           : nullptr;
+    if (!lidx || (!val && !valf)) {
+        std::free(chunk_ptr);
+        std::free(chunk_len);
+        std::free(chunk_nre);
+        std::free(lidx);
+        std::free(val);
+        std::free(valf);
+        return KPM_ENOMEM;
+    }
+    parallel_parts(n_chunks, 1 << 9, [&](int64_t lo, int64_t hi, int) {
+        std::vector<int> order;
+        for (int64_t c = lo; c < hi; c++) {
+            const int len = s->chunk_len[c], len_s = chunk_len[c];
+            const int64_t e0 = s->chunk_ptr[c], s0 = chunk_ptr[c];
+            for (int64_t r = 0; r < C; r++) {
+                const int own = own_entry(c, r);
+                // staged entry k of this row: SELL entry j (or -1: value 0,
+                // own row), written at index offset io and value offset vo
+                auto put = [&](int j, int64_t io, int64_t vo) {
+                    double re = 0.0, im = 0.0;
+                    uint16_t li = (uint16_t)r;
+                    if (j >= 0) {
+                        const int64_t e = e0 + (int64_t)j * C + r;
+                        re = s->val_ri[2 * e];
+                        im = s->val_ri[2 * e + 1];
+                        li = g->lidx[e];
+                    }
+                    if (form == 1) {
+                        valf[2 * (s0 + vo)] = (float)re;
+                        valf[2 * (s0 + vo) + 1] = (float)im;
+                    } else if (form == 3) {
+                        valf[s0 + vo] = (float)(im != 0.0 ? im : re);
+                    } else if (form == 0) {
+                        val[2 * (s0 + vo)] = re;
+                        val[2 * (s0 + vo) + 1] = im;
+                    } else {
+                        const bool imag = re == 0.0 && im != 0.0;
+                        val[2 * (s0 + vo)] = imag ? -im : re;
+                        val[2 * (s0 + vo) + 1] = imag ? im : re;
+                        if (imag)
+                            li = (uint16_t)(li | 0x8000u);
+                    }
+                    lidx[s0 + io] = li;
+                };
+                if (form == 3) {
+                    const int n_re = chunk_nre[c], n_im = len_s - 1 - n_re;
+                    int kr = 0, ki = 0;
+                    for (int j = 0; j < len; j++) {
+                        if (j == own)
+                            continue;
+                        if (is_imag(e0 + (int64_t)j * C + r)) {
+                            const int64_t o = C * n_re + group_offset(C, n_im, ki++, r);
+                            put(j, o, o);
+                        } else {
+                            const int64_t o = group_offset(C, n_re, kr++, r);
+                            put(j, o, o);
+                        }
+                    }
+                    while (kr < n_re) {
+                        const int64_t o = group_offset(C, n_re, kr++, r);
+                        put(-1, o, o);
+                    }
+                    while (ki < n_im) {
+                        const int64_t o = C * n_re + group_offset(C, n_im, ki++, r);
+                        put(-1, o, o);
+                    }
+                    put(own, C * (len_s - 1) + r, C * (len_s - 1) + r);
+                    continue;
+                }
+                const int vf = form == 1 ? 1 : 0;
+                int k = 0;
+                auto put_k = [&](int j) {
+                    put(j, staged_index_offset(C, len_s, k, r),
+                        staged_value_offset(C, len_s, k, r, vf));
+                    k++;
+                };
+                for (int j = 0; j < len; j++)
+                    if (j != own)
+                        put_k(j);
+                while (k < len_s - 1)
+                    put_k(-1);
+                put_k(own);
+            }
+        }
+    });
+    out->n_chunks = n_chunks;
+    out->n_stored = n_stored;
+    out->l_max = l_max;
+    out->form = form;
+    out->chunk_ptr = chunk_ptr;
+    out->chunk_len = chunk_len;
+    out->chunk_nre = chunk_nre;
+    out->lidx = lidx;
+    out->val = val;
+    out->valf = valf;
+    return KPM_OK;
+}
+
+void kpm_staged_release(kpm_staged *st)
+{
+    if (!st)
+        return;
+    std::free(st->chunk_ptr);
+    std::free(st->chunk_len);
+    std::free(st->chunk_nre);
+    std::free(st->lidx);
+    std::free(st->val);
+    std::free(st->valf);
+    std::memset(st, 0, sizeof(*st));
+}
+
+}  // extern "C"

@@ -40,22 +40,25 @@ struct SweepParams {
 #define KPM_DEVERR_TIMEOUT 1
 
 // Per-chunk producer record of the staged kernel: 32 int2 (256 bytes),
-// [0] = first stored entry of the chunk (int64 as lo, hi), [1] = (chunk_len,
-// run count), [2] = index of run KPM_REC_INLINE_RUNS in the overflow array
-// (int64), [3 + q] = run q (first row, row count) for q < KPM_REC_INLINE_RUNS.
+// [0] = first entry of the chunk in the staged entry arrays (int64 as lo,
+// hi), [1] = (staged chunk length, run count), [2] = index of run
+// KPM_REC_INLINE_RUNS in the overflow array (int64), [3 + q] = run q (first
+// row, row count) for q < KPM_REC_INLINE_RUNS.
 #define KPM_REC_WORDS 32
 #define KPM_REC_INLINE_RUNS 29
 
 // One problem of a staged launch: its arrays, where its chunks sit in the
 // launch's global tile sequence, and where its eta partials go (slot s,
 // entry t = q*RB + r at partial[s*ps + t*qs]; slot = the first chunk of the
-// problem a block handled, so slots < min(grid, n_tiles)).
+// problem a block handled, so slots < min(grid, n_tiles)).  The entry
+// arrays are the staged ones (kpm_staged in kpm.h: per row the own entry
+// last, indices in groups of 8/4/2/1, complex float values in pairs).
 struct StagedProblem {
     const int2 *rec;       // [n_tiles][KPM_REC_WORDS]
     const int2 *ovf;       // runs beyond the inline ones
-    const uint16_t *lidx;  // [n_stored] local positions (SELL order)
-    const void *val;       // [n_stored] values (SELL order): complex float or double,
-                           // or the half-complex form's operand pairs
+    const uint16_t *lidx;  // staged local indices
+    const void *val;       // staged values: complex float, complex double, or
+                           // the half-complex form's operand pairs
     void *buf[2];          // vector blocks: V = buf[parity], W = buf[parity ^ 1]
     double *partial;
     int64_t tile0, n_tiles;
@@ -68,11 +71,13 @@ static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte
 // Arguments of one staged sweep (aug_spmmv_staged.cu) over a table of
 // problems (probs, n_probs entries, in device memory) or the single problem
 // `one` (probs = NULL, n_probs = 1), and the shared-memory layout of one
-// stage: V rows [u_max][RB] at 0, values [l_max][C] at off_val, local
-// indices [l_max][C] at off_lidx (SELL order, column-major in the chunk).  Stages start at bar_bytes; the barriers, each
-// stage's chunk length, problem and chunk number, the record ring, the eta
-// sum and the problem table sit before them, the block's W buffer (C rows
-// of RB columns) after them at off_wbuf.
+// stage: V rows [u_max][RB] at 0, the chunk's staged values at off_val and
+// staged local indices at off_lidx (l_max * C entries each).  Stages start
+// at bar_bytes; the barriers, each stage's chunk length, the record ring,
+// the eta sum and the problem table sit before them; after them, at
+// off_aux, the block's W buffer (complex double: C rows of RB columns) or
+// the consumer warps' eta accumulators (complex float: 3 x RB doubles per
+// consumer warp).
 struct StagedParams {
     StagedProblem one;
     const StagedProblem *probs;
@@ -82,24 +87,31 @@ struct StagedParams {
     int64_t stall_after;  // >= 0: the producer stops after this many chunks per
                           // block (test of the bounded waits); -1: never
     int *err;  // device error word (KPM_DEVERR_*)
-    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux;
     int32_t fp64;  // complex double (else complex float)
-    int32_t half;  // complex double, every stored entry purely real or imaginary
+    int32_t half;  // every stored entry purely real or imaginary (the half-complex form)
 };
 
 // The shared-memory layout of a staged launch; false if fewer than
 // min_stages stages fit in max_smem bytes.
 struct StagedLayout {
-    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_wbuf;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux;
     int stages;
     size_t smem;
 };
-// csize: bytes of one complex number (8 or 16).
-bool staged_layout(int C, int T, int RB, int csize, int u_max, int l_max, int stages,
+// csize: bytes of one complex number of the vector blocks (8 or 16);
+// vsize: bytes of one staged value (staged_value_bytes).
+bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_max, int stages,
                    int n_probs, size_t max_smem, StagedLayout &out);
 bool staged_shape_supported(int T, int E, bool fp64);
 int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream);
-int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64);
+int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64, bool half);
+// Bytes of one staged value: complex double or its operand pair (16),
+// complex float (8), one float of the complex float half form (4).
+inline int staged_value_bytes(bool fp64, bool half)
+{
+    return fp64 ? 16 : (half ? 4 : 8);
+}
 
 // stages = 0: the register-path kernel of aug_spmmv.cuh with `threads` per
 // block; stages >= 1: the staged kernel of aug_spmmv_staged.cu with that
@@ -193,9 +205,9 @@ struct kpm_ctx {
     // contexts: the staged kernel's two-FMA form, with its own operand
     // array and bit 15 of d_lidx marking the imaginary entries)
     bool half_ok = false;
-    void *d_val_half = nullptr;  // [n_stored] (a, b) operand pairs
+    void *d_val_staged = nullptr;  // staged values (kpm_staged; form by precision and half_ok)
     int64_t upload_bytes = 0;    // host -> device bytes kpm_create copied
-    uint16_t *d_lidx = nullptr;  // [n_stored] local positions (SELL order)
+    uint16_t *d_lidx = nullptr;  // staged local indices (kpm_staged)
     int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;
     int32_t u_max = 0, l_max = 0;

@@ -68,6 +68,16 @@ class Launch(ctypes.Structure):
                 ("tile_groups", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
+class Staged(ctypes.Structure):
+    _fields_ = [("n_chunks", ctypes.c_int64), ("n_stored", ctypes.c_int64),
+                ("l_max", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("chunk_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("chunk_len", ctypes.POINTER(ctypes.c_int32)),
+                ("chunk_nre", ctypes.POINTER(ctypes.c_int32)),
+                ("lidx", ctypes.POINTER(ctypes.c_uint16)), ("val", ctypes.POINTER(ctypes.c_double)),
+                ("valf", ctypes.POINTER(ctypes.c_float))]
+
+
 class Gather(ctypes.Structure):
     _fields_ = [("n_chunks", ctypes.c_int64), ("n_runs", ctypes.c_int64),
                 ("u_max", ctypes.c_int32), ("l_max", ctypes.c_int32),
@@ -93,6 +103,9 @@ _SIGS = {
     "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
     "kpm_gather_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather)]),
     "kpm_gather_release": (None, [ctypes.POINTER(Gather)]),
+    "kpm_staged_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather), _i32,
+                                ctypes.POINTER(Staged)]),
+    "kpm_staged_release": (None, [ctypes.POINTER(Staged)]),
     "kpm_check_device_error": (_int, [_vp]),
     "kpm_test_stall_staged": (_int, [_vp, _i64]),
     "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
@@ -253,6 +266,67 @@ def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
     finally:
         lib.kpm_sell_release(ctypes.byref(s))
     return sell, gat
+
+
+STAGED_FP64, STAGED_FP32, STAGED_HALF, STAGED_HALF32 = 0, 1, 2, 3
+
+
+def staged_build(csr, a, b, form, C=32, sigma=256, row_order=None):
+    """The SELL layout (as sell_build), the gather lists (as gather_build) and
+    the staged kernel's entry arrays of kpm_staged_build for `form` (0 complex
+    double, 1 complex float, 2 half-complex double, 3 half-complex float):
+    (sell, gather, staged) with staged = {"chunk_ptr", "chunk_len",
+    "chunk_nre" (form 3, else None), "l_max", "lidx", "val"} -- val a
+    complex numpy array for forms 0-2 (float values widened), the real
+    float64 array of the stored floats for form 3."""
+    n, rp, col, val = _csr(csr)
+    s = Sell()
+    order = None if row_order is None else np.ascontiguousarray(row_order, dtype=np.int32)
+    _check(lib.kpm_sell_build(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), a, b, C, sigma,
+                              _p(order, _i32) if order is not None else None, ctypes.byref(s)),
+           "kpm_sell_build")
+    g = Gather()
+    st = Staged()
+    try:
+        sell = _sell_dict(s)
+        _check(lib.kpm_gather_build(ctypes.byref(s), ctypes.byref(g)), "kpm_gather_build")
+        try:
+            gat = {
+                "u_max": g.u_max, "l_max": g.l_max,
+                "lidx": np.ctypeslib.as_array(g.lidx, (max(s.n_stored, 1),))[:s.n_stored].copy(),
+                "run_ptr": np.ctypeslib.as_array(g.run_ptr, (g.n_chunks + 1,)).copy(),
+                "runs": np.ctypeslib.as_array(g.runs, (max(2 * g.n_runs, 1),))[:2 * g.n_runs]
+                .copy().reshape(-1, 2),
+            }
+            _check(lib.kpm_staged_build(ctypes.byref(s), ctypes.byref(g), form, ctypes.byref(st)),
+                   "kpm_staged_build")
+            try:
+                ns = st.n_stored
+                if form == STAGED_HALF32:
+                    v = np.ctypeslib.as_array(st.valf, (max(ns, 1),))[:ns].astype(np.float64)
+                elif form == STAGED_FP32:
+                    v = np.ctypeslib.as_array(st.valf, (max(2 * ns, 2),))[:2 * ns].copy()
+                    v = v.astype(np.float64).view(np.complex128)
+                else:
+                    v = np.ctypeslib.as_array(st.val, (max(2 * ns, 2),))[:2 * ns].copy()
+                    v = v.view(np.complex128)
+                stg = {
+                    "n_stored": ns, "l_max": st.l_max,
+                    "chunk_ptr": np.ctypeslib.as_array(st.chunk_ptr, (st.n_chunks + 1,)).copy(),
+                    "chunk_len": np.ctypeslib.as_array(st.chunk_len, (max(st.n_chunks, 1),))
+                    [:st.n_chunks].copy(),
+                    "chunk_nre": (np.ctypeslib.as_array(st.chunk_nre, (max(st.n_chunks, 1),))
+                                  [:st.n_chunks].copy() if form == STAGED_HALF32 else None),
+                    "lidx": np.ctypeslib.as_array(st.lidx, (max(ns, 1),))[:ns].copy(),
+                    "val": v,
+                }
+            finally:
+                lib.kpm_staged_release(ctypes.byref(st))
+        finally:
+            lib.kpm_gather_release(ctypes.byref(g))
+    finally:
+        lib.kpm_sell_release(ctypes.byref(s))
+    return sell, gat, stg
 
 
 def _sell_dict(s):

@@ -184,3 +184,49 @@ def test_staged_bounded_wait_expires_and_context_recovers(kpm):
         got, got_eta = sweep(ctx, R, V, W, False)
     assert np.array_equal(got, want)
     assert np.array_equal(got_eta, want_eta)
+
+
+def test_staged_bounded_wait_in_a_two_problem_ensemble(kpm):
+    """The bounded waits of a staged launch over a table of two problems (one
+    ensemble class).  With two lattices of 256 chunks each and between 256
+    and 512 blocks, each block's second chunk belongs to the second problem,
+    so in the stalled launch the consumer warps cross a problem boundary --
+    and the eta flush there, the only barrier among them -- at the stage
+    that never arrives.  The launches must end with KPM_ETIMEOUT (every wait
+    gives up, no barrier is left short), and a batch built afterwards on the
+    same contexts gives the moments of one built before, bit for bit."""
+    import time
+
+    import torch
+    R, M = 32, 4
+    ctxs = []
+    for seed in (1, 2):
+        h = ham.ti_hamiltonian(16, 16, 8, gamma=0.5, seed=seed)  # 256 chunks of 32 rows
+        a, b = scaled(h, kpm)
+        ctxs.append(kpm.create(h, a, b, precision=kpm.PREC_FP32))
+    launch = ctxs[0].get_launch(R)
+    assert launch["stages"] >= 1
+    grid = launch["blocks_per_sm"] * torch.cuda.get_device_properties(0).multi_processor_count
+    assert 256 < grid < 512, grid
+    try:
+        with kpm.Batch(ctxs, [M, M], [R, R], [5, 6]) as batch:
+            batch.launch()
+            want = [batch.eta(0), batch.eta(1)]
+        ctxs[0].test_stall_staged(1)  # captured by batches built from now on
+        with kpm.Batch(ctxs, [M, M], [R, R], [5, 6]) as batch:
+            t0 = time.perf_counter()
+            batch.launch()
+            with pytest.raises(kpm.KPMError) as e:
+                batch.eta(0)
+            waited = time.perf_counter() - t0
+        assert e.value.status == kpm.KPM_ETIMEOUT
+        assert 0.5 < waited < 60.0
+        ctxs[0].test_stall_staged(-1)
+        with kpm.Batch(ctxs, [M, M], [R, R], [5, 6]) as batch:
+            batch.launch()
+            got = [batch.eta(0), batch.eta(1)]
+    finally:
+        for c in ctxs:
+            c.close()
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)

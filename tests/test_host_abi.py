@@ -401,3 +401,157 @@ def test_gershgorin_does_not_depend_on_the_host_thread_count(kpm, monkeypatch):
         monkeypatch.setenv("KPM_HOST_THREADS", t)
         got.append(kpm.gershgorin(h))
     assert got[1] == got[0] and got[2] == got[0]
+
+
+def _region_offsets(C, n, r):
+    """Offsets of row r's entries 0..n-1 in a region of n entries per row
+    laid out as documented: groups of 8, then of 4, 2, 1 (binary digits of
+    n mod 8), a group of g entries starting at j holding row r's entries at
+    C*j + g*r."""
+    out, j = [], 0
+    while j + 8 <= n:
+        out += [C * j + 8 * r + e for e in range(8)]
+        j += 8
+    for g in (4, 2, 1):
+        if n - j >= g:
+            out += [C * j + g * r + e for e in range(g)]
+            j += g
+    return out
+
+
+def _staged_offsets(C, L, r):
+    """Index and value offsets (within a chunk of staged length L) of row r's
+    entries j = 0..L-1 as the staged layout is documented: the first L - 1
+    indices in groups of 8, then of 4, 2, 1 (binary digits of (L-1) mod 8),
+    the last (own) entry's index at C*(L-1) + r; complex float values in
+    pairs below (L-1) rounded down to even, others at C*j + r."""
+    nm = L - 1
+    idx, j = [], 0
+    while j + 8 <= nm:
+        idx += [C * j + 8 * r + e for e in range(8)]
+        j += 8
+    for g in (4, 2, 1):
+        if nm - j >= g:
+            idx += [C * j + g * r + e for e in range(g)]
+            j += g
+    idx.append(C * nm + r)
+    np2 = nm & ~1
+    valf = [C * (j & ~1) + 2 * r + (j & 1) if j < np2 else C * j + r for j in range(L)]
+    vald = [C * j + r for j in range(L)]
+    return np.array(idx), np.array(valf), np.array(vald)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("C", [8, 32])
+def test_staged_arrays_hold_each_row_with_its_own_entry_last(kpm, form, C):
+    """kpm_staged_build: decoded through the documented layout and the gather
+    lists, every row's staged entries are its SELL entries (values rounded to
+    float for complex float, operand pairs for the half-complex form) plus
+    zero fillers, the last one reading the row's own V row, and the offsets
+    of a chunk cover it exactly once."""
+    mats = [(ham.ti_hamiltonian(5, 4, 3, gamma=0.7, seed=3), 0.1, 0.3),
+            # b = 0 and rows without a diagonal: chunks get one more entry
+            (ham.random_hermitian(203, 5, seed=4, empty_rows=0.05, diag=False), 0.1, 0.0)]
+    if form == 2:  # the half-complex form needs real or imaginary entries
+        mats = mats[:1] + [(ham.ti_hamiltonian(4, 4, 3, gamma=0.0, seed=1), 0.1, 0.0)]
+    for m, a, b in mats:
+        sell, gat, stg = kpm.staged_build(m, a, b, form, C=C, sigma=1)
+        for c in range(sell["n_chunks"]):
+            rows = _expand_runs(gat, c)
+            L0, L = sell["chunk_len"][c], stg["chunk_len"][c]
+            e0, s0 = sell["chunk_ptr"][c], stg["chunk_ptr"][c]
+            assert stg["chunk_ptr"][c + 1] - s0 == C * L
+            own_missing = False
+            covered_i, covered_v = [], []
+            for r in range(C):
+                p = c * C + r
+                sel = [e0 + j * C + r for j in range(L0)]
+                has_own = any(sell["col"][e] == p for e in sel)
+                own_missing |= not has_own
+                oi, ovf, ovd = _staged_offsets(C, L, r)
+                covered_i += list(oi)
+                covered_v += list(ovf if form == 1 else ovd)
+                li = stg["lidx"][s0 + oi].astype(np.int64)
+                vals = stg["val"][s0 + (ovf if form == 1 else ovd)]
+                if form == 2:
+                    imag = (li & 0x8000) != 0
+                    li = li & 0x7FFF
+                    # operand pairs back to the complex values
+                    assert np.all(vals[~imag].real == vals[~imag].imag)
+                    assert np.all(vals[imag].real == -vals[imag].imag)
+                    vals = np.where(imag, 1j * vals.imag, vals.real + 0j)
+                cols = rows[li]
+                assert cols[-1] == p  # the own entry comes last
+                want = sell["val"][sel]
+                if form == 1:
+                    want = want.astype(np.complex64).astype(np.complex128)
+                got_nz = sorted((int(x), complex(v)) for x, v in zip(cols, vals) if v != 0)
+                want_nz = sorted((int(x), complex(v)) for x, v in
+                                 zip(sell["col"][sel], want) if v != 0)
+                assert got_nz == want_nz
+                # zero entries read the row's own V row only where SELL had
+                # padding or a filler was added
+                zero_cols = [x for x, v in zip(cols, vals) if v == 0]
+                assert all(x == p for x in zero_cols) or any(
+                    v == 0 for v in sell["val"][sel])
+            assert L == L0 + (1 if own_missing else 0)
+            assert sorted(covered_i) == list(range(C * L))
+            assert sorted(covered_v) == list(range(C * L))
+        assert stg["l_max"] == stg["chunk_len"].max()
+
+
+def test_staged_build_rejects_full_complex_entries_in_the_half_form(kpm):
+    h = ham.random_hermitian(64, 4, seed=2)  # general complex off-diagonals
+    with pytest.raises(kpm.KPMError) as e:
+        kpm.staged_build(h, 0.1, 0.0, kpm.STAGED_HALF, C=8, sigma=1)
+    assert e.value.status == kpm.KPM_EINVAL
+
+
+def test_half_float_staged_arrays_split_real_and_imaginary_entries(kpm):
+    """kpm_staged_build, form 3 (half-complex float): decoded through the
+    documented two-region layout, every row holds its real SELL entries in
+    the real region, its imaginary ones in the imaginary region (one float
+    each), zero fillers on its own index, and its own entry last; the
+    offsets of a chunk cover it exactly once."""
+    C = 32
+    for m, a, b in ((ham.ti_hamiltonian(5, 4, 3, gamma=0.7, seed=3), 0.1, 0.3),
+                    (ham.ti_hamiltonian(3, 4, 5, gamma=0.0, seed=1,
+                                        periodic=(True, True, False)), 0.2, 0.0)):
+        sell, gat, stg = kpm.staged_build(m, a, b, kpm.STAGED_HALF32, C=C, sigma=1)
+        for c in range(sell["n_chunks"]):
+            rows = _expand_runs(gat, c)
+            L0, L, nA = sell["chunk_len"][c], stg["chunk_len"][c], stg["chunk_nre"][c]
+            nB = L - 1 - nA
+            e0, s0 = sell["chunk_ptr"][c], stg["chunk_ptr"][c]
+            assert stg["chunk_ptr"][c + 1] - s0 == C * L
+            covered = []
+            for r in range(C):
+                p = c * C + r
+                offA = _region_offsets(C, nA, r)
+                offB = [C * nA + o for o in _region_offsets(C, nB, r)]
+                own = C * (L - 1) + r
+                covered += offA + offB + [own]
+                colA = rows[stg["lidx"][s0 + np.array(offA, dtype=np.int64)]] if nA else []
+                colB = rows[stg["lidx"][s0 + np.array(offB, dtype=np.int64)]] if nB else []
+                assert rows[stg["lidx"][s0 + own]] == p
+                got = [(int(x), complex(v, 0)) for x, v in zip(colA, stg["val"][s0 + np.array(offA, dtype=np.int64)]) if v != 0] if nA else []
+                got += [(int(x), complex(0, v)) for x, v in zip(colB, stg["val"][s0 + np.array(offB, dtype=np.int64)]) if v != 0] if nB else []
+                if stg["val"][s0 + own] != 0:
+                    got.append((p, complex(stg["val"][s0 + own], 0)))
+                sel = [e0 + j * C + r for j in range(L0)]
+                want = sell["val"][sel].astype(np.complex64).astype(np.complex128)
+                want_nz = [(int(x), complex(v)) for x, v in zip(sell["col"][sel], want) if v != 0]
+                assert sorted(got) == sorted(want_nz)
+                # fillers read the row's own V row
+                for cols, offs in ((colA, offA), (colB, offB)):
+                    for x, o in zip(cols, offs):
+                        if stg["val"][s0 + o] == 0:
+                            assert x == p or any(v == 0 for v in sell["val"][sel])
+            assert sorted(covered) == list(range(C * L))
+
+
+def test_half_float_staged_build_rejects_full_complex_entries(kpm):
+    h = ham.random_hermitian(64, 4, seed=2)
+    with pytest.raises(kpm.KPMError) as e:
+        kpm.staged_build(h, 0.1, 0.0, kpm.STAGED_HALF32, C=8, sigma=1)
+    assert e.value.status == kpm.KPM_EINVAL
