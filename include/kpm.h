@@ -514,7 +514,9 @@ void kpm_naive_destroy(kpm_naive *nv);
  * Sec. "Application Scenario"), the staged kernel multiplies with two real
  * FMAs per entry and column instead of four in both forms (the skipped
  * products are exact zeros, so W is the same); complex float then stores
- * one float per entry. */
+ * one float per entry.  Complex float stages also carry the chunk's old W
+ * rows where the larger stages keep the number of blocks per SM (else each
+ * lane loads its old W a chunk ahead). */
 typedef struct kpm_launch {
     int32_t lanes_per_row, cols_per_lane, block_threads, blocks_per_sm, tile_groups;
     int32_t stages;  /* 0: register-path kernel (block_threads per block, tile_groups);

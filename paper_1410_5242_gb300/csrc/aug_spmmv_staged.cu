@@ -273,15 +273,17 @@ struct WarpEta {
             pend[i] = 0.f;
         }
     }
-    // after fold(): this lane's running sums to the warp's accumulators acc
-    // (double [3][RB], column c of quantity q at q*RB + c), then cleared
-    __device__ __forceinline__ void store(double *acc, int tl, int team)
+    // after fold(): this lane's running sums added to red (double [3][RB],
+    // column c of quantity q at q*RB + c), or written if first; then cleared
+    __device__ __forceinline__ void add_to(double *red, int tl, int team, bool first)
     {
 #pragma unroll
         for (int i = 0; i < NV; i++) {
-            if (team == i % P)
-                acc[(i / E) * (T * E) + owned_column<float, T, E>(tl, i % E)] =
-                    (double)hi[i / P] + (double)lo[i / P];
+            if (team == i % P) {
+                double &d = red[(i / E) * (T * E) + owned_column<float, T, E>(tl, i % E)];
+                const double v = (double)hi[i / P] + (double)lo[i / P];
+                d = first ? v : d + v;
+            }
         }
 #pragma unroll
         for (int i = 0; i < KH; i++)
@@ -425,7 +427,10 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const uint32_t st = stage0 + (uint32_t)s * p.stage_bytes;
         const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * (uint32_t)VSIZE;
         const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
-        const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes;
+        // the chunk's old W rows with the stage (complex float, off_w set)
+        const bool w_in_stage = p.off_w != 0 && !p.init;
+        const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes +
+                               (w_in_stage ? (uint32_t)p.C * row_bytes : 0u);
         if (lane == 0) {
             volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
@@ -439,10 +444,14 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             if (lane == 1)
                 bulk_g2s(st + p.off_lidx, lidxb + e0 * 2, lidx_bytes, full);
         }
-        // the consumers read the chunk's old W rows themselves; ask L2 for
-        // them now (whole rows: contiguous, 16-byte multiples)
-        if (!p.init && lane == 2 && ((int64_t)ld * CSIZE & 15) == 0)
+        if (w_in_stage) {
+            if (lane == 2)
+                copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, ld, col0, row_bytes, full, CSIZE);
+        } else if (!p.init && lane == 2 && ((int64_t)ld * CSIZE & 15) == 0) {
+            // the consumers read the chunk's old W rows themselves; ask L2
+            // for them now (whole rows: contiguous, 16-byte multiples)
             prefetch_l2(Wb + lt * (int64_t)p.C * ld * CSIZE, (uint64_t)p.C * ld * CSIZE);
+        }
         if (has_run && count > 0)
             copy_rows(st + (uint32_t)(incl - count) * row_bytes, Vb, word.x, count, ld, col0,
                       row_bytes, full, CSIZE);
@@ -471,24 +480,23 @@ __device__ __forceinline__ void consumer_bar(int n_cw)
     asm volatile("bar.sync 1, %0;" ::"r"(n_cw * 32) : "memory");
 }
 
-// Complex float: one problem's eta sums from the consumer warps'
-// accumulators (acc0: n_cw blocks of [3][RB] doubles, written by
-// WarpEta::store), summed in warp order into the problem's partial slot;
-// the accumulators are cleared.
-template <int RB>
-__device__ __forceinline__ void flush_eta32(double *acc0, const StagedProblem &P, int64_t slot,
-                                            int cw, int n_cw)
+// Complex float: one problem's eta sums, warp after warp into red (3*RB
+// doubles) from each warp's running pairs, then red to the problem's
+// partial slot.  The caller has folded its pending terms.
+template <int T, int E, bool IMAG>
+__device__ __forceinline__ void flush_eta32(WarpEta<IMAG, T, E> &pe, double *red,
+                                            const StagedProblem &P, int64_t slot, int cw, int n_cw)
 {
+    constexpr int RB = T * E;
     const int lane = threadIdx.x & 31;
-    consumer_bar(n_cw);
-    for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32) {
-        double s = 0.0;
-        for (int w = 0; w < n_cw; w++) {
-            s += acc0[w * 3 * RB + t];
-            acc0[w * 3 * RB + t] = 0.0;
-        }
-        P.partial[slot * P.ps + t * P.qs] = s;
+    const int tl = lane % T, team = lane / T;
+    for (int w = 0; w < n_cw; w++) {
+        if (cw == w)
+            pe.add_to(red, tl, team, w == 0);
+        consumer_bar(n_cw);
     }
+    for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
+        P.partial[slot * P.ps + t * P.qs] = (!IMAG && t >= 2 * RB) ? 0.0 : red[t];
     consumer_bar(n_cw);
 }
 
@@ -668,12 +676,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
     const int C = p.C, NS = p.stages;
     const int64_t G = gridDim.x;
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
-    double *acc0 = reinterpret_cast<double *>(smem + p.off_aux);
-    double *accw = acc0 + cw * 3 * RB;
-    for (int i = lane; i < 3 * RB; i += 32)
-        accw[i] = 0.0;
-    __syncwarp();
-
+    double *red = reinterpret_cast<double *>(smem + kRedOffset);
     WarpEta<IMAG, T, E> pe;
     pe.clear();
     int nfold = 0;
@@ -706,9 +709,8 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         if (cp.pi != cp.cur) {
             if (cp.cur >= 0 && p.dots) {
                 pe.fold(team);
-                pe.store(accw, tl, team);
                 nfold = 0;
-                flush_eta32<RB>(acc0, tab[cp.cur], cp.slot, cw, n_cw);
+                flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
             }
             cp.cur = cp.pi;
             cp.slot = lt;
@@ -718,7 +720,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         }
         if (failed)
             continue;
-        if (!p.init && !have_w)
+        if (!p.init && !p.off_w && !have_w)
             load_w(gt, cp.pi);
         const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -814,6 +816,14 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             for (int i = 0; i < 2 * E; i++)
                 w[i] *= 0.5f;
         } else {
+            if (p.off_w) {
+                // the old W rows came with the stage
+                const float *ws = reinterpret_cast<const float *>(st + p.off_w) + (size_t)rit * 2 * RB +
+                                  2 * tl * EV;
+#pragma unroll
+                for (int q = 0; q < NP; q++)
+                    wo[q] = *reinterpret_cast<const float4 *>(ws + 2 * q * T * EV);
+            }
 #pragma unroll
             for (int q = 0; q < NP; q++) {
                 w[4 * q] -= wo[q].x;
@@ -826,7 +836,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, w);
         // the next tile's old W, while this one's scalar products are added
         have_w = false;
-        if (!p.init && gt + G < total) {
+        if (!p.init && !p.off_w && gt + G < total) {
             load_w(gt + G, advance_problem(tab, p.n_probs, cp.pi, gt + G));
             have_w = true;
         }
@@ -849,8 +859,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         return;
     if (cp.cur >= 0) {
         pe.fold(team);
-        pe.store(accw, tl, team);
-        flush_eta32<RB>(acc0, tab[cp.cur], cp.slot, cw, n_cw);
+        flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
     } else if (p.probs == nullptr) {
         // a single problem's partials are read for every block: a block
         // without chunks contributes zeros
@@ -1091,11 +1100,11 @@ bool staged_shape_supported(int T, int E, bool fp64)
 }
 
 bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_max, int stages,
-                   int n_probs, size_t max_smem, StagedLayout &o)
+                   int n_probs, bool wstage, size_t max_smem, StagedLayout &o)
 {
     auto up = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
     if (C < 8 || T < 1 || RB < 1 || RB > 64 || (csize != 8 && csize != 16) ||
-        (vsize != 4 && vsize != 8 && vsize != 16) || u_max < C ||
+        (vsize != 4 && vsize != 8 && vsize != 16) || (wstage && csize != 8) || u_max < C ||
         l_max < 0 || stages < 1 || stages > 8 || n_probs < 1 || (C * T) % 32 != 0 ||
         32 + C * T > KPM_STAGED_MAX_THREADS)
         return false;
@@ -1105,15 +1114,19 @@ bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_
     off = up(off + (uint64_t)C * l_max * vsize, 128);
     o.off_lidx = (uint32_t)off;
     off = up(off + (uint64_t)C * l_max * 2, 128);
+    o.off_w = 0;
+    if (wstage) {
+        // the chunk's old W rows (complex float)
+        o.off_w = (uint32_t)off;
+        off = up(off + (uint64_t)C * row_bytes, 128);
+    }
     o.stage_bytes = (uint32_t)off;
     o.bar_bytes = (uint32_t)up(kTableOffset + (uint64_t)n_probs * sizeof(StagedProblem), 128);
     o.stages = stages;
     // after the stages: complex double, the block's W buffer (one slot per
-    // row of a chunk); complex float, each consumer warp's eta accumulators
-    // (3 x RB doubles)
+    // row of a chunk); complex float nothing
     o.off_aux = (uint32_t)(o.bar_bytes + (uint64_t)stages * o.stage_bytes);
-    const uint64_t n_cw = (uint64_t)C * T / 32;
-    o.smem = o.off_aux + (csize == 16 ? (uint64_t)C * row_bytes : n_cw * 3 * RB * 8);
+    o.smem = o.off_aux + (csize == 16 ? (uint64_t)C * row_bytes : 0);
     return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 

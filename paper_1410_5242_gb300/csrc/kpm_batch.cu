@@ -353,17 +353,26 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             l_max = std::max(l_max, c->l_max);
         }
         // the class's stage count, or fewer where the wider gather lists of
-        // other problems (or the problem table) do not leave room
+        // other problems (or the problem table) do not leave room; the old
+        // W rows travel with the stages where that keeps the blocks per SM
         bool fits = false;
+        const int vs = staged_value_bytes(false, c0->half_ok);
         for (int ns = ok ? sh.stages : 0; ns >= 1 && !fits; ns--)
-            fits = staged_layout(c0->C, sc.T, RB, 8, staged_value_bytes(false, c0->half_ok), u_max,
-                                 l_max, ns, last - first,
+            fits = staged_layout(c0->C, sc.T, RB, 8, vs, u_max, l_max, ns, last - first, false,
                                  ctx[0]->max_smem, sc.L);
         ok = ok && fits;
         if (ok) {
-            const int bps =
-                staged_max_blocks_per_sm(sc.T, sc.E, ctx[order[first]]->C, sc.L.smem, false,
-                                         c0->half_ok);
+            int bps = staged_max_blocks_per_sm(sc.T, sc.E, c0->C, sc.L.smem, false, c0->half_ok);
+            StagedLayout Lw;
+            if (staged_layout(c0->C, sc.T, RB, 8, vs, u_max, l_max, sc.L.stages, last - first, true,
+                              ctx[0]->max_smem, Lw)) {
+                const int bw = staged_max_blocks_per_sm(sc.T, sc.E, c0->C, Lw.smem, false,
+                                                        c0->half_ok);
+                if (bw >= bps && bw > 0) {
+                    sc.L = Lw;
+                    bps = bw;
+                }
+            }
             sc.grid = bps * ctx[0]->n_sm;
             ok = bps > 0;
         }
@@ -515,6 +524,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.off_val = sc.L.off_val;
                 q.off_lidx = sc.L.off_lidx;
                 q.off_aux = sc.L.off_aux;
+                q.off_w = sc.L.off_w;
                 rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
                 if (rc != KPM_OK)
                     break;

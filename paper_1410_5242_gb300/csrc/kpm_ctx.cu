@@ -211,6 +211,26 @@ std::vector<int> column_widths(int R, int cap)
     return w;
 }
 
+// Complex float staged shapes: the old W rows travel with each stage (the
+// producer copies them, the consumers read them from shared memory) where
+// the larger stages keep the same number of blocks per SM; otherwise each
+// consumer lane loads its row's old W into registers a chunk ahead.
+int choose_wstage(const kpm_ctx *c, const LaunchShape &s)
+{
+    if (c->precision != KPM_PREC_FP32 || s.stages < 1 || !c->gather_ok)
+        return 0;
+    const int vs = staged_value_bytes(false, c->half_ok);
+    StagedLayout L0, L1;
+    if (!staged_layout(c->C, s.T, s.T * s.E, 8, vs, c->u_max, c->l_max, s.stages, 1, false,
+                       c->max_smem, L0) ||
+        !staged_layout(c->C, s.T, s.T * s.E, 8, vs, c->u_max, c->l_max, s.stages, 1, true,
+                       c->max_smem, L1))
+        return 0;
+    const int o0 = staged_max_blocks_per_sm(s.T, s.E, c->C, L0.smem, false, c->half_ok);
+    const int o1 = staged_max_blocks_per_sm(s.T, s.E, c->C, L1.smem, false, c->half_ok);
+    return o1 >= o0 && o1 > 0 ? 1 : 0;
+}
+
 LaunchShape default_shape(const kpm_ctx *c, int RB)
 {
     LaunchShape s;
@@ -237,11 +257,11 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
     if (c->gather_ok && RB >= 8 && RB % E == 0 && staged_shape_supported(RB / E, E, fp64)) {
         StagedLayout L;
         if (staged_layout(c->C, RB / E, RB, fp64 ? 16 : 8, staged_value_bytes(fp64, c->half_ok),
-                          c->u_max, c->l_max, 2, 1,
-                          c->max_smem, L)) {
+                          c->u_max, c->l_max, 2, 1, false, c->max_smem, L)) {
             s.E = E;
             s.T = RB / E;
             s.stages = 2;
+            s.wstage = choose_wstage(c, s);
         }
     }
     return s;
@@ -255,7 +275,7 @@ bool shape_layout(const kpm_ctx *c, const LaunchShape &s, StagedLayout &L)
     if (s.stages < 1 || !c->gather_ok || !staged_shape_supported(s.T, s.E, fp64))
         return false;
     return staged_layout(c->C, s.T, s.T * s.E, fp64 ? 16 : 8, staged_value_bytes(fp64, c->half_ok),
-                         c->u_max, c->l_max, s.stages, 1,
+                         c->u_max, c->l_max, s.stages, 1, s.wstage != 0,
                          c->max_smem, L);
 }
 
@@ -418,6 +438,7 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
         q.off_val = L.off_val;
         q.off_lidx = L.off_lidx;
         q.off_aux = L.off_aux;
+        q.off_w = L.off_w;
         return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
     }
     if (c->precision == KPM_PREC_FP64)
@@ -1094,6 +1115,7 @@ std::vector<LaunchShape> shape_candidates(const kpm_ctx *c, int RB)
         for (int ns = 1; ns <= 3; ns++) {
             LaunchShape s{T, E, 128, 0, 1};
             s.stages = ns;
+            s.wstage = choose_wstage(c, s);
             StagedLayout L;
             if (shape_layout(c, s, L) &&
                 staged_occupancy(c, s, L) > 0)
@@ -1320,6 +1342,7 @@ int kpm_set_launch(kpm_ctx *c, int32_t R, const kpm_launch *l)
                   l->tile_groups > 0 ? l->tile_groups : 4};
     s.stages = l->stages;
     DeviceGuard guard(c->device);
+    s.wstage = choose_wstage(c, s);
     if (s.stages > 0) {
         StagedLayout L;
         if (!shape_layout(c, s, L) || staged_occupancy(c, s, L) < 1)

@@ -75,9 +75,9 @@ static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte
 // staged local indices at off_lidx (l_max * C entries each).  Stages start
 // at bar_bytes; the barriers, each stage's chunk length, the record ring,
 // the eta sum and the problem table sit before them; after them, at
-// off_aux, the block's W buffer (complex double: C rows of RB columns) or
-// the consumer warps' eta accumulators (complex float: 3 x RB doubles per
-// consumer warp).
+// off_aux, the block's W buffer (complex double: C rows of RB columns).
+// off_w != 0 (complex float): each stage also holds the chunk's old W rows
+// at off_w, copied by the producer.
 struct StagedParams {
     StagedProblem one;
     const StagedProblem *probs;
@@ -87,7 +87,7 @@ struct StagedParams {
     int64_t stall_after;  // >= 0: the producer stops after this many chunks per
                           // block (test of the bounded waits); -1: never
     int *err;  // device error word (KPM_DEVERR_*)
-    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux, off_w;
     int32_t fp64;  // complex double (else complex float)
     int32_t half;  // every stored entry purely real or imaginary (the half-complex form)
 };
@@ -95,14 +95,15 @@ struct StagedParams {
 // The shared-memory layout of a staged launch; false if fewer than
 // min_stages stages fit in max_smem bytes.
 struct StagedLayout {
-    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux;
+    uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux, off_w;
     int stages;
     size_t smem;
 };
 // csize: bytes of one complex number of the vector blocks (8 or 16);
-// vsize: bytes of one staged value (staged_value_bytes).
+// vsize: bytes of one staged value (staged_value_bytes); wstage: the old W
+// rows travel with each stage (complex float only).
 bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_max, int stages,
-                   int n_probs, size_t max_smem, StagedLayout &out);
+                   int n_probs, bool wstage, size_t max_smem, StagedLayout &out);
 bool staged_shape_supported(int T, int E, bool fp64);
 int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream);
 int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64, bool half);
@@ -119,6 +120,7 @@ inline int staged_value_bytes(bool fp64, bool half)
 struct LaunchShape {
     int T, E, threads, blocks_per_sm, tile_groups;
     int stages = 0;
+    int wstage = 0;  // staged complex float: the old W rows travel with each stage
 };
 
 // Launch one sweep of the given shape; grid = blocks_per_sm * n_sm.
@@ -247,4 +249,5 @@ int launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t st);
 int launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, int64_t n_pad, int R,
                       int ld, uint64_t seed, int n_sm, cudaStream_t st);
 LaunchShape default_shape(const kpm_ctx *c, int RB);
+int choose_wstage(const kpm_ctx *c, const LaunchShape &s);
 }  // namespace kpm
