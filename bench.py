@@ -318,6 +318,7 @@ def bench_ours(args, world, rank, local):
     k32_gbs = k32_bytes / t_k32 / 1e9
     traffic32 = measured_traffic("fp32")
     launch32 = ctx32.get_launch(R4)
+    half32 = bool(ctx32.info()["half_complex"])
 
     fp32_err = None
     if rank == 0 and not args.skip_accuracy:
@@ -331,17 +332,21 @@ def bench_ours(args, world, rank, local):
             t32s = kernel_only(ctx32, Rs, max(10, args.kernel_launches // 2), stream)
             b64 = model.sweep_bytes(n, nnz, Rs, 16)
             b32 = model.sweep_bytes(h4["n"], nnz4, Rs, 8)
+            # the widest column block's shape (complex double splits R = 64
+            # into two 32-wide blocks): lanes per row x columns per lane,
+            # blocks per SM, stages
+            shape = {}
+            for nm_, c_ in (("fp64", ctx), ("fp32", ctx32)):
+                L = c_.get_launch(min(Rs, c_.max_block_width()))
+                shape[nm_] = "%dx%d b%d s%d" % (L["lanes_per_row"], L["cols_per_lane"],
+                                                L["blocks_per_sm"], L["stages"])
             r_sweep.append({
                 "R": Rs, "B_min_fp64_bytes_per_flop": round(model.code_balance(nnz / n, Rs), 3),
                 "fp64_ms": round(t64 * 1e3, 4), "fp64_GBs": round(b64 / t64 / 1e9, 1),
                 "fp64_TFLOPs": round(model.fused_fp64_flops(nnz, n, Rs, half=half) / t64 / 1e12,
                                      4),
                 "fp32_ms": round(t32s * 1e3, 4), "fp32_GBs": round(b32 / t32s / 1e9, 1),
-                "fp32_frac_hbm": round(b32 / t32s / 1e9 / hbm_peak, 4),
-                # the widest column block's shape (complex double splits R = 64
-                # into two 32-wide blocks)
-                "launch_fp64": ctx.get_launch(min(Rs, ctx.max_block_width())),
-                "launch_fp32": ctx32.get_launch(min(Rs, ctx32.max_block_width()))})
+                "fp32_frac_hbm": round(b32 / t32s / 1e9 / hbm_peak, 4), "shape": shape})
 
     # ---------------- optimisation stages of the paper on this GPU
     ablation = None
@@ -367,6 +372,11 @@ def bench_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(h, a, b, cfg)
+
+    # ---------------- the 240 x 240 x 120 lattice (N = 1 only: it holds ~60 GB)
+    large = None
+    if world == 1 and not args.skip_large:
+        large = large_rate(kpm, stream, hbm_peak, peak_src)
 
     sweeps = M // 2
     out = {
@@ -399,6 +409,7 @@ def bench_ours(args, world, rank, local):
             "bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
             "traffic": traffic,
+            "traffic_source": traffic_source("fp64", traffic),
             # the FP64 pipe's busy fraction in the same ncu capture (the flop
             # count above leaves out the old-W subtraction and the 1/2 of the
             # initial sweep)
@@ -420,9 +431,10 @@ def bench_ours(args, world, rank, local):
             "speedup_per_sweep_vs_fp64": round((t_step / sweeps) / (t32 / (M4 // 2)), 3),
             "roofline": {"bound": "hbm", "achieved": round(k32_gbs, 1), "peak": hbm_peak,
                          "unit": "GB/s", "frac": round(k32_gbs / hbm_peak, 4),
-                         "traffic": traffic32, "avg_launch_ms": round(t_k32 * 1e3, 4),
+                         "traffic": traffic32, "traffic_source": traffic_source("fp32", traffic32),
+                         "avg_launch_ms": round(t_k32 * 1e3, 4),
                          "algorithmic_bytes": k32_bytes,
-                         "kernel": kernel_name("fp32", launch32),
+                         "kernel": kernel_name("fp32", launch32, half32),
                          "launch": launch32,
                          "peak_source": "HBM %s %.0f GB/s" % (peak_src, hbm_peak)},
             "accuracy": fp32_err,
@@ -431,15 +443,57 @@ def bench_ours(args, world, rank, local):
         "ablation": ablation,
         "ensemble": ens,
         "spectral_function": spectral,
+        "large": large,
         "e2e": e2e,
         "gpu_launches": launches * world,
         "clocks": clock_info,
         "cpu_baseline": cpu,
     }
+    out["summary"] = summary(out)
     ctx.close()
     ctx32.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def traffic_source(form, traffic):
+    if traffic is None:
+        return ("none: profiles/aug_spmmv_traffic.txt was taken on other kernel sources "
+                "(hash %s now)" % kernel_hash(form))
+    return "ncu record in profiles/aug_spmmv_traffic.txt, kernel hash %s" % kernel_hash(form)
+
+
+def summary(out):
+    """The figures the targets name, last on the line: the FP32-storage form's
+    roofline fraction, speed-up and error, the FP64 form's pipe fraction, the
+    240x240x120 lattice in both forms, the ensemble and the R sweep."""
+    def r(x, k=4):
+        return None if x is None else round(x, k)
+    fp = out["fp32_form"]
+    acc = fp.get("accuracy") or {}
+    sm = {"fp64_sweep_frac_of_fp64_peak": out["roofline"]["frac"],
+          "fp64_sweep_hbm_frac": out["roofline"]["hbm_frac"],
+          "fp32_sweep_frac_of_hbm": fp["roofline"]["frac"],
+          "fp32_sweep_ms": fp["roofline"]["avg_launch_ms"],
+          "fp32_speedup_per_sweep_vs_fp64": fp["speedup_per_sweep_vs_fp64"],
+          "fp32_max_abs_dmu_vs_oracle": acc.get("max_abs_dmu_vs_oracle"),
+          "fp32_dos_l1_vs_oracle": acc.get("dos_l1_vs_oracle"),
+          "fp32_max_abs_dmu_vs_gpu_fp64": acc.get("max_abs_dmu_vs_gpu_fp64"),
+          "fp64_max_abs_dmu_vs_oracle": acc.get("fp64_form_max_abs_dmu_vs_oracle")}
+    if out["r_sweep"]:
+        sm["r_sweep_fp32_frac"] = {str(e["R"]): e["fp32_frac_hbm"] for e in out["r_sweep"]}
+    lg = out.get("large")
+    if lg:
+        sm["large_240x240x120"] = {
+            "fp64_frac_of_fp64_peak": lg["fp64"].get("frac_of_fp64_peak"),
+            "fp64_hbm_frac": lg["fp64"]["frac_of_hbm_peak"],
+            "fp32_frac_of_hbm": lg["fp32"]["frac_of_hbm_peak"],
+            "fp32_max_abs_dmu_vs_fp64": r(lg["fp32_max_abs_dmu_vs_fp64"], 12),
+            "fp32_dos_l1_vs_fp64": r(lg["fp32_dos_l1_vs_fp64"], 9),
+            "fp64_mu0_minus_1": r(lg["fp64"]["checks"]["mu0_minus_1"], 16)}
+    if out.get("ensemble"):
+        sm["ensemble_frac_of_hbm"] = out["ensemble"]["frac_of_hbm_peak"]
+    return sm
 
 
 def ablation_stages(kpm, h, a, b, ctx, ctx32, n, nnz, n4, nnz4, stream):
@@ -673,45 +727,88 @@ def bench_reference(args, world, rank):
     print(json.dumps(out))
 
 
-def large_lattice(args):
-    """The 240 x 240 x 120 lattice (N = 27,648,000 rows, 359M entries; the
-    single-GPU roofline workload): the sweep kernel alone at R = 32 in both
-    forms, CUDA events on the launching stream.  Not part of the default run
-    (building the lattice and its layouts takes a few minutes of host time)."""
+def moment_checks(kpm, eta, eti):
+    """Invariants of the moments that hold at any size (Sec. "Problem
+    Description" and the recurrence of Eq. 3): mu_0 = 1, Im eta = 0 for a
+    Hermitian H, eta_2m = <nu_m|nu_m> >= 0, and |c_n| <= eta_0 per vector
+    (the spectrum of a(H - b) lies in [-1, 1])."""
+    eta0 = eta[:, :1]
+    c = eta.copy()
+    c[:, 2::2] = 2 * eta[:, 2::2] - eta0
+    c[:, 3::2] = 2 * eta[:, 3::2] - eta[:, 1:2]
+    return {"mu0_minus_1": float(kpm.eta_to_mu(eta)[0] - 1.0),
+            "max_abs_im_eta_over_eta0": float(np.abs(eti).max() / eta0.min()),
+            "min_eta_even_over_eta0": float((eta[:, 0::2] / eta0).min()),
+            "max_abs_c_over_eta0": float(np.abs(c / eta0).max())}
+
+
+def large_rate(kpm, stream, hbm_peak, peak_src, launches64=5, launches32=20):
+    """The 240 x 240 x 120 lattice (N = 27,648,000 rows, 359M entries, gamma
+    = 2, seed 2; the single-GPU roofline workload): in both forms the sweep
+    kernel alone at R = 32 (CUDA events on the launching stream) and one
+    KPM-DOS run of M = 1024 moments through kpm_moments (host output), the
+    invariants of the FP64 moments, and the FP32 form's moment and DOS
+    error against them.  Parity against the CPU oracle on this lattice is a
+    GPU test (columns 0, 1, 16, 31)."""
     import torch
-    from paper_1410_5242_gb300 import build
-    build.build()
-    from paper_1410_5242_gb300 import kpm
     cfg = workloads.TI_LARGE
     t0 = time.perf_counter()
     h, a, b = ti_problem(cfg)
     t_build = time.perf_counter() - t0
-    n, R = h["n"], cfg["R"]
-    stream = torch.cuda.current_stream()
-    hbm_peak, peak_src = peaks()
-    out = {"workload": "TI lattice 240x240x120 (N=%d, nnz=%d), R=%d, gamma=%g, seed %d"
-                       % (n, len(h["col"]), R, cfg["gamma"], cfg["seed"]),
+    n, R, M, seed = h["n"], cfg["R"], cfg["M"], cfg["seed"]
+    out = {"workload": "TI lattice 240x240x120 (N=%d, nnz=%d), R=%d, M=%d, gamma=%g, seed %d"
+                       % (n, len(h["col"]), R, M, cfg["gamma"], seed),
            "lattice_build_s": round(t_build, 1)}
-    for name, prec, sd, launches in (("fp64", kpm.PREC_FP64, 16, 5), ("fp32", kpm.PREC_FP32, 8, 20)):
+    etas = {}
+    for name, prec, sd, launches in (("fp64", kpm.PREC_FP64, 16, launches64),
+                                     ("fp32", kpm.PREC_FP32, 8, launches32)):
         t0 = time.perf_counter()
         ctx = kpm.create(h, a, b, precision=prec)
         t_create = time.perf_counter() - t0
-        nnz = ctx.info()["nnz"]
+        info = ctx.info()
+        nnz = info["nnz"]
         t = kernel_only(ctx, R, launches, stream)
         byt = model.sweep_bytes(n, nnz, R, sd)
         entry = {"create_s": round(t_create, 1), "launch": ctx.get_launch(R),
+                 "half_complex": bool(info["half_complex"]),
                  "avg_launch_ms": round(t * 1e3, 3), "algorithmic_bytes": byt,
                  "GBs": round(byt / t / 1e9, 1), "frac_of_hbm_peak": round(byt / t / 1e9 / hbm_peak, 4)}
         if prec == kpm.PREC_FP64:
-            fl = model.fused_fp64_flops(nnz, n, R, half=bool(ctx.info()["half_complex"]))
+            fl = model.fused_fp64_flops(nnz, n, R, half=bool(info["half_complex"]))
             entry["TFLOPs"] = round(fl / t / 1e12, 4)
             entry["frac_of_fp64_peak"] = round(fl / t / 1e12 / FP64_PEAK_TFLOPS, 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eta, eti = ctx.moments(M, R, seed, imag=True, stream=stream)
+        t_run = time.perf_counter() - t0
+        entry["run_s"] = round(t_run, 3)
+        entry["run_GBs"] = round(run_bytes(n, nnz, R, M, sd) / t_run / 1e9, 1)
+        etas[name] = eta
+        if prec == kpm.PREC_FP64:
+            entry["checks"] = moment_checks(kpm, eta, eti)
         out[name] = entry
         ctx.close()
+        del ctx
         torch.cuda.empty_cache()
+    mu64, mu32 = kpm.eta_to_mu(etas["fp64"]), kpm.eta_to_mu(etas["fp32"])
+    _, r64 = kpm.dos(mu64, 4096, a, b)
+    _, r32 = kpm.dos(mu32, 4096, a, b)
+    out["fp32_max_abs_dmu_vs_fp64"] = float(np.abs(mu32 - mu64).max())
+    out["fp32_dos_l1_vs_fp64"] = float(np.abs(r32 - r64).sum() / np.abs(r64).sum())
     out["peak_source"] = "HBM %s %.0f GB/s; FP64 %.2f TFLOP/s nominal" % (peak_src, hbm_peak,
                                                                          FP64_PEAK_TFLOPS)
-    print(json.dumps({"large_lattice": out}))
+    return out
+
+
+def large_lattice(args):
+    """--large: only the 240 x 240 x 120 lattice leg (see large_rate)."""
+    import torch
+    from paper_1410_5242_gb300 import build
+    build.build()
+    from paper_1410_5242_gb300 import kpm
+    hbm_peak, peak_src = peaks()
+    print(json.dumps({"large_lattice": large_rate(kpm, torch.cuda.current_stream(), hbm_peak,
+                                                  peak_src)}))
 
 
 def profile_sweeps(args):
@@ -746,6 +843,8 @@ def main():
     ap.add_argument("--skip-r-sweep", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--skip-spectral", action="store_true")
+    ap.add_argument("--skip-large", action="store_true",
+                    help="leave out the 240x240x120 lattice leg (a few minutes of host setup)")
     ap.add_argument("--ensemble-runs", type=int, default=1)
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")

@@ -12,7 +12,8 @@ import numpy as np
 import pytest
 
 from kpm_inputs import hamiltonians as ham
-from kpm_inputs import vectors, workloads
+from kpm_inputs import vectors
+from kpm_inputs import workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -276,3 +277,49 @@ def test_full_size_moments_sampled_columns(kpm, orc, ti64, prec):
     else:
         dmu = np.abs(kpm.eta_to_mu(got) - orc.eta_to_mu(ref)).max()
         assert dmu <= FP32_MU_TOL, dmu
+
+
+def test_config2_full_moment_count_sampled_columns(kpm, orc, ti64):
+    """The bench workload in full: 64^3 lattice, complex double, M = 2000,
+    R = 32, seed 1, the bench's layout and launch.  Columns 0 and 31 over all
+    2000 moments against the oracle (R11 of the readings: 1e-10 eta_0, and
+    1e-10 relative where |eta| >= 1e-3 eta_0).  At this grid the eta
+    partials of about 570 sweeps fit one reduction batch, so the 1000 sweeps
+    cross a batch boundary; batches of 300 sweeps must give the same
+    moments bit for bit (each sweep's partials are summed in block order,
+    whatever the batch)."""
+    cfg, h = ti64
+    a, b = scaled(h, kpm)
+    M, R, seed = cfg["M"], cfg["R"], cfg["seed"]
+    assert M == 2000
+    with kpm.create(h, a, b, chunk_height=cfg["chunk_height"], sigma=cfg["sigma"]) as ctx:
+        eta = ctx.moments(M, R, seed)
+        ctx.set_reduce_interval(300)
+        eta300 = ctx.moments(M, R, seed)
+    assert np.array_equal(eta, eta300)
+    ref, _ = orc.moments(h, a, b, M, seed, [0, 31], threads=2)
+    check_eta_fp64(eta[[0, 31]], ref)
+
+
+def test_config4_recipe_against_the_oracle(kpm, orc):
+    """The precision form's own recipe: 64^3 lattice (gamma 1, seed 2),
+    complex float storage, M = 1024, R = 32; vectors 0 and 1 against the
+    FP64 oracle: max |d mu_n| <= 1e-5 and the Jackson DOS on K = 4096
+    Chebyshev nodes within 1e-4 in relative L1 (a 1e-5 error in every
+    moment could move it by up to (1 + 4(M-1)/pi) * 1e-5 = 1.3e-2; the
+    errors measured are far smaller and of no fixed sign)."""
+    cfg = workloads.TI_64_FP32
+    h = ham.ti_hamiltonian(*cfg["dims"], gamma=cfg["gamma"], seed=cfg["seed"])
+    a, b = scaled(h, kpm)
+    M, R, seed = cfg["M"], cfg["R"], cfg["seed"]
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32, chunk_height=32, sigma=256) as ctx:
+        eta = ctx.moments(M, R, seed)
+    cols = [0, 1]
+    ref, _ = orc.moments(h, a, b, M, seed, cols, threads=2)
+    mu_g, mu_o = kpm.eta_to_mu(eta[cols]), orc.eta_to_mu(ref)
+    dmu = np.abs(mu_g - mu_o).max()
+    assert dmu <= FP32_MU_TOL, dmu
+    _, rg = kpm.dos(mu_g, 4096, a, b)
+    _, ro = orc.dos(mu_o, 4096, a, b)
+    l1 = np.abs(rg - ro).sum() / np.abs(ro).sum()
+    assert l1 <= 1e-4, l1

@@ -32,6 +32,11 @@ def scaled(h, k):
     return k.scale_from_bounds(*k.gershgorin(h), 0.01)
 
 
+def random_block(n, R, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal((n, R)) + 1j * g.standard_normal((n, R))
+
+
 def sweep(ctx, R, V, W, init):
     import torch
     dV, dW = ctx.new_block(R), ctx.new_block(R)
@@ -230,3 +235,54 @@ def test_staged_bounded_wait_in_a_two_problem_ensemble(kpm):
             c.close()
     for x, y in zip(got, want):
         assert np.array_equal(x, y)
+
+
+def gamma_k(k):
+    """gamma_k = k u / (1 - k u), u = 2^-24: the bound on the relative error
+    of a sum of k rounded operations in single precision (Higham, Accuracy
+    and Stability of Numerical Algorithms, Sec. 3.1)."""
+    u = 2.0 ** -24
+    return k * u / (1 - k * u)
+
+
+@pytest.mark.parametrize("R", [32, 64])
+def test_staged_float_eta_error_bound_on_a_wide_dynamic_range(kpm, orc, R):
+    """The complex float form's eta accumulation against its error bound.
+    Each lane sums the products of at most 8 rows per column in one FMA chain
+    (16 rounded FMAs), the lanes of a warp's rows are added by an xor
+    butterfly (log2(32/T) roundings: 2 at R = 32, 1 at R = 64), and
+    everything after that is exact to O(u^2) (float-float pairs, then
+    double).  So |eta_gpu - eta| <= gamma_18 * sum_i |terms_i|.  Rows of V
+    and W are scaled by 10^U(-4, 4), where a single-precision running sum
+    over the 1M rows fails that bound (checked below): <V|V> against the
+    oracle on the same single-precision V, <W|V> against its definition in
+    double on the W the kernel wrote."""
+    import torch
+    h = ham.ti_hamiltonian(64, 64, 64, gamma=1.0, seed=5)
+    a, b = scaled(h, kpm)
+    n = h["n"]
+    g = np.random.default_rng(21)
+    scale = 10.0 ** g.uniform(-4, 4, size=(n, 1))
+    V = (scale * vectors.random_phase_block(5, n, range(R))).astype(np.complex64)
+    W = (10.0 ** g.uniform(-4, 4, size=(n, 1)) * random_block(n, R, 6)).astype(np.complex64)
+    V, W = V.astype(np.complex128), W.astype(np.complex128)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        assert ctx.get_launch(R)["stages"] >= 1
+        Wg, eg = sweep(ctx, R, V, W, False)
+    bound = gamma_k(18)
+    cols = [0, 7, R // 2, R - 1]
+    for r in cols:
+        _, e_ref = orc.aug_spmv(h, a, b, V[:, r], W[:, r])
+        vv = e_ref[0]
+        assert abs(eg[0, r] - vv) <= bound * vv, (r, abs(eg[0, r] - vv) / vv)
+        # a single-precision running sum of the same terms misses the bound
+        t = (V[:, r].real ** 2 + V[:, r].imag ** 2).astype(np.float32)
+        naive = float(np.cumsum(t, dtype=np.float32)[-1])
+        assert abs(naive - vv) > bound * vv
+    w, v = Wg, V
+    re_terms = np.abs(w.real * v.real) + np.abs(w.imag * v.imag)
+    im_terms = np.abs(w.real * v.imag) + np.abs(w.imag * v.real)
+    wv = np.sum(w.real * v.real + w.imag * v.imag, axis=0)
+    wvi = np.sum(w.real * v.imag - w.imag * v.real, axis=0)
+    assert np.all(np.abs(eg[1] - wv) <= bound * re_terms.sum(axis=0))
+    assert np.all(np.abs(eg[2] - wvi) <= bound * im_terms.sum(axis=0))
