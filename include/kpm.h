@@ -295,9 +295,12 @@ void kpm_destroy(kpm_ctx *ctx);
 int kpm_moments(kpm_ctx *ctx, int32_t M, int32_t R, uint64_t seed, double *eta,
                 double *eta_imag, void *stream);
 
-/* As kpm_moments with caller-given start vectors: v0_ri is host
- * double[2 * n * R], row-major complex n x R (entry (i, r) at 2*(i*R + r)),
- * in the original row numbering.  Basis vectors give exact traces. */
+/* As kpm_moments with caller-given start vectors (Fig. 5 with nu_0 given,
+ * Eq. 3 unchanged): v0_ri is host double[2 * n * R], row-major complex
+ * n x R (entry (i, r) at 2*(i*R + r)), in the original row numbering.  The
+ * n basis vectors give the exact trace tr T_m(H~) in place of the
+ * stochastic estimate of Sec. "Problem Description" (the sum over r of
+ * <r|T_m|r> with random phases). */
 int kpm_moments_v0(kpm_ctx *ctx, int32_t M, int32_t R, const double *v0_ri, double *eta,
                    double *eta_imag, void *stream);
 
@@ -327,7 +330,9 @@ int kpm_moments_plane_wave(kpm_ctx *ctx, int32_t M, int32_t R, int32_t nx, int32
                            int32_t norb, const double *q, const int32_t *orb, double *eta,
                            double *eta_imag, void *stream);
 
-/* Ensemble: count independent problems (each its own context, all on the
+/* Ensemble (not in the paper, which scales one problem over many nodes; each
+ * problem is the KPM-DOS of Sec. "Problem Description" and Fig. 5, run as
+ * in kpm_moments): count independent problems (each its own context, all on the
  * same device and of the same precision), problem p with M[p] moments
  * (even, >= 2), R[p] random-phase vectors from seed[p] (R[p] a power of two
  * <= 64, else KPM_EUNSUPPORTED); eta[p] is host double[R[p]][M[p]].
@@ -445,12 +450,18 @@ int kpm_aug_spmmv(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_d
  * (8 MiB) that every GPU loading this library holds until the process
  * exits; the call makes no cudaMalloc, cudaFree or other allocating call.
  *   - The first call on a device looks up the scratch's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture on that device.
+ *     (cudaGetSymbolAddress) and caches it for the life of the process;
+ *     make that first call before any stream capture on that device.  A
+ *     device reset (cudaDeviceReset) reloads the library's module and is
+ *     not supported between calls.
  *   - R needing more partials than the scratch holds is rejected with
  *     KPM_EINVAL before anything is launched.  The need is the sum over
- *     column blocks of grid * 3 * width doubles; with the default launch
- *     shapes of both forms every R <= 256 fits.
+ *     column blocks of grid * 3 * width doubles, grid depending on the
+ *     launch shape and the device's SM count; with the default staged
+ *     shapes of both forms on a 152-SM GB300 every R <= 256 fits (tested).
+ *     The register-path shapes (contexts without gather lists) and shapes
+ *     from kpm_autotune or kpm_set_launch can need more and then get
+ *     KPM_EINVAL.
  *   - Nothing in the scratch has to start at zero: every call writes each
  *     partial it later reads.  Calls share the one array and it keeps the
  *     last call's contents, so calls that overlap on the GPU (other streams,

@@ -34,13 +34,9 @@ int launch_sweep_fp64(const SweepParams &p, const LaunchShape &s, int grid, bool
 #define KPM_CASE(T_, E_)                                                                       \
     if (s.T == T_ && s.E == E_) {                                                              \
         if (KPM_SWEEP_MAX_L1) {                                                                \
-            static bool carved = false;                                                        \
-            if (!carved) {                                                                     \
-                cudaFuncSetAttribute(aug_spmmv_kernel<double, T_, E_, false>,                       \
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,           \
-                                     cudaSharedmemCarveoutMaxL1);                              \
-                carved = true;                                                                 \
-            }                                                                                  \
+            if (ensure_carveout_max_l1((const void *)aug_spmmv_kernel<double, T_, E_, false>) != \
+                KPM_OK)                                                                        \
+                return KPM_ECUDA;                                                              \
         }                                                                                      \
         if (p.with_imag)                                                                       \
             aug_spmmv_kernel<double, T_, E_, true><<<grid, s.threads, smem, st>>>(p, init ? 1 : 0);  \

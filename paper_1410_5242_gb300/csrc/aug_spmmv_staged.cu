@@ -1146,19 +1146,13 @@ int occupancy_of(int threads, size_t smem)
     return nb;
 }
 
-// Launches one instantiation, raising its dynamic shared-memory limit the
-// first time a launch needs more.
+// Launches one instantiation, raising its dynamic shared-memory limit on
+// the current device the first time a launch there needs more.
 template <typename Real, int T, int E, bool IMAG, bool HALF>
 int launch_one_staged(const StagedParams &p, int grid, int threads, size_t smem, cudaStream_t st)
 {
-    static size_t set = 0;
-    if (set < smem) {
-        if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return KPM_ECUDA;
-        set = smem;
-    }
+    KPM_TRY(ensure_max_dynamic_smem((const void *)aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
+                                    smem));
     aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF><<<grid, threads, smem, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;
 }

@@ -8,7 +8,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "aug_spmmv.cuh"
@@ -164,6 +166,46 @@ __global__ void reduce_single_kernel(const double *partial, int G, int RB, int c
 }  // namespace
 
 namespace kpm {
+
+static std::mutex g_attr_lock;
+// (kernel, device, attribute) -> the value set last
+static std::map<std::tuple<const void *, int, int>, size_t> g_attr_set;
+
+int ensure_max_dynamic_smem(const void *func, size_t smem)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return KPM_ECUDA;
+    std::lock_guard<std::mutex> lock(g_attr_lock);
+    size_t &have = g_attr_set[std::make_tuple(func, dev, 0)];
+    if (have >= smem)
+        return KPM_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return KPM_ECUDA;
+    }
+    have = smem;
+    return KPM_OK;
+}
+
+int ensure_carveout_max_l1(const void *func)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return KPM_ECUDA;
+    std::lock_guard<std::mutex> lock(g_attr_lock);
+    size_t &have = g_attr_set[std::make_tuple(func, dev, 1)];
+    if (have)
+        return KPM_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxL1) != cudaSuccess) {
+        cudaGetLastError();
+        return KPM_ECUDA;
+    }
+    have = 1;
+    return KPM_OK;
+}
 
 void *dev_alloc(kpm_ctx *c, size_t bytes)
 {

@@ -153,6 +153,14 @@ struct DeviceGuard {
     }
 };
 
+// Kernel attributes are per function and per device (context).  These set
+// one on the current device, once per kernel, device and value, and are
+// safe to call from several host threads.
+// The dynamic shared-memory limit of func raised to at least smem bytes.
+int ensure_max_dynamic_smem(const void *func, size_t smem);
+// The shared-memory carve-out preference of func set to the maximum L1.
+int ensure_carveout_max_l1(const void *func);
+
 inline int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess)

@@ -362,8 +362,10 @@ class _TorchAllocator:
     def __init__(self, device):
         torch = _torch()
         self.device = device
+        self.calls = 0  # allocations the library asked for
 
         def alloc(nbytes, user):
+            self.calls += 1
             try:
                 return torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device)
             except Exception:  # noqa: BLE001 - reported to the library as NULL

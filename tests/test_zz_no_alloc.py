@@ -39,7 +39,7 @@ def _blocks(ctx, R, V0, W0):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("R", [3, 32, 100])
+@pytest.mark.parametrize("R", [3, 32, 100, 256])
 def test_static_sweep_matches_allocating_sweep_twice(kpm, prec, R):
     import torch
     h = ham.ti_hamiltonian(6, 5, 4, gamma=0.8, seed=2)
@@ -64,6 +64,43 @@ def test_static_sweep_matches_allocating_sweep_twice(kpm, prec, R):
             np.testing.assert_allclose(es, ea, rtol=0, atol=tol_e * np.abs(ea[:R]).max())
             Va, Wa = Wa, Va   # next step of the recurrence: the new W becomes V
             Vs, Ws = Ws, Vs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_static_sweep_allocates_nothing_on_a_fresh_context(kpm, prec):
+    """On a context that has never run a sweep, two calls of the static
+    sweep ask the context's allocator hook for nothing and leave PyTorch's
+    allocation count unchanged, and give the allocating sweep's results
+    (computed afterwards on a second context)."""
+    import torch
+    h = ham.ti_hamiltonian(6, 5, 4, gamma=0.8, seed=2)
+    a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+    n, R = h["n"], 32
+    V0 = vectors.random_phase_block(5, n, range(R))
+    g = np.random.default_rng(7)
+    W0 = g.standard_normal((n, R)) + 1j * g.standard_normal((n, R))
+    with kpm.create(h, a, b, precision=prec) as ctx:
+        V, W = _blocks(ctx, R, V0, W0)
+        eta = torch.zeros(3 * R, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        hook0 = ctx._alloc.calls
+        torch0 = torch.cuda.memory_stats()["allocation.all.allocated"]
+        ctx.aug_spmmv_static(R, V, W, eta)
+        ctx.aug_spmmv_static(R, W, V, eta)
+        torch.cuda.synchronize()
+        assert ctx._alloc.calls == hook0
+        assert torch.cuda.memory_stats()["allocation.all.allocated"] == torch0
+        ws, es = ctx.block_download(R, V), eta.cpu().numpy()
+    with kpm.create(h, a, b, precision=prec) as ctx:
+        V, W = _blocks(ctx, R, V0, W0)
+        eta = torch.zeros(3 * R, dtype=torch.float64, device="cuda")
+        ctx.aug_spmmv(R, V, W, eta)
+        ctx.aug_spmmv(R, W, V, eta)
+        torch.cuda.synchronize()
+        wa, ea = ctx.block_download(R, V), eta.cpu().numpy()
+    tol_w, tol_e = (1e-13, 1e-12) if prec == 0 else (2e-6, 2e-6)
+    np.testing.assert_allclose(ws, wa, rtol=0, atol=tol_w * np.abs(wa).max())
+    np.testing.assert_allclose(es, ea, rtol=0, atol=tol_e * np.abs(ea[:R]).max())
 
 
 def test_static_sweep_rejects_too_many_columns(kpm):
