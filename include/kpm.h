@@ -81,6 +81,15 @@ typedef struct kpm_options {
                                  original row) applied before the sigma sort, e.g. to place
                                  rows that share neighbours together for cache reuse; moments
                                  do not depend on it beyond rounding.  Read during kpm_create. */
+    /* One part of a row-partitioned problem (kpm_partition_build): */
+    int64_t n_halo;           /* 0, or the part's halo rows: the CSR's columns run to
+                                 n + n_halo, column n + h reading halo slot h of the vector
+                                 blocks (kpm_halo_unpack); such a context serves the
+                                 device-resident sweep calls only */
+    int64_t global_n;         /* 0 = n; else the rows of the whole problem: start vectors
+                                 draw their phases by global row (stream 1 at index
+                                 r * global_n + global row) */
+    int64_t row0;             /* global row of local row 0 (with global_n) */
 } kpm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -266,6 +275,54 @@ typedef struct kpm_staged {
 int kpm_staged_build(const kpm_sell *s, const kpm_gather *g, int32_t form, kpm_staged *out);
 void kpm_staged_release(kpm_staged *st);
 
+/* Row partition for several processes (Sec. "Symmetric Heterogeneous
+ * Execution": each process holds a contiguous, weighted share of the rows,
+ * receives before every sweep the rows of the vector block its rows read
+ * from other processes -- the halo -- and the scalar products are summed
+ * over processes once, at the end, as in the single global reduction of
+ * Table III).  Host only.
+ *
+ * kpm_partition_rows: boundaries row_start[0..parts] (row_start[0] = 0,
+ * row_start[parts] = n) of parts contiguous shares of n rows, part k about
+ * weights[k]/sum(weights) of them (weights NULL = equal), every boundary a
+ * multiple of align rows (a lattice plane: z-slabs for the numbering of Eq.
+ * 1) and every part at least align rows.  KPM_EINVAL unless n is a multiple
+ * of align, there are at least parts planes and the weights are positive.
+ *
+ * kpm_partition_build: part `part` of the CSR matrix under row_start: its
+ * rows [row0, row0 + n_local) as a local CSR whose columns are the local
+ * row (columns in the part) or n_local + h for halo slot h (the other
+ * parts' rows the part's rows read, halo_rows[h] increasing); within a row
+ * local columns come first, each group increasing.  The peers are the
+ * parts it receives from or sends to (increasing): halo slots
+ * [recv_ptr[q], recv_ptr[q+1]) come from peer[q], and peer[q] needs this
+ * part's local rows send_rows[send_ptr[q] .. send_ptr[q+1]), in the order
+ * of its own halo slots.  The whole CSR is read (every part sees the whole
+ * matrix here).  Free with kpm_partition_release. */
+typedef struct kpm_part {
+    int64_t n;            /* rows of the whole matrix */
+    int64_t row0;         /* global row of local row 0 */
+    int64_t n_local;      /* rows of this part */
+    int64_t n_halo;       /* halo slots */
+    int64_t nnz;          /* entries of the local CSR */
+    int32_t n_peers;
+    int32_t reserved;
+    int64_t *row_ptr;     /* [n_local + 1] */
+    int32_t *col;         /* [nnz] */
+    double *val_ri;       /* [2 * nnz] */
+    int64_t *halo_rows;   /* [n_halo] global rows */
+    int32_t *peer;        /* [n_peers] */
+    int64_t *recv_ptr;    /* [n_peers + 1] */
+    int64_t *send_ptr;    /* [n_peers + 1] */
+    int32_t *send_rows;   /* [send_ptr[n_peers]] local rows */
+} kpm_part;
+int kpm_partition_rows(int64_t n, int32_t parts, const double *weights, int64_t align,
+                       int64_t *row_start);
+int kpm_partition_build(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                        const double *val_ri, int32_t parts, const int64_t *row_start,
+                        int32_t part, kpm_part *out);
+void kpm_partition_release(kpm_part *p);
+
 /* ============================================================ GPU calls */
 
 /* Creates a context on opt->device: validates the CSR (and, if asked,
@@ -400,9 +457,10 @@ typedef struct kpm_info {
 
 int kpm_get_info(const kpm_ctx *ctx, kpm_info *out);
 
-/* Reads and clears the context's device error word: KPM_OK, or
- * KPM_ETIMEOUT if a bounded device-side wait of the staged kernel gave up
- * since the last check (its results are then invalid).  The moment calls
+/* Reads and clears the context's device error word: KPM_OK; KPM_ETIMEOUT
+ * if a bounded device-side wait of the staged kernel gave up since the last
+ * check (its results are then invalid); KPM_EINVAL if a kernel met an index
+ * outside its array and skipped it (kpm_halo_pack's rows).  The moment calls
  * check it themselves before returning; the device-resident calls leave it
  * to the caller.  Synchronous. */
 int kpm_check_device_error(kpm_ctx *ctx);
@@ -419,9 +477,10 @@ int kpm_check_device_error(kpm_ctx *ctx);
 int kpm_test_stall_staged(kpm_ctx *ctx, int64_t chunks_per_block);
 
 /* Bytes of one device vector block of width R in the context's layout:
- * n_pad rows of ld(R) complex numbers (complex double for FP64, complex
- * float for FP32), ld(R) = R, rounded up to even for FP32 when R > 1,
- * rows in the permuted order of the sparse layout. */
+ * n_pad (+ n_halo for a part) rows of ld(R) complex numbers (complex double
+ * for FP64, complex float for FP32), ld(R) = R, rounded up to even for
+ * FP32 when R > 1, rows in the permuted order of the sparse layout, halo
+ * slots after them. */
 int64_t kpm_block_bytes(const kpm_ctx *ctx, int32_t R);
 
 /* Host (original row order, double complex n x R row-major) <-> device block
@@ -469,6 +528,24 @@ int kpm_aug_spmmv(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_d
  *     them on one stream. */
 int kpm_aug_spmmv_static(kpm_ctx *ctx, int32_t R, const void *V, void *W, double *eta_dev,
                          int32_t init, int32_t with_imag, void *stream);
+
+/* Halo exchange of a part's context (kpm_options.n_halo > 0): the vector
+ * blocks hold the part's rows and then n_halo halo slots.
+ * kpm_halo_pack copies local rows rows_dev[0..count) (device int32, local
+ * row numbers) of block V to buf (device, count rows of the block's row
+ * length: kpm_block_bytes / rows); kpm_halo_unpack copies count rows of buf
+ * into halo slots first .. first + count - 1 of V.  Asynchronous on stream.
+ * KPM_EINVAL for a range outside the block; a row of rows_dev outside
+ * [0, n) is skipped and reported by kpm_check_device_error (KPM_EINVAL). */
+int kpm_halo_pack(kpm_ctx *ctx, int32_t R, const void *V, const int32_t *rows_dev, int32_t count,
+                  void *buf, void *stream);
+int kpm_halo_unpack(kpm_ctx *ctx, int32_t R, void *V, const void *buf, int64_t first,
+                    int32_t count, void *stream);
+/* Start block of random phases for a part (or any context): entry (p, r)
+ * of V for the context's rows exp(2 pi i u), u from stream 1 at index
+ * r * global_n + global row (kpm_moments' start vectors of the whole
+ * problem); halo slots and padding rows zero.  Asynchronous on stream. */
+int kpm_block_phases(kpm_ctx *ctx, int32_t R, uint64_t seed, void *V, void *stream);
 
 /* kpm_moments with everything on the device: random-phase start vectors
  * from seed are generated on the GPU and eta_dev / eta_imag_dev (device

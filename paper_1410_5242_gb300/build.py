@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libkpm.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["kpm_host.cpp", "kpm_ctx.cu", "kpm_batch.cu", "kpm_naive.cu", "aug_spmmv_fp64.cu",
+SOURCES = ["kpm_host.cpp", "kpm_part.cpp", "kpm_ctx.cu", "kpm_batch.cu", "kpm_naive.cu", "aug_spmmv_fp64.cu",
            "aug_spmmv_fp32.cu", "aug_spmmv_staged.cu"]
 HEADERS = ["kpm_internal.h", "aug_spmmv.cuh", os.path.join(INCLUDE, "kpm.h")]
 

@@ -271,6 +271,8 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     for (int32_t p = 0; p < count; p++) {
         if (!ctx[p] || M[p] < 2 || (M[p] & 1) || R[p] < 1)
             return KPM_EINVAL;
+        if (ctx[p]->n_halo > 0)
+            return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
         if (R[p] > 64 || (R[p] & (R[p] - 1)))
             return KPM_EUNSUPPORTED;
         if (ctx[p]->device != ctx[0]->device || ctx[p]->precision != ctx[0]->precision)

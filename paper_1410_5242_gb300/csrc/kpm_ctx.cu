@@ -32,20 +32,23 @@ __host__ __device__ inline uint64_t splitmix_mix(uint64_t z)
 
 // ------------------------------------------------------------- kernels
 // Random-phase start block: V[p][r] = exp(2 pi i u), u from stream 1 at
-// index r*n + perm[p]; rows p >= n and columns r >= R are zero.
+// index r*gn + row0 + perm[p] (gn = the whole problem's rows, row0 = the
+// global row of local row 0; n and 0 for an unpartitioned problem); rows
+// p >= n (padding, halo slots) and columns r >= R are zero.  rows = the
+// block's rows.
 template <typename Real>
-__global__ void phases_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n_pad, int R,
-                              int ld, uint64_t key)
+__global__ void phases_kernel(Real *V, const int32_t *perm, int64_t n, int64_t rows, int R,
+                              int ld, uint64_t key, int64_t gn, int64_t row0)
 {
-    const int64_t total = n_pad * ld;
+    const int64_t total = rows * ld;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = idx / ld;
         const int r = (int)(idx - p * ld);
         Real re = 0, im = 0;
         if (p < n && r < R) {
-            const uint64_t i = perm ? (uint64_t)perm[p] : (uint64_t)p;
-            const uint64_t x = splitmix_mix(key + ((uint64_t)r * (uint64_t)n + i + 1) * kGolden);
+            const uint64_t i = (uint64_t)row0 + (perm ? (uint64_t)perm[p] : (uint64_t)p);
+            const uint64_t x = splitmix_mix(key + ((uint64_t)r * (uint64_t)gn + i + 1) * kGolden);
             const double u = (double)(x >> 11) * 0x1.0p-53;
             if constexpr (sizeof(Real) == 8) {
                 double s, c;
@@ -80,6 +83,28 @@ __global__ void basis_kernel(Real *V, const int32_t *perm, int64_t n, int64_t n_
         const bool one = p < n && r < R && (int64_t)perm[p] == rows[r];
         V[2 * idx] = one ? Real(1) : Real(0);
         V[2 * idx + 1] = Real(0);
+    }
+}
+
+// Halo exchange of a part: out row k = V row iperm[rows[k]]; rows of ld
+// complex numbers.  A row outside [0, n) is skipped (its output stays as
+// it was) and recorded in the error word.
+template <typename Real>
+__global__ void halo_pack_kernel(const Real *V, const int32_t *iperm, const int32_t *rows,
+                                 int64_t count, int ld, int64_t n, Real *out, int *err)
+{
+    const int64_t total = count * ld;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx / ld, r = idx - k * ld;
+        const int32_t row = rows[k];
+        if (row < 0 || row >= n) {
+            atomicExch(err, KPM_DEVERR_RANGE);
+            continue;
+        }
+        const int64_t src = ((int64_t)iperm[row] * ld + r) * 2;
+        out[2 * idx] = V[src];
+        out[2 * idx + 1] = V[src + 1];
     }
 }
 
@@ -370,7 +395,7 @@ int plan_blocks(kpm_ctx *c, int R, std::vector<ColumnBlock> &blocks, int64_t &sl
 
 int ensure_vectors(kpm_ctx *c, int R)
 {
-    const int64_t bytes = c->n_pad * block_ld(c, R) * (int64_t)c->sdc;
+    const int64_t bytes = (c->n_pad + c->n_halo) * block_ld(c, R) * (int64_t)c->sdc;
     if (bytes <= c->vw_bytes)
         return KPM_OK;
     dev_free(c, c->d_V);
@@ -496,9 +521,9 @@ int kpm::launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, i
     const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
     const int grid = n_sm * 8;
     if (fp64)
-        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, perm, n, n_pad, R, ld, key);
+        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, perm, n, n_pad, R, ld, key, n, 0);
     else
-        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, perm, n, n_pad, R, ld, key);
+        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, perm, n, n_pad, R, ld, key, n, 0);
     return cuda_status(cudaGetLastError());
 }
 
@@ -507,13 +532,15 @@ int kpm::launch_phases(kpm_ctx *c, void *V, int R, uint64_t seed, cudaStream_t s
     const uint64_t key = splitmix_mix(seed + 2 * kGolden);  // stream 1
     const int ld = (int)block_ld(c, R);
     const int grid = c->n_sm * 8;
+    const int64_t rows = c->n_pad + c->n_halo;
+    const int64_t gn = c->global_n > 0 ? c->global_n : c->n;
     c->launches++;
     if (c->precision == KPM_PREC_FP64)
-        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, c->d_perm, c->n, c->n_pad, R, ld,
-                                                    key);
+        phases_kernel<double><<<grid, 256, 0, st>>>((double *)V, c->d_perm, c->n, rows, R, ld,
+                                                    key, gn, c->row0);
     else
-        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, c->d_perm, c->n, c->n_pad, R, ld,
-                                                   key);
+        phases_kernel<float><<<grid, 256, 0, st>>>((float *)V, c->d_perm, c->n, rows, R, ld,
+                                                   key, gn, c->row0);
     return cuda_status(cudaGetLastError());
 }
 
@@ -625,7 +652,12 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         return KPM_EINVAL;
     if ((opt.alloc_fn == nullptr) != (opt.free_fn == nullptr))
         return KPM_EINVAL;
-    int rc = validate_csr(n, row_ptr, col, val_ri);
+    // a part of a row-partitioned problem: halo columns, global row numbers
+    if (opt.n_halo < 0 || opt.global_n < 0 || opt.row0 < 0 ||
+        (opt.global_n > 0 && opt.row0 + n > opt.global_n) ||
+        (opt.n_halo > 0 && opt.check_hermitian))
+        return KPM_EINVAL;
+    int rc = validate_csr_rect(n, n + opt.n_halo, row_ptr, col, val_ri);
     if (rc)
         return rc;
     if (opt.check_hermitian) {
@@ -639,8 +671,8 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         return ndev == 0 ? KPM_ECUDA : KPM_EINVAL;
     }
     kpm_sell sell;
-    rc = kpm_sell_build(n, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma, opt.row_order,
-                        &sell);
+    rc = sell_build_rect(n, opt.n_halo, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma,
+                         opt.row_order, &sell);
     if (rc)
         return rc;
 
@@ -669,6 +701,9 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
     c->free_fn = opt.free_fn;
     c->alloc_user = opt.alloc_user;
     c->perm.assign(sell.perm, sell.perm + sell.n_pad);
+    c->n_halo = opt.n_halo;
+    c->global_n = opt.global_n;
+    c->row0 = opt.row0;
 
     DeviceGuard guard(c->device);
     auto fail = [&](int code) {
@@ -709,6 +744,18 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         cudaMemcpy(c->d_perm, sell.perm, sizeof(int32_t) * sell.n_pad, cudaMemcpyHostToDevice) !=
             cudaSuccess)
         return fail(KPM_ECUDA);
+    if (c->n_halo > 0) {
+        // local row -> position in the vector blocks, for the halo exchange
+        std::vector<int32_t> iperm(n);
+        for (int64_t p = 0; p < n; p++)
+            iperm[sell.perm[p]] = (int32_t)p;
+        c->d_iperm = (int32_t *)dev_alloc(c, sizeof(int32_t) * n);
+        if (!c->d_iperm)
+            return fail(KPM_ENOMEM);
+        if (cudaMemcpy(c->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(KPM_ECUDA);
+    }
     if (c->precision == KPM_PREC_FP64) {
         if (cudaMemcpy(c->d_val, sell.val_ri, 16 * sell.n_stored, cudaMemcpyHostToDevice) !=
             cudaSuccess)
@@ -839,6 +886,7 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_col);
     dev_free(c, c->d_val);
     dev_free(c, c->d_perm);
+    dev_free(c, c->d_iperm);
     dev_free(c, c->d_V);
     dev_free(c, c->d_W);
     dev_free(c, c->d_partial);
@@ -871,7 +919,7 @@ int kpm_check_device_error(kpm_ctx *c)
     if (word == 0)
         return KPM_OK;
     KPM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
-    return KPM_ETIMEOUT;
+    return word == KPM_DEVERR_RANGE ? KPM_EINVAL : KPM_ETIMEOUT;
 }
 
 int kpm_get_info(const kpm_ctx *c, kpm_info *out)
@@ -901,7 +949,7 @@ int64_t kpm_block_bytes(const kpm_ctx *c, int32_t R)
 {
     if (!c || R < 1)
         return -1;
-    return c->n_pad * block_ld(c, R) * (int64_t)c->sdc;
+    return (c->n_pad + c->n_halo) * block_ld(c, R) * (int64_t)c->sdc;
 }
 
 int kpm_block_upload(kpm_ctx *c, int32_t R, const double *host_ri, void *dev, void *stream)
@@ -942,6 +990,49 @@ int kpm_block_download(kpm_ctx *c, int32_t R, const void *dev, double *host_ri, 
         std::memcpy(host_ri + i * R * 2, &staging[p * ld * 2], sizeof(double) * 2 * R);
     }
     return KPM_OK;
+}
+
+int kpm_halo_pack(kpm_ctx *c, int32_t R, const void *V, const int32_t *rows_dev, int32_t count,
+                  void *buf, void *stream)
+{
+    if (!c || R < 1 || !V || !buf || count < 0 || (count > 0 && !rows_dev) || c->n_halo < 1)
+        return KPM_EINVAL;
+    if (count == 0)
+        return KPM_OK;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ld = (int)block_ld(c, R);
+    const int grid = c->n_sm * 4;
+    c->launches++;
+    if (c->precision == KPM_PREC_FP64)
+        halo_pack_kernel<double><<<grid, 256, 0, st>>>((const double *)V, c->d_iperm, rows_dev,
+                                                       count, ld, c->n, (double *)buf, c->d_err);
+    else
+        halo_pack_kernel<float><<<grid, 256, 0, st>>>((const float *)V, c->d_iperm, rows_dev,
+                                                      count, ld, c->n, (float *)buf, c->d_err);
+    return cuda_status(cudaGetLastError());
+}
+
+int kpm_halo_unpack(kpm_ctx *c, int32_t R, void *V, const void *buf, int64_t first, int32_t count,
+                    void *stream)
+{
+    if (!c || R < 1 || !V || !buf || count < 0 || first < 0 || first + count > c->n_halo)
+        return KPM_EINVAL;
+    if (count == 0)
+        return KPM_OK;
+    DeviceGuard guard(c->device);
+    const int64_t row_bytes = block_ld(c, R) * (int64_t)c->sdc;
+    char *dst = static_cast<char *>(V) + (c->n_pad + first) * row_bytes;
+    return cuda_status(cudaMemcpyAsync(dst, buf, (size_t)count * row_bytes,
+                                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+int kpm_block_phases(kpm_ctx *c, int32_t R, uint64_t seed, void *V, void *stream)
+{
+    if (!c || R < 1 || !V)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    return launch_phases(c, V, R, seed, (cudaStream_t)stream);
 }
 
 int kpm_aug_spmmv(kpm_ctx *c, int32_t R, const void *V, void *W, double *eta_dev, int32_t init,
@@ -1006,6 +1097,8 @@ int kpm_set_reduce_interval(kpm_ctx *c, int32_t sweeps)
 int kpm_moments_device(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta_dev,
                        double *eta_imag_dev, void *stream)
 {
+    if (c && c->n_halo > 0)
+        return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta_dev)
         return KPM_EINVAL;
     DeviceGuard guard(c->device);
@@ -1032,6 +1125,8 @@ static int moments_to_host(kpm_ctx *c, int32_t M, int32_t R, double *eta, double
 int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, double *eta_imag,
                 void *stream)
 {
+    if (c && c->n_halo > 0)
+        return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta)
         return KPM_EINVAL;
     DeviceGuard guard(c->device);
@@ -1048,6 +1143,8 @@ int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, do
 int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double *eta,
                    double *eta_imag, void *stream)
 {
+    if (c && c->n_halo > 0)
+        return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta || !v0_ri)
         return KPM_EINVAL;
     DeviceGuard guard(c->device);
@@ -1064,6 +1161,8 @@ int kpm_moments_v0(kpm_ctx *c, int32_t M, int32_t R, const double *v0_ri, double
 int kpm_moments_local(kpm_ctx *c, int32_t M, int32_t R, const int64_t *rows, double *eta,
                       double *eta_imag, void *stream)
 {
+    if (c && c->n_halo > 0)
+        return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta || !rows)
         return KPM_EINVAL;
     for (int32_t r = 0; r < R; r++)
@@ -1094,6 +1193,8 @@ int kpm_moments_plane_wave(kpm_ctx *c, int32_t M, int32_t R, int32_t nx, int32_t
                            int32_t norb, const double *q, const int32_t *orb, double *eta,
                            double *eta_imag, void *stream)
 {
+    if (c && c->n_halo > 0)
+        return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta || !q || !orb || nx < 1 || ny < 1 || nz < 1 ||
         norb < 1 || (int64_t)nx * ny * nz * norb != c->n)
         return KPM_EINVAL;

@@ -70,7 +70,13 @@ int parallel_parts(int64_t n, int64_t grain, F &&f)
 
 int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri)
 {
-    if (n < 1 || n > INT32_MAX || !row_ptr)
+    return validate_csr_rect(n, n, row_ptr, col, val_ri);
+}
+
+int validate_csr_rect(int64_t n, int64_t n_cols, const int64_t *row_ptr, const int32_t *col,
+                      const double *val_ri)
+{
+    if (n < 1 || n > INT32_MAX || n_cols < n || n_cols > INT32_MAX || !row_ptr)
         return KPM_EINVAL;
     if (row_ptr[0] != 0)
         return KPM_EINVAL;
@@ -91,7 +97,7 @@ int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const do
         for (int64_t i = b; i < e; i++) {
             int64_t prev = -1;
             for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-                if (col[k] < 0 || col[k] >= n || col[k] <= prev) {
+                if (col[k] < 0 || col[k] >= n_cols || col[k] <= prev) {
                     bad = true;
                     return;
                 }
@@ -416,13 +422,22 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
                    double a, double b, int32_t C, int32_t sigma, const int32_t *row_order,
                    kpm_sell *out)
 {
+    return kpm::sell_build_rect(n, 0, row_ptr, col, val_ri, a, b, C, sigma, row_order, out);
+}
+
+}  // extern "C"
+
+int kpm::sell_build_rect(int64_t n, int64_t n_halo, const int64_t *row_ptr, const int32_t *col,
+                         const double *val_ri, double a, double b, int32_t C, int32_t sigma,
+                         const int32_t *row_order, kpm_sell *out)
+{
     if (!out)
         return KPM_EINVAL;
     std::memset(out, 0, sizeof(*out));
     if (C < 1 || C > 1024 || (C & (C - 1)) || sigma < 1 || !(a > 0.0) || !std::isfinite(a) ||
-        !std::isfinite(b))
+        !std::isfinite(b) || n_halo < 0)
         return KPM_EINVAL;
-    int rc = validate_csr(n, row_ptr, col, val_ri);
+    int rc = validate_csr_rect(n, n + n_halo, row_ptr, col, val_ri);
     if (rc)
         return rc;
 
@@ -534,7 +549,9 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
                             re = two_a * (re - b), im = two_a * im;
                         else
                             re = two_a * re, im = two_a * im;
-                        put(iperm[col[k]], re, im);
+                        // a halo column (>= n) reads the vector row after the
+                        // padded local rows
+                        put(col[k] < n ? iperm[col[k]] : (int32_t)(n_pad + (col[k] - n)), re, im);
                     }
                     if (!diag_done)
                         put((int32_t)p, -two_a * b, 0.0);
@@ -561,6 +578,8 @@ int kpm_sell_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
     out->perm = perm_out;
     return KPM_OK;
 }
+
+extern "C" {
 
 void kpm_sell_release(kpm_sell *s)
 {

@@ -14,6 +14,14 @@ namespace kpm {
 
 // Validates a CSR matrix (see kpm_gershgorin in kpm.h for the rules).
 int validate_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri);
+// The same for n rows with columns in [0, n_cols) (a part's local matrix).
+int validate_csr_rect(int64_t n, int64_t n_cols, const int64_t *row_ptr, const int32_t *col,
+                      const double *val_ri);
+// kpm_sell_build for a part's local matrix: columns n .. n + n_halo - 1 are
+// halo slots, stored as vector rows n_pad + (column - n).
+int sell_build_rect(int64_t n, int64_t n_halo, const int64_t *row_ptr, const int32_t *col,
+                    const double *val_ri, double a, double b, int32_t C, int32_t sigma,
+                    const int32_t *row_order, kpm_sell *out);
 // KPM_OK if H == H^dagger within rel_tol * max|h_ij|, else KPM_ENOTHERMITIAN.
 int check_hermitian(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
                     double rel_tol);
@@ -37,7 +45,8 @@ struct SweepParams {
 };
 
 // Device-side error codes a kernel records in the context's error word.
-#define KPM_DEVERR_TIMEOUT 1
+#define KPM_DEVERR_TIMEOUT 1  // a bounded wait gave up (KPM_ETIMEOUT)
+#define KPM_DEVERR_RANGE 2    // an index outside its array was skipped (KPM_EINVAL)
 
 // Per-chunk producer record of the staged kernel: 32 int2 (256 bytes),
 // [0] = first entry of the chunk in the staged entry arrays (int64 as lo,
@@ -201,6 +210,11 @@ struct kpm_ctx {
     kpm_alloc_fn alloc_fn = nullptr;
     kpm_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
+
+    // a part of a row-partitioned problem: halo slots after the n_pad rows
+    // of each vector block; start vectors by global row
+    int64_t n_halo = 0, global_n = 0, row0 = 0;
+    int32_t *d_iperm = nullptr;  // [n] local row -> position (parts only)
 
     int64_t *d_chunk_ptr = nullptr;
     int32_t *d_chunk_len = nullptr;

@@ -35,7 +35,20 @@ class Options(ctypes.Structure):
                 ("sigma", ctypes.c_int32), ("check_hermitian", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("alloc_fn", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("row_order", ctypes.POINTER(ctypes.c_int32))]
+                ("row_order", ctypes.POINTER(ctypes.c_int32)), ("n_halo", ctypes.c_int64),
+                ("global_n", ctypes.c_int64), ("row0", ctypes.c_int64)]
+
+
+class Part(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("row0", ctypes.c_int64), ("n_local", ctypes.c_int64),
+                ("n_halo", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_peers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("row_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("col", ctypes.POINTER(ctypes.c_int32)), ("val_ri", ctypes.POINTER(ctypes.c_double)),
+                ("halo_rows", ctypes.POINTER(ctypes.c_int64)),
+                ("peer", ctypes.POINTER(ctypes.c_int32)),
+                ("recv_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("send_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("send_rows", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Sell(ctypes.Structure):
@@ -107,6 +120,13 @@ _SIGS = {
                                 ctypes.POINTER(Staged)]),
     "kpm_staged_release": (None, [ctypes.POINTER(Staged)]),
     "kpm_check_device_error": (_int, [_vp]),
+    "kpm_partition_rows": (_int, [_i64, _i32, _pd, _i64, _pi64]),
+    "kpm_partition_build": (_int, [_i64, _pi64, _pi32, _pd, _i32, _pi64, _i32,
+                                   ctypes.POINTER(Part)]),
+    "kpm_partition_release": (None, [ctypes.POINTER(Part)]),
+    "kpm_halo_pack": (_int, [_vp, _i32, _vp, _vp, _i32, _vp, _vp]),
+    "kpm_halo_unpack": (_int, [_vp, _i32, _vp, _vp, _i64, _i32, _vp]),
+    "kpm_block_phases": (_int, [_vp, _i32, _u64, _vp, _vp]),
     "kpm_test_stall_staged": (_int, [_vp, _i64]),
     "kpm_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, ctypes.POINTER(Options),
                           ctypes.POINTER(_vp)]),
@@ -169,7 +189,9 @@ def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def _csr(csr):
+def _csr(csr, n_cols=None):
+    # n_cols: a part's local matrix has halo columns past its n rows (checked
+    # by the library)
     rp = np.ascontiguousarray(csr["row_ptr"], dtype=np.int64)
     col = np.ascontiguousarray(csr["col"], dtype=np.int32)
     val = np.ascontiguousarray(csr["val"], dtype=np.complex128).view(np.float64)
@@ -329,6 +351,45 @@ def staged_build(csr, a, b, form, C=32, sigma=256, row_order=None):
     return sell, gat, stg
 
 
+def partition_rows(n, parts, align=1, weights=None):
+    """kpm_partition_rows: int64[parts + 1] row boundaries."""
+    out = np.empty(parts + 1, dtype=np.int64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    _check(lib.kpm_partition_rows(int(n), int(parts), _p(w, _d) if w is not None else None,
+                                  int(align), _p(out, _i64)), "kpm_partition_rows")
+    return out
+
+
+def partition_build(csr, row_start, part):
+    """kpm_partition_build: one part's local CSR (columns: local rows, then
+    n_local + halo slot), its halo rows and its exchange lists, as numpy."""
+    n, rp, col, val = _csr(csr)
+    rs = np.ascontiguousarray(row_start, dtype=np.int64)
+    P = Part()
+    _check(lib.kpm_partition_build(n, _p(rp, _i64), _p(col, _i32), _p(val, _d), rs.size - 1,
+                                   _p(rs, _i64), int(part), ctypes.byref(P)), "kpm_partition_build")
+    try:
+        nl, nh, nnz, npr = P.n_local, P.n_halo, P.nnz, P.n_peers
+
+        def arr(ptr, count, dtype):
+            return np.ctypeslib.as_array(ptr, (max(count, 1),))[:count].astype(dtype, copy=True)
+        send_ptr = arr(P.send_ptr, npr + 1, np.int64)
+        out = {
+            "n": P.n, "row0": P.row0, "n_local": nl, "n_halo": nh, "part": int(part),
+            "csr": {"n": nl, "row_ptr": arr(P.row_ptr, nl + 1, np.int64),
+                    "col": arr(P.col, nnz, np.int32),
+                    "val": arr(P.val_ri, 2 * nnz, np.float64).view(np.complex128)},
+            "halo_rows": arr(P.halo_rows, nh, np.int64),
+            "peer": arr(P.peer, npr, np.int32),
+            "recv_ptr": arr(P.recv_ptr, npr + 1, np.int64),
+            "send_ptr": send_ptr,
+            "send_rows": arr(P.send_rows, int(send_ptr[-1]), np.int32),
+        }
+    finally:
+        lib.kpm_partition_release(ctypes.byref(P))
+    return out
+
+
 def _sell_dict(s):
     return {
             "n": s.n, "n_pad": s.n_pad, "C": s.C, "sigma": s.sigma, "n_chunks": s.n_chunks,
@@ -384,9 +445,12 @@ class Context:
 
     def __init__(self, csr, a, b, precision=PREC_FP64, chunk_height=32, sigma=256,
                  check_hermitian=False, device=0, torch_allocator=True, autotune=False,
-                 row_order=None):
-        n, rp, col, val = _csr(csr)
+                 row_order=None, n_halo=0, global_n=0, row0=0):
+        n, rp, col, val = _csr(csr, n_cols=csr["n"] + n_halo)
         opt = default_options()
+        opt.n_halo = n_halo
+        opt.global_n = global_n
+        opt.row0 = row0
         opt.precision = precision
         opt.chunk_height = chunk_height
         opt.sigma = sigma
@@ -508,6 +572,24 @@ class Context:
         return (eta, eti) if imag else eta
 
     # -- device-buffer calls (torch tensors)
+    def halo_pack(self, R, V, rows_dev, buf, stream=None):
+        """kpm_halo_pack: local rows rows_dev (device int32 tensor) of block V into buf."""
+        _check(lib.kpm_halo_pack(self.handle, R, ctypes.c_void_p(V.data_ptr()),
+                                 ctypes.c_void_p(rows_dev.data_ptr()), int(rows_dev.numel()),
+                                 ctypes.c_void_p(buf.data_ptr()), _stream_ptr(stream)),
+               "kpm_halo_pack")
+
+    def halo_unpack(self, R, V, buf, first, count, stream=None):
+        """kpm_halo_unpack: count rows of buf into halo slots first.. of block V."""
+        _check(lib.kpm_halo_unpack(self.handle, R, ctypes.c_void_p(V.data_ptr()),
+                                   ctypes.c_void_p(buf.data_ptr()), int(first), int(count),
+                                   _stream_ptr(stream)), "kpm_halo_unpack")
+
+    def block_phases(self, R, seed, V, stream=None):
+        """kpm_block_phases: random-phase start block (by global row) into V."""
+        _check(lib.kpm_block_phases(self.handle, R, seed, ctypes.c_void_p(V.data_ptr()),
+                                    _stream_ptr(stream)), "kpm_block_phases")
+
     def new_block(self, R):
         torch = _torch()
         nbytes = self.block_bytes(R)
