@@ -545,18 +545,35 @@ def ablation_stages(kpm, h, a, b, ctx, ctx32, n, nnz, n4, nnz4, stream):
 def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
     """The ensemble recipe (64 lattices 16..96 x 16..96 x 16..48, gamma in
     [0, 4], even M in [512, 4096], R in {8, 16, 32, 64}, complex float) as
-    one kpm_batch: graph launches timed with CUDA events (setup excluded)."""
+    one kpm_batch: graph launches timed with CUDA events (setup excluded).
+    Each block-width class takes the SELL chunk height and sorting window
+    that kpm_autotune_layout picks on its largest problem."""
     probs = workloads.ensemble()
     t0 = time.perf_counter()
-    ctxs, Ms, Rs, seeds = [], [], [], []
+    hs = []
     for p in probs:
         h = hamiltonians.ti_hamiltonian(*p["dims"], gamma=p["gamma"], seed=p["seed"])
         a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
-        ctxs.append(kpm.create(h, a, b, precision=kpm.PREC_FP32, device=dev))
+        hs.append((h, a, b))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    layout = {}
+    for R in sorted(set(p["R"] for p in probs)):
+        big = max((i for i, p in enumerate(probs) if p["R"] == R), key=lambda i: hs[i][0]["n"])
+        h, a, b = hs[big]
+        layout[R] = kpm.autotune_layout(h, a, b, R, precision=kpm.PREC_FP32, sweeps=3,
+                                        device=dev)
+    t_layout = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctxs, Ms, Rs, seeds = [], [], [], []
+    for p, (h, a, b) in zip(probs, hs):
+        L = layout[p["R"]]
+        ctxs.append(kpm.create(h, a, b, precision=kpm.PREC_FP32, device=dev,
+                               chunk_height=L["chunk_height"], sigma=L["sigma"]))
         Ms.append(p["M"])
         Rs.append(p["R"])
         seeds.append(p["seed"])
-    t_setup = time.perf_counter() - t0
+    t_setup = time.perf_counter() - t0 + t_build
     # autotune the launch shape of each block-width class on its largest
     # problem (kpm_autotune) and give it to the class's other problems: the
     # batch launches each class with its first problem's shape
@@ -590,6 +607,9 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
            "algorithmic_bytes_per_run": info["algorithmic_bytes"], "sweeps": info["sweeps"],
            "steps": info["steps"], "graph_kernel_nodes": info["kernel_launches"],
            "setup_s": round(t_setup, 1), "autotune_s": round(t_tune, 1), "tuned_launch": tuned,
+           "layout_autotune_s": round(t_layout, 1),
+           "tuned_layout": {str(R): {"C": L["chunk_height"], "sigma": L["sigma"]}
+                            for R, L in layout.items()},
            "capture_s": round(t_capture, 2),
            "mu0_problem0": float(kpm.eta_to_mu(eta0)[0])}
     batch.close()
@@ -756,14 +776,22 @@ def large_rate(kpm, stream, hbm_peak, peak_src, launches64=5, launches32=20):
     h, a, b = ti_problem(cfg)
     t_build = time.perf_counter() - t0
     n, R, M, seed = h["n"], cfg["R"], cfg["M"], cfg["seed"]
-    out = {"workload": "TI lattice 240x240x120 (N=%d, nnz=%d), R=%d, M=%d, gamma=%g, seed %d"
-                       % (n, len(h["col"]), R, M, cfg["gamma"], seed),
+    # rows in tiles of 240 x 24 sites through all z (kpm_options.row_order):
+    # a V row's +z and -z uses are then one tile plane (0.9 MB of rows)
+    # apart instead of a whole 240 x 240 plane, so the rows stay in L2
+    # between them; the moments do not depend on the order
+    nx, ny, nz = cfg["dims"]
+    tile = (nx, cfg["tile_y"], nz)
+    row_order = hamiltonians.cube_row_order(cfg["dims"], block=tile)
+    out = {"workload": "TI lattice 240x240x120 (N=%d, nnz=%d), R=%d, M=%d, gamma=%g, seed %d; "
+                       "rows in %dx%dx%d site tiles" % (n, len(h["col"]), R, M, cfg["gamma"], seed,
+                                                        *tile),
            "lattice_build_s": round(t_build, 1)}
     etas = {}
     for name, prec, sd, launches in (("fp64", kpm.PREC_FP64, 16, launches64),
                                      ("fp32", kpm.PREC_FP32, 8, launches32)):
         t0 = time.perf_counter()
-        ctx = kpm.create(h, a, b, precision=prec)
+        ctx = kpm.create(h, a, b, precision=prec, row_order=row_order)
         t_create = time.perf_counter() - t0
         info = ctx.info()
         nnz = info["nnz"]

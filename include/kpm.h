@@ -635,7 +635,7 @@ int kpm_autotune(kpm_ctx *ctx, int32_t R, int32_t sweeps, void *stream, kpm_laun
 int kpm_get_max_block_width(const kpm_ctx *ctx);
 
 /* Layout autotuner: builds trial contexts with SELL chunk heights C in
- * {8, 32, 128} and, for matrices with rows of different lengths, sorting
+ * {8, 16, 32, 64, 128} and, for matrices with rows of different lengths, sorting
  * windows sigma in {1, 256, 4096}, tunes the launch shape of each for width
  * R (as kpm_autotune) and returns in *best the options of the fastest
  * (base's other fields kept, autotune set) and its time per sweep in

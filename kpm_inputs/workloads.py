@@ -12,7 +12,8 @@ from . import rng
 TI_SMALL = dict(name="ti_8x8x8_fp64", dims=(8, 8, 8), gamma=0.5, M=256, R=4, seed=0)
 TI_64 = dict(name="ti_64x64x64_fp64", dims=(64, 64, 64), gamma=1.0, M=2000, R=32, seed=1,
              chunk_height=32, sigma=256)
-TI_LARGE = dict(name="ti_240x240x120_fp64", dims=(240, 240, 120), gamma=2.0, M=1024, R=32, seed=2)
+TI_LARGE = dict(name="ti_240x240x120_fp64", dims=(240, 240, 120), gamma=2.0, M=1024, R=32, seed=2,
+                tile_y=24)
 TI_64_FP32 = dict(name="ti_64x64x64_fp32", dims=(64, 64, 64), gamma=1.0, M=1024, R=32, seed=2)
 R_SWEEP = (1, 4, 8, 16, 32, 64)
 

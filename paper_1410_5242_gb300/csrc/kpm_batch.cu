@@ -485,6 +485,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     }
 
     // ---- capture the schedule
+    NvtxRange range("kpm_batch_create: capture");
     if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess)
         return fail(KPM_ECUDA);
     if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -561,6 +562,7 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
 
 int kpm_batch_launch(kpm_batch *b, void *stream)
 {
+    NvtxRange range("kpm_batch_launch");
     if (!b || !b->exec)
         return KPM_EINVAL;
     DeviceGuard guard(b->device);

@@ -282,6 +282,8 @@ std::vector<int> column_widths(int R, int cap)
 // producer copies them, the consumers read them from shared memory) where
 // the larger stages keep the same number of blocks per SM; otherwise each
 // consumer lane loads its row's old W into registers a chunk ahead.
+// (Complex double keeps its lanes' cp.async of the old W: staging it, with
+// the sums started from -W, measured slower on the FP64-bound sweep.)
 int choose_wstage(const kpm_ctx *c, const LaunchShape &s)
 {
     if (c->precision != KPM_PREC_FP32 || s.stages < 1 || !c->gather_ok)
@@ -551,6 +553,7 @@ int autotune_shapes(kpm_ctx *c, int R, int sweeps, cudaStream_t st, float *ms_pe
 // The sweep schedule of Fig. 5 on device buffers already holding V = nu_0.
 int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
 {
+    NvtxRange range("sweeps and eta reductions (enqueue)");
     std::vector<ColumnBlock> blocks;
     int64_t slot_doubles = 0;
     KPM_TRY(plan_blocks(c, R, blocks, slot_doubles));
@@ -634,6 +637,7 @@ extern "C" {
 int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val_ri,
                double a, double b, const kpm_options *opt_in, kpm_ctx **out)
 {
+    NvtxRange range("kpm_create");
     if (!out)
         return KPM_EINVAL;
     *out = nullptr;
@@ -671,8 +675,11 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         return ndev == 0 ? KPM_ECUDA : KPM_EINVAL;
     }
     kpm_sell sell;
-    rc = sell_build_rect(n, opt.n_halo, row_ptr, col, val_ri, a, b, opt.chunk_height, opt.sigma,
-                         opt.row_order, &sell);
+    {
+        NvtxRange r("kpm_create: SELL-C-sigma build (host)");
+        rc = sell_build_rect(n, opt.n_halo, row_ptr, col, val_ri, a, b, opt.chunk_height,
+                             opt.sigma, opt.row_order, &sell);
+    }
     if (rc)
         return rc;
 
@@ -785,6 +792,7 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
         // gather lists and staged entry arrays for the staged kernel; a
         // matrix whose lists do not fit the 16-bit local indices keeps the
         // register-path kernel only
+        NvtxRange r("kpm_create: gather lists, staged arrays, upload");
         kpm_gather g;
         const int grc = kpm_gather_build(&sell, &g);
         if (grc == KPM_ENOMEM)
@@ -1113,6 +1121,7 @@ int kpm_moments_device(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *
 static int moments_to_host(kpm_ctx *c, int32_t M, int32_t R, double *eta, double *eta_imag,
                            cudaStream_t st)
 {
+    NvtxRange range("eta to host (waits for the sweeps)");
     const int64_t count = (int64_t)M * R;
     KPM_CUDA(cudaMemcpyAsync(eta, c->d_eta, count * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (eta_imag)
@@ -1125,6 +1134,7 @@ static int moments_to_host(kpm_ctx *c, int32_t M, int32_t R, double *eta, double
 int kpm_moments(kpm_ctx *c, int32_t M, int32_t R, uint64_t seed, double *eta, double *eta_imag,
                 void *stream)
 {
+    NvtxRange range("kpm_moments");
     if (c && c->n_halo > 0)
         return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
     if (!c || M < 2 || (M & 1) || R < 1 || !eta)
@@ -1404,7 +1414,7 @@ int kpm_autotune_layout(int64_t n, const int64_t *row_ptr, const int32_t *col,
     bool uniform = true;
     for (int64_t i = 1; i < n && uniform; i++)
         uniform = (row_ptr[i + 1] - row_ptr[i]) == (row_ptr[1] - row_ptr[0]);
-    const int Cs[] = {8, 32, 128};
+    const int Cs[] = {8, 16, 32, 64, 128};
     const int sigmas_ragged[] = {1, 256, 4096};
     double best_t = 1e300;
     int rc = KPM_EUNSUPPORTED;

@@ -8,6 +8,8 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kpm.h"
 
 namespace kpm {
@@ -169,6 +171,15 @@ struct DeviceGuard {
 int ensure_max_dynamic_smem(const void *func, size_t smem);
 // The shared-memory carve-out preference of func set to the maximum L1.
 int ensure_carveout_max_l1(const void *func);
+
+// A named NVTX range for the lifetime of the object (the phases of a call
+// in profiler timelines; no cost without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline int cuda_status(cudaError_t e)
 {

@@ -445,7 +445,11 @@ class Context:
 
     def __init__(self, csr, a, b, precision=PREC_FP64, chunk_height=32, sigma=256,
                  check_hermitian=False, device=0, torch_allocator=True, autotune=False,
-                 row_order=None, n_halo=0, global_n=0, row0=0):
+                 row_order=None, n_halo=0, global_n=0, row0=0, allocator=None):
+        """allocator: None, or an object with ctypes callbacks `alloc`
+        (ALLOC_FN) and `free` (FREE_FN) for every device buffer of the
+        context (kpm_options.alloc_fn / free_fn), used instead of torch's
+        caching allocator; it must stay alive as long as the context."""
         n, rp, col, val = _csr(csr, n_cols=csr["n"] + n_halo)
         opt = default_options()
         opt.n_halo = n_halo
@@ -461,8 +465,11 @@ class Context:
             self._row_order = np.ascontiguousarray(row_order, dtype=np.int32)
             opt.row_order = _p(self._row_order, _i32)
         self._alloc = None
-        if torch_allocator:
+        if allocator is not None:
+            self._alloc = allocator
+        elif torch_allocator:
             self._alloc = _TorchAllocator(device)
+        if self._alloc is not None:
             opt.alloc_fn = self._alloc.alloc
             opt.free_fn = self._alloc.free
         h = ctypes.c_void_p()
