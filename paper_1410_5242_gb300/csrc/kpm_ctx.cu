@@ -468,51 +468,98 @@ SweepParams sweep_params(const kpm_ctx *c, const ColumnBlock &cb, int R, const v
     return p;
 }
 
+// The staged kernel's arguments for one sweep of column block cb.
+int staged_params(const kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init,
+                  bool dots, StagedParams &q, StagedLayout &L)
+{
+    if (!shape_layout(c, cb.shape, L))
+        return KPM_EUNSUPPORTED;
+    q.one.rec = c->d_rec;
+    q.one.ovf = c->d_ovf;
+    q.one.lidx = c->d_lidx;
+    q.one.val = c->d_val_staged;
+    q.one.buf[0] = const_cast<void *>(p.V);
+    q.one.buf[1] = p.W;
+    q.one.partial = p.partial;
+    q.one.tile0 = 0;
+    q.one.n_tiles = c->n_chunks;
+    q.one.ps = 3 * cb.RB;  // [grid][3][RB]
+    q.one.qs = 1;
+    q.one.ld = p.ld;
+    q.one.col0 = p.col0;
+    q.probs = nullptr;
+    q.n_probs = 1;
+    q.parity = 0;
+    q.C = c->C;
+    q.stages = L.stages;
+    q.with_imag = p.with_imag;
+    q.init = init ? 1 : 0;
+    q.dots = dots ? 1 : 0;
+    q.fp64 = c->precision == KPM_PREC_FP64 ? 1 : 0;
+    q.half = c->half_ok ? 1 : 0;
+    q.stall_after = c->stall_after;
+    q.err = c->d_err;
+    q.bar_bytes = L.bar_bytes;
+    q.stage_bytes = L.stage_bytes;
+    q.off_val = L.off_val;
+    q.off_lidx = L.off_lidx;
+    q.off_aux = L.off_aux;
+    q.off_w = L.off_w;
+    return KPM_OK;
+}
+
 int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init,
                cudaStream_t st, bool dots = true)
 {
     c->launches++;
     if (cb.shape.stages > 0) {
         StagedLayout L;
-        if (!shape_layout(c, cb.shape, L))
-            return KPM_EUNSUPPORTED;
         StagedParams q;
-        q.one.rec = c->d_rec;
-        q.one.ovf = c->d_ovf;
-        q.one.lidx = c->d_lidx;
-        q.one.val = c->d_val_staged;
-        q.one.buf[0] = const_cast<void *>(p.V);
-        q.one.buf[1] = p.W;
-        q.one.partial = p.partial;
-        q.one.tile0 = 0;
-        q.one.n_tiles = c->n_chunks;
-        q.one.ps = 3 * cb.RB;  // [grid][3][RB]
-        q.one.qs = 1;
-        q.one.ld = p.ld;
-        q.one.col0 = p.col0;
-        q.probs = nullptr;
-        q.n_probs = 1;
-        q.parity = 0;
-        q.C = c->C;
-        q.stages = L.stages;
-        q.with_imag = p.with_imag;
-        q.init = init ? 1 : 0;
-        q.dots = dots ? 1 : 0;
-        q.fp64 = c->precision == KPM_PREC_FP64 ? 1 : 0;
-        q.half = c->half_ok ? 1 : 0;
-        q.stall_after = c->stall_after;
-        q.err = c->d_err;
-        q.bar_bytes = L.bar_bytes;
-        q.stage_bytes = L.stage_bytes;
-        q.off_val = L.off_val;
-        q.off_lidx = L.off_lidx;
-        q.off_aux = L.off_aux;
-        q.off_w = L.off_w;
-        return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
+        KPM_TRY(staged_params(c, cb, p, init, dots, q, L));
+        return launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st,
+                                   c->overlap != KPM_OVERLAP_NONE);
     }
     if (c->precision == KPM_PREC_FP64)
         return launch_sweep_fp64(p, cb.shape, cb.grid, init, st);
     return launch_sweep_fp32(p, cb.shape, cb.grid, init, st);
+}
+
+// Whether column block cb's sweeps can run as a chain (KPM_OVERLAP_CHAIN).
+bool chain_ok(const kpm_ctx *c, const ColumnBlock &cb)
+{
+    return c->overlap == KPM_OVERLAP_CHAIN && c->d_dep && cb.shape.stages > 0 &&
+           c->stall_after < 0 && c->n_halo == 0 && c->n_chunks >= 2 * (int64_t)cb.grid;
+}
+
+// Sweeps m0 .. m0 + sweeps - 1 of column block cb as one chain launch: V of
+// sweep m0 in V, its W in W, sweep m0 + j's partials at partial + j *
+// stride.  KPM_EUNSUPPORTED if the blocks cannot all be resident.
+int launch_chain(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init, int sweeps,
+                 int64_t stride, cudaStream_t st)
+{
+    StagedLayout L;
+    StagedParams q;
+    KPM_TRY(staged_params(c, cb, p, init, true, q, L));
+    const int64_t G = cb.grid;
+    const int64_t np = (c->n_chunks + G - 1) / G * G;
+    const int64_t waves = (int64_t)sweeps * (np / G);
+    if (waves > c->prog_ints) {
+        dev_free(c, c->d_prog);
+        c->d_prog = (int *)dev_alloc(c, sizeof(int) * waves);
+        c->prog_ints = c->d_prog ? waves : 0;
+        if (!c->d_prog)
+            return KPM_ENOMEM;
+    }
+    KPM_CUDA(cudaMemsetAsync(c->d_prog, 0, sizeof(int) * waves, st));
+    q.chain_sweeps = sweeps;
+    q.chain_np = np;
+    q.chain_stride = stride;
+    q.prog = c->d_prog;
+    q.dep = c->d_dep;
+    const int rc = launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
+    if (rc == KPM_OK)
+        c->launches++;
+    return rc;
 }
 
 }  // namespace
@@ -550,7 +597,11 @@ namespace {
 
 int autotune_shapes(kpm_ctx *c, int R, int sweeps, cudaStream_t st, float *ms_per_sweep = nullptr);
 
-// The sweep schedule of Fig. 5 on device buffers already holding V = nu_0.
+// The sweep schedule of Fig. 5 on device buffers already holding V = nu_0:
+// sweep m reads V = d_V (m even) or d_W (m odd) and overwrites the other.
+// Sweeps run in batches of `slots` between eta reductions; per column block
+// a batch is one chain launch where the block allows it, else one launch per
+// sweep.
 int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
 {
     NvtxRange range("sweeps and eta reductions (enqueue)");
@@ -564,28 +615,34 @@ int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStre
         slots = std::min(slots, c->reduce_interval);
     KPM_TRY(ensure_partial(c, slots * slot_doubles));
     const bool imag = eta_im != nullptr;
-    void *V = c->d_V, *W = c->d_W;
-    int pending = 0, m0 = 0;
-    for (int m = 0; m < sweeps; m++) {
-        if (m > 0)
-            std::swap(V, W);
-        double *slot = c->d_partial + (int64_t)pending * slot_doubles;
+    for (int m0 = 0; m0 < sweeps; m0 += slots) {
+        const int pending = std::min(slots, sweeps - m0);
         for (const ColumnBlock &cb : blocks) {
-            SweepParams p = sweep_params(c, cb, R, V, W, slot + cb.partial_offset, imag);
-            KPM_TRY(launch_one(c, cb, p, m == 0, st));
-        }
-        pending++;
-        if (pending == slots || m == sweeps - 1) {
-            for (const ColumnBlock &cb : blocks) {
-                const int threads = pending * 3 * cb.RB;
-                c->launches++;
-                reduce_moments_kernel<<<(threads + 255) / 256, 256, 0, st>>>(
-                    c->d_partial + cb.partial_offset, slot_doubles, pending, cb.grid, cb.RB,
-                    cb.col0, M, m0, eta, eta_im);
-                KPM_CUDA(cudaGetLastError());
+            int rc = KPM_EUNSUPPORTED;
+            if (pending >= 2 && chain_ok(c, cb)) {
+                void *V = (m0 & 1) ? c->d_W : c->d_V, *W = (m0 & 1) ? c->d_V : c->d_W;
+                SweepParams p = sweep_params(c, cb, R, V, W, c->d_partial + cb.partial_offset, imag);
+                rc = launch_chain(c, cb, p, m0 == 0, pending, slot_doubles, st);
+                if (rc != KPM_OK && rc != KPM_EUNSUPPORTED)
+                    return rc;
             }
-            m0 += pending;
-            pending = 0;
+            if (rc == KPM_OK)
+                continue;
+            for (int j = 0; j < pending; j++) {
+                const int m = m0 + j;
+                void *V = (m & 1) ? c->d_W : c->d_V, *W = (m & 1) ? c->d_V : c->d_W;
+                double *slot = c->d_partial + (int64_t)j * slot_doubles;
+                SweepParams p = sweep_params(c, cb, R, V, W, slot + cb.partial_offset, imag);
+                KPM_TRY(launch_one(c, cb, p, m == 0, st));
+            }
+        }
+        for (const ColumnBlock &cb : blocks) {
+            const int threads = pending * 3 * cb.RB;
+            c->launches++;
+            reduce_moments_kernel<<<(threads + 255) / 256, 256, 0, st>>>(
+                c->d_partial + cb.partial_offset, slot_doubles, pending, cb.grid, cb.RB, cb.col0, M,
+                m0, eta, eta_im);
+            KPM_CUDA(cudaGetLastError());
         }
     }
     return KPM_OK;
@@ -860,6 +917,40 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 (ovf.empty() || cudaMemcpy(c->d_ovf, ovf.data(), sizeof(int2) * ovf.size(),
                                            cudaMemcpyHostToDevice) == cudaSuccess);
+            // the dependency table of sweep chains (none for a part: its
+            // sweeps are separated by halo exchanges)
+            if (ok && opt.n_halo == 0 && g.n_chunks <= INT32_MAX) {
+                std::vector<int32_t> dep;
+                try {
+                    dep.resize(2 * (size_t)g.n_chunks);
+                } catch (const std::bad_alloc &) {
+                    kpm_staged_release(&sg);
+                    kpm_gather_release(&g);
+                    return fail(KPM_ENOMEM);
+                }
+                if (kpm_sweep_chain_deps(&g, sell.C, dep.data()) == KPM_OK) {
+                    // interleaved for the kernel: one 8-byte entry per chunk
+                    std::vector<int32_t> both(dep.size());
+                    for (int64_t q = 0; q < g.n_chunks; q++) {
+                        both[2 * q] = dep[q];
+                        both[2 * q + 1] = dep[g.n_chunks + q];
+                    }
+                    dep.swap(both);
+                    c->d_dep = (int2 *)dev_alloc(c, sizeof(int32_t) * dep.size());
+                    if (!c->d_dep) {
+                        kpm_staged_release(&sg);
+                        kpm_gather_release(&g);
+                        return fail(KPM_ENOMEM);
+                    }
+                    if (cudaMemcpy(c->d_dep, dep.data(), sizeof(int32_t) * dep.size(),
+                                   cudaMemcpyHostToDevice) != cudaSuccess) {
+                        kpm_staged_release(&sg);
+                        kpm_gather_release(&g);
+                        return fail(KPM_ECUDA);
+                    }
+                    c->upload_bytes += (int64_t)(sizeof(int32_t) * dep.size());
+                }
+            }
             c->u_max = g.u_max;
             c->l_max = sg.l_max;
             const int64_t n_staged = sg.n_stored;
@@ -905,6 +996,8 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_aux);
     dev_free(c, c->d_rec);
     dev_free(c, c->d_ovf);
+    dev_free(c, c->d_dep);
+    dev_free(c, c->d_prog);
     dev_free(c, c->d_err);
     delete c;
 }
@@ -1099,6 +1192,14 @@ int kpm_set_reduce_interval(kpm_ctx *c, int32_t sweeps)
     if (!c || sweeps < 0)
         return KPM_EINVAL;
     c->reduce_interval = sweeps;
+    return KPM_OK;
+}
+
+int kpm_set_sweep_overlap(kpm_ctx *c, int32_t mode)
+{
+    if (!c || mode < KPM_OVERLAP_NONE || mode > KPM_OVERLAP_CHAIN)
+        return KPM_EINVAL;
+    c->overlap = mode;
     return KPM_OK;
 }
 

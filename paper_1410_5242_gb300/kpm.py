@@ -25,6 +25,9 @@ KPM_EUNSUPPORTED = -6
 
 PREC_FP64 = 0
 PREC_FP32 = 1
+OVERLAP_NONE = 0   # kpm_set_sweep_overlap modes
+OVERLAP_PDL = 1
+OVERLAP_CHAIN = 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -116,6 +119,7 @@ _SIGS = {
     "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
     "kpm_gather_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather)]),
     "kpm_gather_release": (None, [ctypes.POINTER(Gather)]),
+    "kpm_sweep_chain_deps": (_int, [ctypes.POINTER(Gather), _i32, _vp]),
     "kpm_staged_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather), _i32,
                                 ctypes.POINTER(Staged)]),
     "kpm_staged_release": (None, [ctypes.POINTER(Staged)]),
@@ -157,6 +161,7 @@ _SIGS = {
                                    _i32, ctypes.POINTER(Options), _pd]),
     "kpm_sweep_variant": (_int, [_vp, _i32, _vp, _vp, _i32, _vp]),
     "kpm_set_reduce_interval": (_int, [_vp, _i32]),
+    "kpm_set_sweep_overlap": (_int, [_vp, _i32]),
     "kpm_naive_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, ctypes.POINTER(_vp)]),
     "kpm_naive_moments": (_int, [_vp, _i32, _i32, _u64, _vp, _vp]),
     "kpm_naive_destroy": (None, [_vp]),
@@ -264,7 +269,8 @@ def sell_build(csr, a, b, C=32, sigma=256, row_order=None):
 
 def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
     """The SELL layout (as sell_build) and the staged kernel's gather lists of
-    kpm_gather_build: (sell dict, {"u_max", "l_max", "lidx", "run_ptr", "runs"})."""
+    kpm_gather_build: (sell dict, {"u_max", "l_max", "lidx", "run_ptr", "runs",
+    "dep"}), dep being kpm_sweep_chain_deps' table [2][n_chunks]."""
     n, rp, col, val = _csr(csr)
     s = Sell()
     order = None if row_order is None else np.ascontiguousarray(row_order, dtype=np.int32)
@@ -283,6 +289,10 @@ def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
                 "runs": np.ctypeslib.as_array(g.runs, (max(2 * g.n_runs, 1),))[:2 * g.n_runs]
                 .copy().reshape(-1, 2),
             }
+            dep = np.empty((2, g.n_chunks), dtype=np.int32)
+            _check(lib.kpm_sweep_chain_deps(ctypes.byref(g), s.C, dep.ctypes.data),
+                   "kpm_sweep_chain_deps")
+            gat["dep"] = dep
         finally:
             lib.kpm_gather_release(ctypes.byref(g))
     finally:
@@ -639,6 +649,13 @@ class Context:
 
     def set_reduce_interval(self, sweeps):
         _check(lib.kpm_set_reduce_interval(self.handle, sweeps), "kpm_set_reduce_interval")
+
+    def set_sweep_overlap(self, mode):
+        """kpm_set_sweep_overlap: OVERLAP_NONE (one plain launch per sweep),
+        OVERLAP_PDL (programmatic dependent launches, the default) or
+        OVERLAP_CHAIN (one cooperative launch per batch of sweeps between eta
+        reductions)."""
+        _check(lib.kpm_set_sweep_overlap(self.handle, mode), "kpm_set_sweep_overlap")
 
     def moments_device(self, M, R, seed, eta_dev, eta_imag_dev=None, stream=None):
         _check(lib.kpm_moments_device(
