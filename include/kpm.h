@@ -215,23 +215,6 @@ typedef struct kpm_gather {
 int kpm_gather_build(const kpm_sell *s, kpm_gather *out);
 void kpm_gather_release(kpm_gather *g);
 
-/* Dependency table of a sweep chain (KPM_OVERLAP_CHAIN), from a chunk
- * height C and the gather lists of its kpm_sell.  Successive sweeps of
- * Fig. 5 alternate the roles of the two vector blocks: sweep m reads the
- * rows sweep m-1 wrote, and overwrites the rows sweep m-1 read.  So chunk c
- * of sweep m may start once, in sweep m-1, every chunk whose rows c's list
- * holds and every chunk whose list holds a row of c is done.  A chained
- * sweep visits the chunks at positions j = 0..n-1 in the order
- * (j + rot) mod n, rot = 0 or n/2 (alternating, so that a sweep's first
- * chunks are those the previous one did half a sweep earlier).  dep (host,
- * [2][n_chunks], caller-owned) receives, for each rotation x and chunk c,
- * the largest position in a sweep of rotation x*(n/2) of a chunk c depends
- * on (c itself included: its own rows are in its list).  List rows at or
- * past n_chunks*C (a part's halo slots) belong to no chunk.  KPM_EINVAL for
- * a NULL argument, C < 1, n_chunks outside [1, 2^31 - 1] or a malformed
- * run. */
-int kpm_sweep_chain_deps(const kpm_gather *g, int32_t C, int32_t *dep);
-
 /* Entry arrays of the staged sweep (host view, for inspection and tests;
  * kpm_create builds the same arrays for the device).  The staged kernel
  * reads a chunk's entries from arrays of its own, derived from a kpm_sell
@@ -591,35 +574,21 @@ int kpm_sweep_variant(kpm_ctx *ctx, int32_t R, const void *V, void *W, int32_t v
  * reduction in every iteration, Table III). */
 int kpm_set_reduce_interval(kpm_ctx *ctx, int32_t sweeps);
 
-/* How consecutive staged sweeps overlap (the fixed cost of a sweep launch
- * -- its blocks' set-up, filling their first stages, the launch itself --
- * is ~20 us against ~0.18 ms for the 64^3 lattice at R = 32):
- *   KPM_OVERLAP_NONE   one plain launch per sweep;
- *   KPM_OVERLAP_PDL    (default) each staged sweep is a programmatic
- *                      dependent launch: its blocks are scheduled as the
- *                      previous kernel's blocks retire, set up and fetch
- *                      their first chunk records, and wait (griddepcontrol)
- *                      for that kernel's completion before touching the
- *                      vector blocks or the eta partials; results are those
- *                      of plain launches, bit for bit;
- *   KPM_OVERLAP_CHAIN  in the moment calls, the sweeps between two eta
- *                      reductions run as ONE cooperative launch per column
- *                      block where it has at least two chunks per block of
- *                      the launch: each block moves on to its chunks of the
- *                      next sweep as soon as the chunks they depend on
- *                      (kpm_sweep_chain_deps) are done in every block --
- *                      per-wave completion counters in device memory,
- *                      checked by each block's producer warp before it
- *                      copies a chunk (a bounded wait: KPM_ETIMEOUT through
- *                      kpm_check_device_error if it runs out).  W is the
- *                      same as with separate launches (each row is computed
- *                      the same way); eta's per-block partial sums of the
- *                      half-rotated sweeps cover other chunks, so eta
- *                      agrees to rounding.
+/* How consecutive staged sweeps overlap.  A sweep launch carries a fixed
+ * cost (~20 us against ~0.18 ms for the 64^3 lattice at R = 32): the
+ * launch, its blocks' set-up and the filling of their first stages, and
+ * the blocks that finish last.
+ *   KPM_OVERLAP_NONE  one plain launch per sweep;
+ *   KPM_OVERLAP_PDL   (default) each staged sweep is a programmatic
+ *                     dependent launch: its blocks are scheduled as the
+ *                     previous kernel's blocks retire, set up and fetch
+ *                     their first chunk records, and wait (griddepcontrol)
+ *                     for that kernel's completion and writes before they
+ *                     touch the vector blocks or the eta partials.  Results
+ *                     are those of plain launches, bit for bit.
  * KPM_EINVAL for a NULL context or another mode. */
 #define KPM_OVERLAP_NONE 0
 #define KPM_OVERLAP_PDL 1
-#define KPM_OVERLAP_CHAIN 2
 int kpm_set_sweep_overlap(kpm_ctx *ctx, int32_t mode);
 
 /* The naive KPM-DOS of Fig. 3 from library calls: for each start vector in

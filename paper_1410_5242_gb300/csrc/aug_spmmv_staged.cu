@@ -140,9 +140,7 @@ constexpr int kMetaDepth = 8;
 constexpr uint32_t kMetaOffset = 256;  // per stage: chunk length, problem, chunk number
 constexpr uint32_t kRingOffset = kMetaOffset + 8 * 16;
 constexpr uint32_t kRedOffset = kRingOffset + kMetaDepth * KPM_REC_WORDS * 8;
-// chain: the dependency entries of the next kMetaDepth chunks
-constexpr uint32_t kDepRingOffset = kRedOffset + 3 * 64 * 8;  // eta sum of up to 64 columns
-constexpr uint32_t kTableOffset = kDepRingOffset + kMetaDepth * 8;
+constexpr uint32_t kTableOffset = kRedOffset + 3 * 64 * 8;  // eta sum of up to 64 columns
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
 {
@@ -327,97 +325,6 @@ __device__ __forceinline__ int advance_problem(const StagedProblem *tab, int n_p
     return pi;
 }
 
-// ---------------------------------------------------------- work items
-// A block's work items are the global items blockIdx.x, + gridDim.x, ...;
-// its k-th item lies in wave k (items k*G .. k*G + G - 1, G = gridDim.x).
-//
-// Table mode: item t is tile t - tile0 of the problem owning it.
-//
-// Chain mode (chain_sweeps = S > 0): S consecutive sweeps of the single
-// problem in one launch.  Each sweep owns np = chain_np items (its n chunks
-// rounded up to a multiple of G, so that no wave spans two sweeps); item t
-// is position j = t mod np of sweep m = t / np, idle when j >= n, else
-// chunk (j + rot(m)) mod n with rot(m) = n/2 for odd m and 0 for even m:
-// the chunks a sweep starts with were done half a sweep before the previous
-// sweep ended.  Sweep m reads V from buf[(parity + m) & 1] and writes W to
-// the other block.
-template <bool CHAIN>
-struct ItemWalk {
-    int pi = 0;  // problem (table mode) or sweep (chain mode)
-    // tile within the problem, or position within the sweep (31 bits)
-    std::conditional_t<CHAIN, int, int64_t> pos = 0;
-    __device__ __forceinline__ void set(const StagedParams &p, const StagedProblem *tab, int64_t t)
-    {
-        if constexpr (CHAIN) {
-            pi = (int)(t / p.chain_np);
-            pos = (int)(t - (int64_t)pi * p.chain_np);
-        } else {
-            pi = advance_problem(tab, p.n_probs, 0, t);
-            pos = t - tab[pi].tile0;
-        }
-    }
-    // to item t, G items after the current one
-    __device__ __forceinline__ void step(const StagedParams &p, const StagedProblem *tab, int64_t t,
-                                         int64_t G)
-    {
-        if constexpr (CHAIN) {
-            pos += (int)G;
-            if (pos >= (int)p.chain_np) {
-                pos -= (int)p.chain_np;
-                pi++;
-            }
-        } else {
-            pi = advance_problem(tab, p.n_probs, pi, t);
-            pos = t - tab[pi].tile0;
-        }
-    }
-    __device__ __forceinline__ bool idle(const StagedParams &p, const StagedProblem *tab) const
-    {
-        return CHAIN && pos >= tab[0].n_tiles;
-    }
-    // the item's chunk within its problem (not for idle items)
-    __device__ __forceinline__ int64_t chunk(const StagedParams &p, const StagedProblem *tab) const
-    {
-        if (CHAIN && (pi & 1)) {
-            const int n = (int)tab[0].n_tiles, c = (int)pos + (n >> 1);
-            return c >= n ? c - n : c;
-        }
-        return pos;
-    }
-};
-
-// Per problem (table mode) or sweep (chain mode): the problem entry, the
-// vector-block parity, whether it is the initial step, and its eta partials.
-template <bool CHAIN>
-__device__ __forceinline__ const StagedProblem &prob_of(const StagedParams &p,
-                                                        const StagedProblem *tab, int pi)
-{
-    return tab[CHAIN ? 0 : pi];
-}
-template <bool CHAIN>
-__device__ __forceinline__ int vpar_of(const StagedParams &p, int pi)
-{
-    return CHAIN ? ((p.parity + pi) & 1) : p.parity;
-}
-template <bool CHAIN>
-__device__ __forceinline__ bool init_of(const StagedParams &p, int pi)
-{
-    return p.init && (!CHAIN || pi == 0);
-}
-template <bool CHAIN>
-__device__ __forceinline__ double *partial_of(const StagedParams &p, const StagedProblem *tab,
-                                              int pi)
-{
-    return CHAIN ? tab[0].partial + (int64_t)pi * p.chain_stride : tab[pi].partial;
-}
-
-__device__ __forceinline__ int ld_acquire_gpu(const int *a)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-    return v;
-}
-
 // Programmatic dependent launch: a launch that may start while the kernel
 // before it in the stream still runs lets its blocks set up (barriers,
 // problem table, the first records: data no kernel writes) and then waits
@@ -436,40 +343,12 @@ __device__ __forceinline__ void allow_dependents()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Orders this thread's earlier generic-proxy accesses (an acquire of other
-// blocks' W stores) before its later bulk copies, which read global memory
-// through the async proxy.
-__device__ __forceinline__ void fence_proxy_async_global()
-{
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // The producer warp: for each tile of this block, wait until its stage is
 // free, announce the bytes on full[s], and issue the copies.  Lane l holds
 // word l of the tile's record, i.e. inline run l - 3; runs past the inline
 // ones are read from the overflow array 32 at a time.  Returns the number
 // of tiles armed.
-//
-// CHAIN adds two duties.  Dependencies: before arming chunk c of sweep
-// m >= 1, the producer makes sure the wave holding position
-// dep[c][(m - 1) & 1] of sweep m - 1 is complete (the dependency entry
-// comes with the chunk's record; a probe reads the counter of a wave up to
-// kChainLook waves further, so one read of the counters usually covers
-// many chunks), waiting (bounded) if it is not, then fences the async
-// proxy so that its bulk copies see the other blocks' stores.
-// Publication: the producer learns from the empty barriers which armed
-// items the consumer warps have finished (in order) and counts the block
-// into prog[w] for every wave w it has completed, after a GPU-scope fence:
-// the consumers' W stores reach the producer through the barriers'
-// CTA-scope release and acquire, and the fence makes them visible to every
-// block before the count.  Idle items count once every item before them
-// does.  Counts go out kChainBatch waves at a time, and all at once before
-// the producer waits for other blocks and at the end, so no block waits on
-// a count that another block holds back.
-constexpr int kChainLook = 16;
-constexpr int kChainBatch = 4;
-
-template <int RB, int CSIZE, int VSIZE, bool CHAIN>
+template <int RB, int CSIZE, int VSIZE>
 __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char *smem,
                                            const StagedProblem *tab, int64_t total,
                                            volatile int *abort_flag)
@@ -480,213 +359,62 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
     const uint32_t ring0 = smem_u32(smem + kRingOffset);
     const int2 *ring = reinterpret_cast<const int2 *>(smem + kRingOffset);
-    const uint32_t dring0 = smem_u32(smem + kDepRingOffset);
-    const int2 *dring = reinterpret_cast<const int2 *>(smem + kDepRingOffset);
     const uint32_t stage0 = smem_u32(smem + p.bar_bytes);
     const int64_t G = gridDim.x;
+    const int par = p.parity;
 
     // the record stream runs kMetaDepth tiles ahead of the issue stream; the
     // fields of the problem each stream is in are kept in registers
     int pj = -1;
     int64_t j_end = -1, j_tile0 = 0;
     const int2 *j_rec = nullptr;
-    ItemWalk<CHAIN> jw;  // chain: the item whose record is fetched next
-    if constexpr (CHAIN)
-        jw.set(p, tab, blockIdx.x);
     auto fetch_record = [&](int64_t t, uint32_t slot) {
         if (t < total) {
-            if constexpr (CHAIN) {
-                if (!jw.idle(p, tab)) {
-                    const int64_t c = jw.chunk(p, tab);
-                    cp_async8(ring0 + (slot * KPM_REC_WORDS + lane) * 8,
-                              tab[0].rec + c * KPM_REC_WORDS + lane);
-                    if (lane == 0)
-                        cp_async8(dring0 + slot * 8, p.dep + c);
-                }
-            } else {
-                if (t >= j_end) {
-                    pj = advance_problem(tab, p.n_probs, pj < 0 ? 0 : pj, t);
-                    j_rec = tab[pj].rec;
-                    j_tile0 = tab[pj].tile0;
-                    j_end = j_tile0 + tab[pj].n_tiles;
-                }
-                cp_async8(ring0 + (slot * KPM_REC_WORDS + lane) * 8,
-                          j_rec + (t - j_tile0) * KPM_REC_WORDS + lane);
+            if (t >= j_end) {
+                pj = advance_problem(tab, p.n_probs, pj < 0 ? 0 : pj, t);
+                j_rec = tab[pj].rec;
+                j_tile0 = tab[pj].tile0;
+                j_end = j_tile0 + tab[pj].n_tiles;
             }
+            cp_async8(ring0 + (slot * KPM_REC_WORDS + lane) * 8,
+                      j_rec + (t - j_tile0) * KPM_REC_WORDS + lane);
         }
         cp_async_commit();
-        if constexpr (CHAIN)
-            jw.step(p, tab, t + G, G);
     };
     for (int i = 0; i < kMetaDepth; i++)
         fetch_record(blockIdx.x + i * G, (uint32_t)i);
     grid_dependency_wait();
-
-    // chain: armed items c_lo .. k-1 are not yet known finished (their
-    // waves are kept in the stages' metadata words); waves < front are
-    // finished in this block, waves < pub counted, waves < done_w known
-    // complete in every block (wave numbers fit 31 bits: checked at launch)
-    int c_lo = 0, pub = 0, done_w = 0, kk = 0, front = 0;
-    int cs = 0;        // stage of armed item c_lo
-    uint32_t cph = 0;  // parity of that stage's use by item c_lo
-    int64_t k = 0;     // items armed
-    auto wave_slot = [&](int st) {
-        return reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * st + 8);
-    };
-    // counts the block into waves pub .. front - 1 (kChainBatch at a time
-    // unless forced)
-    auto publish = [&](bool force) {
-        if (front > pub && (force || front - pub >= kChainBatch)) {
-            if (lane == 0) {
-                __threadfence();
-                for (int w = pub; w < front; w++)
-                    atomicAdd(p.prog + w, 1);
-            }
-            pub = front;
-        }
-    };
-    // moves the frontier past finished armed items: waiting for each (every
-    // lane) while c_lo < lim, then, if test, past those a test (lane 0)
-    // finds finished; false if a wait failed
-    auto reap = [&](int64_t lim, bool test) -> bool {
-        while (c_lo < k) {
-            const uint32_t e = empty0 + 8 * cs;
-            if (c_lo < lim) {
-                const bool ok = mbar_wait_bounded(e, cph, abort_flag, p.err, true);
-                if (!__all_sync(0xffffffffu, ok))
-                    return false;
-            } else if (!test) {
-                return true;
-            } else {
-                const int got = lane == 0 ? (int)mbar_try_wait(e, cph) : 0;
-                if (!__shfl_sync(0xffffffffu, got, 0))
-                    return true;
-            }
-            c_lo++;
-            if (++cs == NS) {
-                cs = 0;
-                cph ^= 1u;
-            }
-            front = c_lo < k ? *wave_slot(cs) : kk;
-        }
-        return true;
-    };
-    // whether wave w is complete in every block (an acquire read)
-    auto wave_done = [&](int w) -> bool {
-        const int v = lane == 0 ? ld_acquire_gpu(p.prog + w) : 0;
-        return __shfl_sync(0xffffffffu, v, 0) >= (int)G;
-    };
-    // waits until wave w is complete in every block, counting the block's
-    // own finished items meanwhile
-    auto wait_wave = [&](int w) -> bool {
-        const long long t0 = clock64();
-        for (;;) {
-            if (!reap(0, true))
-                return false;
-            publish(true);
-            if (wave_done(w))
-                return true;
-            int stop = 0;
-            if (lane == 0) {
-                if (*abort_flag) {
-                    stop = 1;
-                } else if (*reinterpret_cast<volatile int *>(p.err) != 0) {
-                    *abort_flag = 1;
-                    stop = 1;
-                } else if (clock64() - t0 > kWaitLimitCycles) {
-                    *abort_flag = 1;
-                    atomicExch(p.err, KPM_DEVERR_TIMEOUT);
-                    stop = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0))
-                return false;
-            __nanosleep(256);
-        }
-    };
-
     int pi = -1;
     int64_t i_end = -1, i_tile0 = 0;
     const char *Vb = nullptr, *Wb = nullptr, *valb = nullptr, *lidxb = nullptr;
     const int2 *ovfp = nullptr;
     int ld = 0, col0 = 0;
-    ItemWalk<CHAIN> iw;  // chain: the item being issued
-    int wps = 0;         // chain: waves per sweep
-    if constexpr (CHAIN) {
-        iw.set(p, tab, blockIdx.x);
-        wps = (int)(p.chain_np / G);
-        valb = static_cast<const char *>(tab[0].val);
-        lidxb = reinterpret_cast<const char *>(tab[0].lidx);
-        ovfp = tab[0].ovf;
-        ld = tab[0].ld;
-        col0 = tab[0].col0;
-    }
+    int64_t k = 0;
     int s = 0;          // stage of tile k
     uint32_t ph = 0;    // parity of that stage's current use
-    bool failed = false;
-    for (int64_t gt = blockIdx.x; gt < total; gt += G, kk++) {
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         if (p.stall_after >= 0 && k >= p.stall_after)
             break;  // test hook: leave the remaining stages unarmed
-        if (CHAIN && kk > 0)
-            iw.step(p, tab, gt, G);
-        const int slot = (int)(kk & (kMetaDepth - 1));
+        const int slot = (int)(k % kMetaDepth);
         cp_async_wait<kMetaDepth - 1>();
         __syncwarp();
         const int2 word = ring[slot * KPM_REC_WORDS + lane];
-        const int2 dword = CHAIN ? dring[slot] : make_int2(0, 0);
         __syncwarp();
         fetch_record(gt + kMetaDepth * G, (uint32_t)slot);
-        bool init = p.init != 0;
-        int64_t lt;  // chunk within the problem
-        if constexpr (CHAIN) {
-            if (iw.idle(p, tab)) {
-                // nothing to copy; counted once the items before it are
-                if (c_lo == k) {
-                    front = kk + 1;
-                    publish(false);
-                }
-                continue;
-            }
-            lt = iw.chunk(p, tab);
-            const int vp = vpar_of<CHAIN>(p, iw.pi);
-            Vb = static_cast<const char *>(tab[0].buf[vp]);
-            Wb = static_cast<const char *>(tab[0].buf[vp ^ 1]);
-            init = init_of<CHAIN>(p, iw.pi);
-            // the chunks this one depends on, done in the previous sweep
-            if (iw.pi >= 1) {
-                const uint32_t dp = (uint32_t)((iw.pi - 1) & 1 ? dword.y : dword.x);
-                const int w0 = (iw.pi - 1) * wps;
-                const int need = w0 + (int)(dp / (uint32_t)G);
-                if (need >= done_w) {
-                    const int probe = min(need + kChainLook, w0 + wps - 1);
-                    if (probe > need && wave_done(probe)) {
-                        done_w = probe + 1;
-                    } else {
-                        if (!wait_wave(need)) {
-                            failed = true;
-                            break;
-                        }
-                        done_w = need + 1;
-                    }
-                    fence_proxy_async_global();
-                }
-            }
-        } else {
-            if (gt >= i_end) {
-                pi = advance_problem(tab, p.n_probs, pi < 0 ? 0 : pi, gt);
-                const StagedProblem &P = tab[pi];
-                i_tile0 = P.tile0;
-                i_end = i_tile0 + P.n_tiles;
-                Vb = static_cast<const char *>(P.buf[p.parity]);
-                Wb = static_cast<const char *>(P.buf[p.parity ^ 1]);
-                valb = static_cast<const char *>(P.val);
-                lidxb = reinterpret_cast<const char *>(P.lidx);
-                ovfp = P.ovf;
-                ld = P.ld;
-                col0 = P.col0;
-            }
-            lt = gt - i_tile0;
+        if (gt >= i_end) {
+            pi = advance_problem(tab, p.n_probs, pi < 0 ? 0 : pi, gt);
+            const StagedProblem &P = tab[pi];
+            i_tile0 = P.tile0;
+            i_end = i_tile0 + P.n_tiles;
+            Vb = static_cast<const char *>(P.buf[par]);
+            Wb = static_cast<const char *>(P.buf[par ^ 1]);
+            valb = static_cast<const char *>(P.val);
+            lidxb = reinterpret_cast<const char *>(P.lidx);
+            ovfp = P.ovf;
+            ld = P.ld;
+            col0 = P.col0;
         }
+        const int64_t lt = gt - i_tile0;  // chunk within the problem
 
         auto word64 = [&](int w) {
             return (int64_t)(uint32_t)__shfl_sync(0xffffffffu, word.x, w) |
@@ -709,14 +437,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         }
 
         const uint32_t full = full0 + 8 * s, empty = empty0 + 8 * s;
-        if constexpr (CHAIN) {
-            // stage s is free once item k - NS is finished
-            if (!reap(k - NS + 1, false)) {
-                failed = true;
-                break;
-            }
-            publish(false);
-        } else if (k >= NS) {
+        if (k >= NS) {
             // every lane waits (and acquires); the warp leaves together
             const bool ok = mbar_wait_bounded(empty, ph ^ 1u, abort_flag, p.err, true);
             if (!__all_sync(0xffffffffu, ok))
@@ -726,15 +447,13 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const uint32_t val_bytes = (uint32_t)p.C * (uint32_t)len * (uint32_t)VSIZE;
         const uint32_t lidx_bytes = (uint32_t)p.C * (uint32_t)len * 2u;
         // the chunk's old W rows with the stage (complex float, off_w set)
-        const bool w_in_stage = p.off_w != 0 && !init;
+        const bool w_in_stage = p.off_w != 0 && !p.init;
         const uint32_t bytes = total_rows * row_bytes + val_bytes + lidx_bytes +
                                (w_in_stage ? (uint32_t)p.C * row_bytes : 0u);
         if (lane == 0) {
             volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
             meta[1] = nre;
-            if constexpr (CHAIN)
-                *wave_slot(s) = kk;
             mbar_arrive_expect_tx(full, bytes);
         }
         __syncwarp();
@@ -747,7 +466,7 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         if (w_in_stage) {
             if (lane == 2)
                 copy_rows(st + p.off_w, Wb, lt * (int64_t)p.C, p.C, ld, col0, row_bytes, full, CSIZE);
-        } else if (!init && lane == 2 && ((int64_t)ld * CSIZE & 15) == 0) {
+        } else if (!p.init && lane == 2 && ((int64_t)ld * CSIZE & 15) == 0) {
             // the consumers read the chunk's old W rows themselves; ask L2
             // for them now (whole rows: contiguous, 16-byte multiples)
             prefetch_l2(Wb + lt * (int64_t)p.C * ld * CSIZE, (uint64_t)p.C * ld * CSIZE);
@@ -766,18 +485,12 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
                           row_bytes, full, CSIZE);
             base += (uint32_t)__shfl_sync(0xffffffffu, ri, 31);
         }
-        k++;
         if (++s == NS) {
             s = 0;
             ph ^= 1u;
         }
     }
     cp_async_wait<0>();
-    // chain: every armed item finished, then the block's last waves counted
-    if (CHAIN && !failed && (int64_t)kk * G + blockIdx.x >= total && reap(k, false)) {
-        front = kk;
-        publish(true);
-    }
     return k;
 }
 
@@ -786,19 +499,12 @@ __device__ __forceinline__ void consumer_bar(int n_cw)
     asm volatile("bar.sync 1, %0;" ::"r"(n_cw * 32) : "memory");
 }
 
-// Where a problem's (or a chained sweep's) eta sums go: element t of the
-// block's slot at partial[slot * ps + t * qs].
-struct PartialSlot {
-    double *partial = nullptr;
-    int64_t slot = 0, ps = 0, qs = 0;
-};
-
 // Complex float: one problem's eta sums, warp after warp into red (3*RB
 // doubles) from each warp's running pairs, then red to the problem's
 // partial slot.  The caller has folded its pending terms.
 template <int T, int E, bool IMAG>
 __device__ __forceinline__ void flush_eta32(WarpEta<IMAG, T, E> &pe, double *red,
-                                            const PartialSlot &P, int cw, int n_cw)
+                                            const StagedProblem &P, int64_t slot, int cw, int n_cw)
 {
     constexpr int RB = T * E;
     const int lane = threadIdx.x & 31;
@@ -809,7 +515,7 @@ __device__ __forceinline__ void flush_eta32(WarpEta<IMAG, T, E> &pe, double *red
         consumer_bar(n_cw);
     }
     for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
-        P.partial[P.slot * P.ps + t * P.qs] = (!IMAG && t >= 2 * RB) ? 0.0 : red[t];
+        P.partial[slot * P.ps + t * P.qs] = (!IMAG && t >= 2 * RB) ? 0.0 : red[t];
     consumer_bar(n_cw);
 }
 
@@ -818,8 +524,8 @@ __device__ __forceinline__ void flush_eta32(WarpEta<IMAG, T, E> &pe, double *red
 // into red (3*RB doubles), then red to the problem's partial slot.  Resets
 // acc.
 template <int T, int E, typename Acc>
-__device__ __forceinline__ void flush_eta64(Acc (&acc)[E], double *red, const PartialSlot &P,
-                                            int cw, int n_cw)
+__device__ __forceinline__ void flush_eta64(Acc (&acc)[E], double *red, const StagedProblem &P,
+                                            int64_t slot, int cw, int n_cw)
 {
     constexpr int RB = T * E;
     const int lane = threadIdx.x & 31;
@@ -848,7 +554,7 @@ __device__ __forceinline__ void flush_eta64(Acc (&acc)[E], double *red, const Pa
         consumer_bar(n_cw);
     }
     for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
-        P.partial[P.slot * P.ps + t * P.qs] = red[t];
+        P.partial[slot * P.ps + t * P.qs] = red[t];
     consumer_bar(n_cw);
 #pragma unroll
     for (int k = 0; k < E; k++)
@@ -947,38 +653,11 @@ __device__ __forceinline__ void walk_region(const uint16_t *lid, const float *hv
 // consumers use.  Every consumer warp derives it from the tile number and
 // the problem table alone (never from what the producer wrote), so all of
 // them see the same sequence of problems.
-template <bool CHAIN>
 struct ConsumerProblem {
-    ItemWalk<CHAIN> it;  // the current item
-    int cur = -1;  // the problem (sweep) whose sums are being accumulated
+    int pi = 0, cur = -1;
     int64_t slot = 0;
     void *W = nullptr;
     int ld = 0, col0 = 0;
-    bool init = false;
-    // the fields of the current item's problem or sweep
-    __device__ __forceinline__ void begin(const StagedParams &p, const StagedProblem *tab)
-    {
-        const StagedProblem &Q = prob_of<CHAIN>(p, tab, it.pi);
-        cur = it.pi;
-        if constexpr (!CHAIN)
-            slot = it.pos;
-        W = Q.buf[vpar_of<CHAIN>(p, it.pi) ^ 1];
-        ld = Q.ld;
-        col0 = Q.col0;
-        init = init_of<CHAIN>(p, it.pi);
-    }
-    // where the sums of problem (sweep) cur go
-    __device__ __forceinline__ PartialSlot out(const StagedParams &p,
-                                               const StagedProblem *tab) const
-    {
-        const StagedProblem &Q = prob_of<CHAIN>(p, tab, cur);
-        PartialSlot o;
-        o.partial = partial_of<CHAIN>(p, tab, cur);
-        o.slot = CHAIN ? (int64_t)blockIdx.x : slot;
-        o.ps = Q.ps;
-        o.qs = Q.qs;
-        return o;
-    }
 };
 
 // Complex float consumer warp.  Per chunk: the row's old W is loaded into
@@ -1001,7 +680,7 @@ struct ConsumerProblem {
 // warp whose wait fails (timeout, or the block's abort flag) sets `failed`
 // and skips the work and the waits of its remaining tiles, but not the
 // flushes: the barrier counts always match.
-template <int T, int E, bool IMAG, bool HALF, bool CHAIN>
+template <int T, int E, bool IMAG, bool HALF>
 __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *smem,
                                           const StagedProblem *tab, int64_t total,
                                           volatile int *abort_flag)
@@ -1023,53 +702,51 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
     int nfold = 0;
     uint64_t pa[E], pb[E];
     float4 wo[NP];  // the row's old W pieces
-    // the old W of the row of chunk lt in block Wv (leading dimension ld)
-    // into wo
-    auto load_w = [&](const void *Wv, int64_t lt, int ld, int col0) {
-        const float *Wq = static_cast<const float *>(Wv);
-        const int64_t row = lt * (int64_t)C + rit;
-        const int64_t wb = row * ld + col0 + tl * EV;
+    // the old W of the row of tile gt (problem q) into wo
+    auto load_w = [&](int64_t gt, int q) {
+        const StagedProblem &Q = tab[q];
+        const float *Wq = static_cast<const float *>(Q.buf[p.parity ^ 1]);
+        const int64_t row = (gt - Q.tile0) * (int64_t)C + rit;
+        const int64_t wb = row * Q.ld + Q.col0 + tl * EV;
 #pragma unroll
         for (int q2 = 0; q2 < NP; q2++)
             wo[q2] = __ldcg(reinterpret_cast<const float4 *>(Wq + 2 * (wb + q2 * T * EV)));
     };
-    constexpr bool chain = CHAIN;
-    ConsumerProblem<CHAIN> cp;
-    cp.it.set(p, tab, blockIdx.x);
+    ConsumerProblem cp;
     bool failed = false, have_w = false;
+    int64_t k = 0;
     int s_next = 0;          // stage of the next tile
     uint32_t ph_next = 0;    // parity of that stage's current use
-    for (int64_t gt = blockIdx.x; gt < total; gt += G) {
-        if (gt != (int64_t)blockIdx.x)
-            cp.it.step(p, tab, gt, G);
-        if (cp.it.pi != cp.cur) {
-            if (cp.cur >= 0 && p.dots) {
-                pe.fold(team);
-                nfold = 0;
-                flush_eta32<T, E, IMAG>(pe, red, cp.out(p, tab), cw, n_cw);
-            }
-            cp.begin(p, tab);
-        }
-        if (failed || cp.it.idle(p, tab))
-            continue;
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         const int s = s_next;
         const uint32_t ph = ph_next;
         if (++s_next == NS) {
             s_next = 0;
             ph_next ^= 1u;
         }
-        const int64_t lt = cp.it.chunk(p, tab);
-        // a chained sweep's old W is read only once the stage is full: the
-        // producer's dependency wait precedes it
-        if (!cp.init && !p.off_w && !have_w && !chain)
-            load_w(cp.W, lt, cp.ld, cp.col0);
+        cp.pi = advance_problem(tab, p.n_probs, cp.pi, gt);
+        const int64_t lt = gt - tab[cp.pi].tile0;
+        if (cp.pi != cp.cur) {
+            if (cp.cur >= 0 && p.dots) {
+                pe.fold(team);
+                nfold = 0;
+                flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
+            }
+            cp.cur = cp.pi;
+            cp.slot = lt;
+            cp.W = tab[cp.pi].buf[p.parity ^ 1];
+            cp.ld = tab[cp.pi].ld;
+            cp.col0 = tab[cp.pi].col0;
+        }
+        if (failed)
+            continue;
+        if (!p.init && !p.off_w && !have_w)
+            load_w(gt, cp.pi);
         const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
         if (!__all_sync(0xffffffffu, ok)) {
             failed = true;
             continue;
         }
-        if (!cp.init && !p.off_w && chain)
-            load_w(cp.W, lt, cp.ld, cp.col0);
         const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
         const volatile int *meta = reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
         const int len = meta[0];
@@ -1154,7 +831,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             w[2 * c] = ar - bi;
             w[2 * c + 1] = ai + br;
         }
-        if (cp.init) {
+        if (p.init) {
 #pragma unroll
             for (int i = 0; i < 2 * E; i++)
                 w[i] *= 0.5f;
@@ -1179,9 +856,8 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, w);
         // the next tile's old W, while this one's scalar products are added
         have_w = false;
-        if (!cp.init && !p.off_w && !chain && gt + G < total) {
-            const StagedProblem &Q = tab[advance_problem(tab, p.n_probs, cp.it.pi, gt + G)];
-            load_w(Q.buf[p.parity ^ 1], gt + G - Q.tile0, Q.ld, Q.col0);
+        if (!p.init && !p.off_w && gt + G < total) {
+            load_w(gt + G, advance_problem(tab, p.n_probs, cp.pi, gt + G));
             have_w = true;
         }
         if (p.dots) {
@@ -1203,7 +879,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         return;
     if (cp.cur >= 0) {
         pe.fold(team);
-        flush_eta32<T, E, IMAG>(pe, red, cp.out(p, tab), cw, n_cw);
+        flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
     } else if (p.probs == nullptr) {
         // a single problem's partials are read for every block: a block
         // without chunks contributes zeros
@@ -1223,7 +899,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
 // form's nonzero products in the same order (the skipped ones add exact
 // zeros), so both forms give the same W.  Eta in plain FMA chains.  Abort
 // safety as in consume32.
-template <int T, int E, bool IMAG, bool HALF, bool CHAIN>
+template <int T, int E, bool IMAG, bool HALF>
 __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *smem,
                                           const StagedProblem *tab, int64_t total,
                                           volatile int *abort_flag)
@@ -1241,28 +917,31 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
     double *red = reinterpret_cast<double *>(smem + kRedOffset);
     StagedEta64<IMAG> acc[E];
-    ConsumerProblem<CHAIN> cp;
-    cp.it.set(p, tab, blockIdx.x);
+    ConsumerProblem cp;
     bool failed = false;
+    int64_t k = 0;
     int s_next = 0;          // stage of the next tile
     uint32_t ph_next = 0;    // parity of that stage's current use
-    for (int64_t gt = blockIdx.x; gt < total; gt += G) {
-        if (gt != (int64_t)blockIdx.x)
-            cp.it.step(p, tab, gt, G);
-        if (cp.it.pi != cp.cur) {
-            if (cp.cur >= 0 && p.dots)
-                flush_eta64<T, E>(acc, red, cp.out(p, tab), cw, n_cw);
-            cp.begin(p, tab);
-        }
-        if (failed || cp.it.idle(p, tab))
-            continue;
+    for (int64_t gt = blockIdx.x; gt < total; gt += G, k++) {
         const int s = s_next;
         const uint32_t ph = ph_next;
         if (++s_next == NS) {
             s_next = 0;
             ph_next ^= 1u;
         }
-        const int64_t lt = cp.it.chunk(p, tab);
+        cp.pi = advance_problem(tab, p.n_probs, cp.pi, gt);
+        const int64_t lt = gt - tab[cp.pi].tile0;
+        if (cp.pi != cp.cur) {
+            if (cp.cur >= 0 && p.dots)
+                flush_eta64<T, E>(acc, red, tab[cp.cur], cp.slot, cw, n_cw);
+            cp.cur = cp.pi;
+            cp.slot = lt;
+            cp.W = tab[cp.pi].buf[p.parity ^ 1];
+            cp.ld = tab[cp.pi].ld;
+            cp.col0 = tab[cp.pi].col0;
+        }
+        if (failed)
+            continue;
         const bool ok = mbar_wait_bounded(full0 + 8 * s, ph, abort_flag, p.err, true);
         if (!__all_sync(0xffffffffu, ok)) {
             failed = true;
@@ -1280,7 +959,7 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
         // (written and read by this lane only) with cp.async
         const int64_t wbase = (lt * (int64_t)C + rit) * cp.ld + cp.col0 + tl * EV;
         double *wsm = reinterpret_cast<double *>(smem + p.off_aux) + rit * 2 * RB;
-        if (!cp.init) {
+        if (!p.init) {
 #pragma unroll
             for (int q = 0; q < NP; q++)
                 cp_async16(smem_u32(wsm + 2 * (q * T * EV + tl * EV)),
@@ -1322,7 +1001,7 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
             },
             [&](int j, uint32_t u) { entry(u, vals[C * j + rit]); });
         entry((uint32_t)lid[C * nm + rit], vals[C * nm + rit]);
-        if (cp.init) {
+        if (p.init) {
 #pragma unroll
             for (int q = 0; q < 2 * E; q++)
                 a[q] *= 0.5;
@@ -1354,14 +1033,14 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
     if (!p.dots)
         return;
     if (cp.cur >= 0) {
-        flush_eta64<T, E>(acc, red, cp.out(p, tab), cw, n_cw);
+        flush_eta64<T, E>(acc, red, tab[cp.cur], cp.slot, cw, n_cw);
     } else if (p.probs == nullptr) {
         for (int t = cw * 32 + lane; t < 3 * RB; t += n_cw * 32)
             tab[0].partial[(int64_t)blockIdx.x * tab[0].ps + t * tab[0].qs] = 0.0;
     }
 }
 
-template <typename Real, int T, int E, bool IMAG, bool HALF, bool CHAIN>
+template <typename Real, int T, int E, bool IMAG, bool HALF>
 __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, E>::value)
     aug_spmmv_staged_kernel(const StagedParams p)
 {
@@ -1400,11 +1079,10 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
             reinterpret_cast<uint64_t *>(tab)[i] = reinterpret_cast<const uint64_t *>(src)[i];
     }
     __syncthreads();
-    const int64_t total = CHAIN ? p.chain_sweeps * p.chain_np
-                                : tab[p.n_probs - 1].tile0 + tab[p.n_probs - 1].n_tiles;
+    const int64_t total = tab[p.n_probs - 1].tile0 + tab[p.n_probs - 1].n_tiles;
 
     if (warp == 0) {
-        const int64_t armed = produce<RB, CSIZE, VSIZE, CHAIN>(p, smem, tab, total, abort_flag);
+        const int64_t armed = produce<RB, CSIZE, VSIZE>(p, smem, tab, total, abort_flag);
         // the copies of the last armed stages must land before the block's
         // shared memory is released
         if (lane == 0)
@@ -1413,9 +1091,9 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
                                   abort_flag, p.err, false);
         __syncwarp();
     } else if constexpr (sizeof(Real) == 4) {
-        consume32<T, E, IMAG, HALF, CHAIN>(p, smem, tab, total, abort_flag);
+        consume32<T, E, IMAG, HALF>(p, smem, tab, total, abort_flag);
     } else {
-        consume64<T, E, IMAG, HALF, CHAIN>(p, smem, tab, total, abort_flag);
+        consume64<T, E, IMAG, HALF>(p, smem, tab, total, abort_flag);
     }
 }
 
@@ -1480,11 +1158,10 @@ template <typename Real, int T, int E, bool IMAG, bool HALF>
 int occupancy_of(int threads, size_t smem)
 {
     int nb = 0;
-    if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, false>,
+    if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, false>, threads, smem) !=
-            cudaSuccess) {
+            &nb, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1492,36 +1169,13 @@ int occupancy_of(int threads, size_t smem)
 }
 
 // Launches one instantiation, raising its dynamic shared-memory limit on
-// the current device the first time a launch there needs more.  A sweep
-// chain runs the CHAIN instantiation as a cooperative launch.
+// the current device the first time a launch there needs more.
 template <typename Real, int T, int E, bool IMAG, bool HALF>
 int launch_one_staged(const StagedParams &p, int grid, int threads, size_t smem, cudaStream_t st,
                       bool pdl)
 {
-    if (p.chain_sweeps > 0) {
-        KPM_TRY(ensure_max_dynamic_smem(
-            (const void *)aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, true>, smem));
-        // a sweep chain's blocks wait for one another: all must be resident
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3((unsigned)threads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        const cudaError_t e =
-            cudaLaunchKernelEx(&cfg, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, true>, p);
-        if (e == cudaErrorCooperativeLaunchTooLarge) {
-            cudaGetLastError();
-            return KPM_EUNSUPPORTED;
-        }
-        return e == cudaSuccess ? KPM_OK : KPM_ECUDA;
-    }
-    KPM_TRY(ensure_max_dynamic_smem(
-        (const void *)aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, false>, smem));
+    KPM_TRY(ensure_max_dynamic_smem((const void *)aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
+                                    smem));
     if (pdl) {
         // may start while the previous kernel in the stream finishes
         cudaLaunchConfig_t cfg = {};
@@ -1534,12 +1188,12 @@ int launch_one_staged(const StagedParams &p, int grid, int threads, size_t smem,
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, false>, p) ==
+        return cudaLaunchKernelEx(&cfg, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>, p) ==
                        cudaSuccess
                    ? KPM_OK
                    : KPM_ECUDA;
     }
-    aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF, false><<<grid, threads, smem, st>>>(p);
+    aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF><<<grid, threads, smem, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? KPM_OK : KPM_ECUDA;
 }
 
@@ -1568,17 +1222,9 @@ int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64, bool h
 int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream,
                         bool pdl)
 {
-    pdl = pdl && p.chain_sweeps == 0;
     const int threads = 32 + p.C * T;
     if (grid < 1 || threads > KPM_STAGED_MAX_THREADS || p.stages < 1 || p.stages > 8 ||
         p.n_probs < 1 || (p.probs == nullptr && p.n_probs != 1))
-        return KPM_EINVAL;
-    if (p.chain_sweeps > 0 &&
-        (p.probs != nullptr || !p.prog || !p.err || !p.dep ||
-         p.one.tile0 != 0 || p.one.n_tiles < 1 || p.one.n_tiles > INT32_MAX ||
-         p.chain_np % grid != 0 || p.chain_np < p.one.n_tiles || p.chain_np - p.one.n_tiles >= grid ||
-         p.chain_np > INT32_MAX - grid || p.chain_sweeps * (p.chain_np / grid) > INT32_MAX - 1 ||
-         p.stall_after >= 0))
         return KPM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 #define KPM_CASE(T_, E_)                                                                       \

@@ -528,7 +528,9 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                 q.off_lidx = sc.L.off_lidx;
                 q.off_aux = sc.L.off_aux;
                 q.off_w = sc.L.off_w;
-                rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture);
+                // a programmatic dependent of the step's previous kernel:
+                // its blocks set up while that kernel finishes
+                rc = launch_sweep_staged(q, sc.T, sc.E, sc.grid, sc.L.smem, b->capture, true);
                 if (rc != KPM_OK)
                     break;
             } else if (fp64)

@@ -524,44 +524,6 @@ int launch_one(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool ini
     return launch_sweep_fp32(p, cb.shape, cb.grid, init, st);
 }
 
-// Whether column block cb's sweeps can run as a chain (KPM_OVERLAP_CHAIN).
-bool chain_ok(const kpm_ctx *c, const ColumnBlock &cb)
-{
-    return c->overlap == KPM_OVERLAP_CHAIN && c->d_dep && cb.shape.stages > 0 &&
-           c->stall_after < 0 && c->n_halo == 0 && c->n_chunks >= 2 * (int64_t)cb.grid;
-}
-
-// Sweeps m0 .. m0 + sweeps - 1 of column block cb as one chain launch: V of
-// sweep m0 in V, its W in W, sweep m0 + j's partials at partial + j *
-// stride.  KPM_EUNSUPPORTED if the blocks cannot all be resident.
-int launch_chain(kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p, bool init, int sweeps,
-                 int64_t stride, cudaStream_t st)
-{
-    StagedLayout L;
-    StagedParams q;
-    KPM_TRY(staged_params(c, cb, p, init, true, q, L));
-    const int64_t G = cb.grid;
-    const int64_t np = (c->n_chunks + G - 1) / G * G;
-    const int64_t waves = (int64_t)sweeps * (np / G);
-    if (waves > c->prog_ints) {
-        dev_free(c, c->d_prog);
-        c->d_prog = (int *)dev_alloc(c, sizeof(int) * waves);
-        c->prog_ints = c->d_prog ? waves : 0;
-        if (!c->d_prog)
-            return KPM_ENOMEM;
-    }
-    KPM_CUDA(cudaMemsetAsync(c->d_prog, 0, sizeof(int) * waves, st));
-    q.chain_sweeps = sweeps;
-    q.chain_np = np;
-    q.chain_stride = stride;
-    q.prog = c->d_prog;
-    q.dep = c->d_dep;
-    const int rc = launch_sweep_staged(q, cb.shape.T, cb.shape.E, cb.grid, L.smem, st);
-    if (rc == KPM_OK)
-        c->launches++;
-    return rc;
-}
-
 }  // namespace
 
 int kpm::launch_phases_raw(void *V, bool fp64, const int32_t *perm, int64_t n, int64_t n_pad,
@@ -599,9 +561,8 @@ int autotune_shapes(kpm_ctx *c, int R, int sweeps, cudaStream_t st, float *ms_pe
 
 // The sweep schedule of Fig. 5 on device buffers already holding V = nu_0:
 // sweep m reads V = d_V (m even) or d_W (m odd) and overwrites the other.
-// Sweeps run in batches of `slots` between eta reductions; per column block
-// a batch is one chain launch where the block allows it, else one launch per
-// sweep.
+// Sweeps run in batches of `slots` between eta reductions, column block by
+// column block.
 int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStream_t st)
 {
     NvtxRange range("sweeps and eta reductions (enqueue)");
@@ -618,16 +579,6 @@ int run_schedule(kpm_ctx *c, int M, int R, double *eta, double *eta_im, cudaStre
     for (int m0 = 0; m0 < sweeps; m0 += slots) {
         const int pending = std::min(slots, sweeps - m0);
         for (const ColumnBlock &cb : blocks) {
-            int rc = KPM_EUNSUPPORTED;
-            if (pending >= 2 && chain_ok(c, cb)) {
-                void *V = (m0 & 1) ? c->d_W : c->d_V, *W = (m0 & 1) ? c->d_V : c->d_W;
-                SweepParams p = sweep_params(c, cb, R, V, W, c->d_partial + cb.partial_offset, imag);
-                rc = launch_chain(c, cb, p, m0 == 0, pending, slot_doubles, st);
-                if (rc != KPM_OK && rc != KPM_EUNSUPPORTED)
-                    return rc;
-            }
-            if (rc == KPM_OK)
-                continue;
             for (int j = 0; j < pending; j++) {
                 const int m = m0 + j;
                 void *V = (m & 1) ? c->d_W : c->d_V, *W = (m & 1) ? c->d_V : c->d_W;
@@ -917,40 +868,6 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 (ovf.empty() || cudaMemcpy(c->d_ovf, ovf.data(), sizeof(int2) * ovf.size(),
                                            cudaMemcpyHostToDevice) == cudaSuccess);
-            // the dependency table of sweep chains (none for a part: its
-            // sweeps are separated by halo exchanges)
-            if (ok && opt.n_halo == 0 && g.n_chunks <= INT32_MAX) {
-                std::vector<int32_t> dep;
-                try {
-                    dep.resize(2 * (size_t)g.n_chunks);
-                } catch (const std::bad_alloc &) {
-                    kpm_staged_release(&sg);
-                    kpm_gather_release(&g);
-                    return fail(KPM_ENOMEM);
-                }
-                if (kpm_sweep_chain_deps(&g, sell.C, dep.data()) == KPM_OK) {
-                    // interleaved for the kernel: one 8-byte entry per chunk
-                    std::vector<int32_t> both(dep.size());
-                    for (int64_t q = 0; q < g.n_chunks; q++) {
-                        both[2 * q] = dep[q];
-                        both[2 * q + 1] = dep[g.n_chunks + q];
-                    }
-                    dep.swap(both);
-                    c->d_dep = (int2 *)dev_alloc(c, sizeof(int32_t) * dep.size());
-                    if (!c->d_dep) {
-                        kpm_staged_release(&sg);
-                        kpm_gather_release(&g);
-                        return fail(KPM_ENOMEM);
-                    }
-                    if (cudaMemcpy(c->d_dep, dep.data(), sizeof(int32_t) * dep.size(),
-                                   cudaMemcpyHostToDevice) != cudaSuccess) {
-                        kpm_staged_release(&sg);
-                        kpm_gather_release(&g);
-                        return fail(KPM_ECUDA);
-                    }
-                    c->upload_bytes += (int64_t)(sizeof(int32_t) * dep.size());
-                }
-            }
             c->u_max = g.u_max;
             c->l_max = sg.l_max;
             const int64_t n_staged = sg.n_stored;
@@ -996,8 +913,6 @@ void kpm_destroy(kpm_ctx *c)
     dev_free(c, c->d_aux);
     dev_free(c, c->d_rec);
     dev_free(c, c->d_ovf);
-    dev_free(c, c->d_dep);
-    dev_free(c, c->d_prog);
     dev_free(c, c->d_err);
     delete c;
 }
@@ -1197,7 +1112,7 @@ int kpm_set_reduce_interval(kpm_ctx *c, int32_t sweeps)
 
 int kpm_set_sweep_overlap(kpm_ctx *c, int32_t mode)
 {
-    if (!c || mode < KPM_OVERLAP_NONE || mode > KPM_OVERLAP_CHAIN)
+    if (!c || mode < KPM_OVERLAP_NONE || mode > KPM_OVERLAP_PDL)
         return KPM_EINVAL;
     c->overlap = mode;
     return KPM_OK;

@@ -724,38 +724,6 @@ void kpm_gather_release(kpm_gather *g)
     std::memset(g, 0, sizeof(*g));
 }
 
-int kpm_sweep_chain_deps(const kpm_gather *g, int32_t C, int32_t *dep)
-{
-    if (!g || !dep || C < 1 || g->n_chunks < 1 || g->n_chunks > INT32_MAX || !g->run_ptr ||
-        (g->n_runs > 0 && !g->runs))
-        return KPM_EINVAL;
-    const int64_t n = g->n_chunks, half = n / 2;
-    int32_t *d0 = dep, *d1 = dep + n;
-    // position of chunk d in a sweep visiting chunk (j + rot) mod n at j
-    auto pos1 = [&](int64_t d) { return (int32_t)(d >= half ? d - half : d + n - half); };
-    for (int64_t c = 0; c < n; c++)
-        d0[c] = d1[c] = -1;
-    for (int64_t c = 0; c < n; c++) {
-        const int32_t c0 = (int32_t)c, c1 = pos1(c);
-        for (int64_t q = g->run_ptr[c]; q < g->run_ptr[c + 1]; q++) {
-            const int64_t r0 = g->runs[2 * q], cnt = g->runs[2 * q + 1];
-            if (cnt < 1 || r0 < 0)
-                return KPM_EINVAL;
-            // rows past the last chunk (a part's halo) belong to no chunk
-            const int64_t a = r0 / C, b = std::min<int64_t>((r0 + cnt - 1) / C, n - 1);
-            for (int64_t d = a; d <= b; d++) {
-                // c reads d's rows (written by d in the previous sweep), and
-                // d's rows are read by c (overwritten by d in the next sweep)
-                d0[c] = std::max(d0[c], (int32_t)d);
-                d1[c] = std::max(d1[c], pos1(d));
-                d0[d] = std::max(d0[d], c0);
-                d1[d] = std::max(d1[d], c1);
-            }
-        }
-    }
-    return KPM_OK;
-}
-
 }  // extern "C"
 
 // ------------------------------------------------ staged entry arrays

@@ -89,18 +89,6 @@ static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte
 // off_aux, the block's W buffer (complex double: C rows of RB columns).
 // off_w != 0 (complex float): each stage also holds the chunk's old W rows
 // at off_w, copied by the producer.
-//
-// chain_sweeps > 0: a sweep chain -- that many consecutive sweeps of the
-// single problem `one` in one cooperative launch (sweep m reads
-// buf[(parity + m) & 1] and writes the other block; only sweep 0 may be the
-// initial step).  Each sweep owns chain_np items (n_tiles rounded up to a
-// multiple of the grid); sweep m's partial sums go to one.partial +
-// m * chain_stride.  prog[w] (zero at launch) counts the blocks that have
-// finished every item of wave w and before it; dep[c].x (.y) is the last
-// position, in a sweep whose chunk order is not rotated (is rotated by
-// n_tiles / 2), of a chunk that chunk c reads or that reads chunk c: sweep
-// m's producer starts chunk c once sweep m - 1 is complete up to that
-// position (kpm_sweep_chain_deps, interleaved).
 struct StagedParams {
     StagedProblem one;
     const StagedProblem *probs;
@@ -113,9 +101,6 @@ struct StagedParams {
     uint32_t bar_bytes, stage_bytes, off_val, off_lidx, off_aux, off_w;
     int32_t fp64;  // complex double (else complex float)
     int32_t half;  // every stored entry purely real or imaginary (the half-complex form)
-    int64_t chain_sweeps = 0, chain_np = 0, chain_stride = 0;
-    int *prog = nullptr;
-    const int2 *dep = nullptr;
 };
 
 // The shared-memory layout of a staged launch; false if fewer than
@@ -132,8 +117,7 @@ bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_
                    int n_probs, bool wstage, size_t max_smem, StagedLayout &out);
 bool staged_shape_supported(int T, int E, bool fp64);
 // pdl: launched as a programmatic dependent of the previous kernel in the
-// stream (its blocks set up while that kernel finishes; single problems,
-// not chains).
+// stream (its blocks set up while that kernel finishes).
 int launch_sweep_staged(const StagedParams &p, int T, int E, int grid, size_t smem, void *stream,
                         bool pdl = false);
 int staged_max_blocks_per_sm(int T, int E, int C, size_t smem, bool fp64, bool half);
@@ -265,12 +249,6 @@ struct kpm_ctx {
     int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;
     int32_t u_max = 0, l_max = 0;
-    // sweep chains: per chunk, the last position (in the unrotated and in
-    // the half-rotated chunk order) of a chunk it reads or that reads it;
-    // the per-wave counters of a chain launch
-    int2 *d_dep = nullptr;
-    int *d_prog = nullptr;
-    int64_t prog_ints = 0;
     int overlap = KPM_OVERLAP_PDL;  // kpm_set_sweep_overlap
     int *d_err = nullptr;  // device error word, KPM_DEVERR_*
     int64_t stall_after = -1;  // kpm_test_stall_staged

@@ -27,7 +27,6 @@ PREC_FP64 = 0
 PREC_FP32 = 1
 OVERLAP_NONE = 0   # kpm_set_sweep_overlap modes
 OVERLAP_PDL = 1
-OVERLAP_CHAIN = 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -119,7 +118,6 @@ _SIGS = {
     "kpm_sell_release": (None, [ctypes.POINTER(Sell)]),
     "kpm_gather_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather)]),
     "kpm_gather_release": (None, [ctypes.POINTER(Gather)]),
-    "kpm_sweep_chain_deps": (_int, [ctypes.POINTER(Gather), _i32, _vp]),
     "kpm_staged_build": (_int, [ctypes.POINTER(Sell), ctypes.POINTER(Gather), _i32,
                                 ctypes.POINTER(Staged)]),
     "kpm_staged_release": (None, [ctypes.POINTER(Staged)]),
@@ -269,8 +267,7 @@ def sell_build(csr, a, b, C=32, sigma=256, row_order=None):
 
 def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
     """The SELL layout (as sell_build) and the staged kernel's gather lists of
-    kpm_gather_build: (sell dict, {"u_max", "l_max", "lidx", "run_ptr", "runs",
-    "dep"}), dep being kpm_sweep_chain_deps' table [2][n_chunks]."""
+    kpm_gather_build: (sell dict, {"u_max", "l_max", "lidx", "run_ptr", "runs"})."""
     n, rp, col, val = _csr(csr)
     s = Sell()
     order = None if row_order is None else np.ascontiguousarray(row_order, dtype=np.int32)
@@ -289,10 +286,6 @@ def gather_build(csr, a, b, C=32, sigma=256, row_order=None):
                 "runs": np.ctypeslib.as_array(g.runs, (max(2 * g.n_runs, 1),))[:2 * g.n_runs]
                 .copy().reshape(-1, 2),
             }
-            dep = np.empty((2, g.n_chunks), dtype=np.int32)
-            _check(lib.kpm_sweep_chain_deps(ctypes.byref(g), s.C, dep.ctypes.data),
-                   "kpm_sweep_chain_deps")
-            gat["dep"] = dep
         finally:
             lib.kpm_gather_release(ctypes.byref(g))
     finally:
@@ -651,10 +644,8 @@ class Context:
         _check(lib.kpm_set_reduce_interval(self.handle, sweeps), "kpm_set_reduce_interval")
 
     def set_sweep_overlap(self, mode):
-        """kpm_set_sweep_overlap: OVERLAP_NONE (one plain launch per sweep),
-        OVERLAP_PDL (programmatic dependent launches, the default) or
-        OVERLAP_CHAIN (one cooperative launch per batch of sweeps between eta
-        reductions)."""
+        """kpm_set_sweep_overlap: OVERLAP_NONE (one plain launch per sweep)
+        or OVERLAP_PDL (programmatic dependent launches, the default)."""
         _check(lib.kpm_set_sweep_overlap(self.handle, mode), "kpm_set_sweep_overlap")
 
     def moments_device(self, M, R, seed, eta_dev, eta_imag_dev=None, stream=None):

@@ -54,7 +54,7 @@ def test_layout_autotuner(kpm, orc):
     h = ham.random_hermitian(500, 5, seed=4, empty_rows=0.1)
     a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
     best = kpm.autotune_layout(h, a, b, 32, precision=kpm.PREC_FP32, sweeps=2)
-    assert best["chunk_height"] in (8, 32, 128)
+    assert best["chunk_height"] in (8, 16, 32, 64, 128)  # kpm_autotune_layout's candidates
     assert best["sigma"] in (1, 256, 4096) and best["ms_per_sweep"] > 0
     with kpm.create(h, a, b, precision=kpm.PREC_FP32, chunk_height=best["chunk_height"],
                     sigma=best["sigma"], autotune=True) as ctx:

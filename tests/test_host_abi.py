@@ -327,119 +327,6 @@ def test_gather_lists_of_the_lattice_are_few_runs(kpm):
     assert nruns.min() >= 5
 
 
-def _chain_related(sell, C):
-    """Per chunk c, from the SELL column indices alone: the chunks c reads
-    (its own included) and the chunks that read c."""
-    n = sell["n_chunks"]
-    reads = []
-    for c in range(n):
-        e0, e1 = sell["chunk_ptr"][c], sell["chunk_ptr"][c + 1]
-        reads.append(set((sell["col"][e0:e1] // C).tolist()) | {c})
-    related = [set(r) for r in reads]
-    for c in range(n):
-        for d in reads[c]:
-            related[d].add(c)
-    return related
-
-
-def _chain_deps_brute(sell, C):
-    """dep[x][c]: the largest position, in a sweep visiting chunk
-    (j + x*(n//2)) % n at position j, of a chunk related to c."""
-    n = sell["n_chunks"]
-    related = _chain_related(sell, C)
-    dep = np.empty((2, n), dtype=np.int64)
-    for x in (0, 1):
-        rot = x * (n // 2)
-        for c in range(n):
-            dep[x, c] = max((d - rot) % n for d in related[c])
-    return dep
-
-
-@pytest.mark.parametrize("C", [8, 32])
-def test_sweep_chain_deps_match_brute_force(kpm, C):
-    h = ham.ti_hamiltonian(6, 5, 4, gamma=0.7, seed=3)
-    for m in (h, ham.random_hermitian(203, 5, seed=4, empty_rows=0.05),
-              ham.random_hermitian(400, 2, seed=9)):
-        sell, gat = kpm.gather_build(m, 0.1, 0.3, C=C, sigma=1)
-        np.testing.assert_array_equal(gat["dep"], _chain_deps_brute(sell, C))
-
-
-def _simulate_chain(dep, related, n, G, S, seed):
-    """The chain protocol of the staged kernel, run by G simulated blocks in
-    a random order that favours the blocks furthest ahead: block b takes
-    items b, b+G, ... (its k-th item lies in wave k) of S sweeps of
-    np = ceil(n/G)*G items (position j >= n idle, else chunk
-    (j + rot(m)) % n, rot = n//2 for odd m); a block counts itself into a
-    wave once it has finished every item up to it; an item of sweep m >= 1
-    starts once wave (m-1)*np/G + dep[(m-1)&1][chunk] // G is counted by
-    all G blocks.  Asserts that every item starts after the chunks related
-    to it finished the previous sweep, that the chunks of a sweep are never
-    overwritten before... every block finishing (no deadlock)."""
-    rng = np.random.default_rng(seed)
-    np_ = -(-n // G) * G
-    wps = np_ // G
-    waves = S * wps
-    count = np.zeros(waves, dtype=np.int64)
-    nxt = [0] * G
-    done = set()
-
-    def item(b, k):
-        m, j = divmod(b + k * G, np_)
-        if j >= n:
-            return m, None
-        return m, (j + (n // 2 if m & 1 else 0)) % n
-
-    while any(k < waves for k in nxt):
-        ready = []
-        for b in range(G):
-            k = nxt[b]
-            if k >= waves:
-                continue
-            m, c = item(b, k)
-            if c is None or m == 0 or count[(m - 1) * wps + dep[(m - 1) & 1][c] // G] == G:
-                ready.append(b)
-        assert ready, "no block can proceed: deadlock"
-        if rng.random() < 0.5:
-            b = max(ready, key=lambda q: nxt[q])
-        else:
-            b = ready[rng.integers(len(ready))]
-        m, c = item(b, nxt[b])
-        if c is not None:
-            for d in related[c]:
-                assert m == 0 or (m - 1, d) in done, (m, c, d)
-                assert (m + 1, d) not in done, (m, c, d)
-            done.add((m, c))
-        count[nxt[b]] += 1
-        nxt[b] += 1
-    assert len(done) == S * n
-
-
-@pytest.mark.parametrize("G", [3, 5, 8])
-def test_sweep_chain_protocol_simulation(kpm, G):
-    # lattice (local dependencies) and random (global) matrices; chunk
-    # counts that are and are not multiples of the block count
-    for m, C in ((ham.ti_hamiltonian(4, 4, 6, gamma=0.7, seed=3), 8),
-                 (ham.random_hermitian(150, 3, seed=5), 8)):
-        sell, gat = kpm.gather_build(m, 0.1, 0.3, C=C, sigma=1)
-        n = sell["n_chunks"]
-        assert n >= 2 * G
-        related = _chain_related(sell, C)
-        for seed in range(3):
-            _simulate_chain(gat["dep"], related, n, G, 4, seed)
-
-
-def test_sweep_chain_simulation_catches_short_waits(kpm):
-    # the simulation has teeth: waiting one wave short (G = 3 chunks), or
-    # for half the position, lets some item start too early
-    m = ham.ti_hamiltonian(4, 4, 6, gamma=0.7, seed=3)
-    sell, gat = kpm.gather_build(m, 0.1, 0.3, C=8, sigma=1)
-    n, related = sell["n_chunks"], _chain_related(sell, C=8)
-    for bad in (gat["dep"] - 3, gat["dep"] // 2):
-        with pytest.raises(AssertionError):
-            for seed in range(6):
-                _simulate_chain(bad, related, n, 3, 4, seed)
-
-
 def test_gather_build_rejects_small_chunks(kpm):
     h = ham.ti_hamiltonian(3, 3, 3)
     with pytest.raises(kpm.KPMError) as e:
