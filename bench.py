@@ -841,7 +841,8 @@ def large_lattice(args):
 
 def profile_sweeps(args):
     """A short program for ncu: 3 warm-up sweeps, then --kernel-launches
-    sweeps of the 64^3 lattice at R = 32 in one form, nothing else."""
+    sweeps of the 64^3 lattice at R = --profile-R (default 32) in one form,
+    nothing else."""
     import torch
     from paper_1410_5242_gb300 import build
     build.build()
@@ -850,8 +851,9 @@ def profile_sweeps(args):
     h, a, b = ti_problem(cfg)
     prec = kpm.PREC_FP64 if args.profile_sweeps == "fp64" else kpm.PREC_FP32
     ctx = kpm.create(h, a, b, precision=prec, chunk_height=32, sigma=256)
-    t = kernel_only(ctx, cfg["R"], args.kernel_launches, torch.cuda.current_stream())
-    print(json.dumps({"profile_sweeps": args.profile_sweeps, "launch": ctx.get_launch(cfg["R"]),
+    R = args.profile_R or cfg["R"]
+    t = kernel_only(ctx, R, args.kernel_launches, torch.cuda.current_stream())
+    print(json.dumps({"profile_sweeps": args.profile_sweeps, "R": R, "launch": ctx.get_launch(R),
                       "avg_launch_ms": round(t * 1e3, 4)}))
     ctx.close()
 
@@ -874,6 +876,8 @@ def main():
     ap.add_argument("--skip-large", action="store_true",
                     help="leave out the 240x240x120 lattice leg (a few minutes of host setup)")
     ap.add_argument("--ensemble-runs", type=int, default=1)
+    ap.add_argument("--profile-R", type=int, default=0,
+                    help="block width of --profile-sweeps (default: the workload's 32)")
     ap.add_argument("--profile-sweeps", choices=["fp32", "fp64"],
                     help="only run a few sweep launches of one form (for ncu captures)")
     ap.add_argument("--ensemble-only", action="store_true",

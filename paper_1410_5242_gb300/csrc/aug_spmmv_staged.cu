@@ -258,6 +258,19 @@ struct WarpEta {
             pend[2 * E + k] = __fmaf_rn(-wi, vr, pend[2 * E + k]);
         }
     }
+    // E = 4: the pending terms of columns k and k ^ 2 (the lane's two
+    // pieces) exchanged where sw is set
+    __device__ __forceinline__ void swap_pieces(int sw)
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const float a = pend[q * E + k], b = pend[q * E + k + 2];
+                pend[q * E + k] = sw ? b : a;
+                pend[q * E + k + 2] = sw ? a : b;
+            }
+    }
     // all lanes of the warp take part
     __device__ __forceinline__ void fold(int team)
     {
@@ -686,19 +699,37 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
                                           volatile int *abort_flag)
 {
     constexpr int P = 32 / T, RB = T * E;
-    grid_dependency_wait();
     constexpr int EV = Pieces<float, E>::EV, NP = Pieces<float, E>::NP;
     static_assert(EV == 2, "two complex floats per 16-byte piece");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cw = warp - 1, n_cw = (blockDim.x >> 5) - 1;
     const int tl = lane % T, team = lane / T;
+    // The order of a lane's two 16-byte pieces (E = 4).  A 16-byte shared
+    // load serves eight lanes per pass; with four lanes per row (T = 4) the
+    // two teams of a pass would read the same 64-byte half of their V rows,
+    // i.e. the same 16 banks, so odd teams take their pieces in the other
+    // order.  With two lanes per row (rows 64 bytes apart), the third and
+    // fourth team of a pass do.  The old W, the stored W and the eta terms
+    // follow the same order (swapped back before eta is summed across
+    // teams).
+    constexpr bool kSwap = NP == 2 && (T == 4 || T == 2);
+    const int sw = kSwap ? (T == 4 ? (team & 1) : ((team >> 1) & 1)) : 0;
+    // this lane's pieces within a row, in floats
+    const int pofs0 = 2 * tl * EV + 2 * sw * T * EV, pofs1 = 2 * tl * EV + 2 * (sw ^ 1) * T * EV;
+    auto po = [&](int q) { return q == 0 ? pofs0 : pofs1; };
+    WarpEta<IMAG, T, E> pe;
+    pe.clear();
+    auto fold = [&]() {
+        if constexpr (kSwap)
+            pe.swap_pieces(sw);
+        pe.fold(team);
+    };
+    grid_dependency_wait();
     const int rit = cw * P + team;  // row within the chunk
     const int C = p.C, NS = p.stages;
     const int64_t G = gridDim.x;
     const uint32_t full0 = smem_u32(smem), empty0 = full0 + 8 * NS;
     double *red = reinterpret_cast<double *>(smem + kRedOffset);
-    WarpEta<IMAG, T, E> pe;
-    pe.clear();
     int nfold = 0;
     uint64_t pa[E], pb[E];
     float4 wo[NP];  // the row's old W pieces
@@ -707,10 +738,10 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         const StagedProblem &Q = tab[q];
         const float *Wq = static_cast<const float *>(Q.buf[p.parity ^ 1]);
         const int64_t row = (gt - Q.tile0) * (int64_t)C + rit;
-        const int64_t wb = row * Q.ld + Q.col0 + tl * EV;
+        const float *wr = Wq + 2 * (row * Q.ld + Q.col0);
 #pragma unroll
         for (int q2 = 0; q2 < NP; q2++)
-            wo[q2] = __ldcg(reinterpret_cast<const float4 *>(Wq + 2 * (wb + q2 * T * EV)));
+            wo[q2] = __ldcg(reinterpret_cast<const float4 *>(wr + po(q2)));
     };
     ConsumerProblem cp;
     bool failed = false, have_w = false;
@@ -728,7 +759,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         const int64_t lt = gt - tab[cp.pi].tile0;
         if (cp.pi != cp.cur) {
             if (cp.cur >= 0 && p.dots) {
-                pe.fold(team);
+                fold();
                 nfold = 0;
                 flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
             }
@@ -757,10 +788,10 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             pa[c] = pb[c] = 0ull;
         auto entry = [&](uint32_t u, float hx, float hy) {
             const uint64_t hx2 = pack2(hx, hx), hy2 = pack2(hy, hy);
-            const float *vr = vb + (size_t)u * 2 * RB + 2 * tl * EV;
+            const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                const float4 v4 = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                const float4 v4 = *reinterpret_cast<const float4 *>(vr + po(q));
                 const uint64_t v0 = pack2(v4.x, v4.y), v1 = pack2(v4.z, v4.w);
                 pa[2 * q] = ffma2(hx2, v0, pa[2 * q]);
                 pb[2 * q] = ffma2(hy2, v0, pb[2 * q]);
@@ -775,10 +806,10 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             const int nre = meta[1];
             auto half_entry = [&](uint64_t (&acc)[E], uint32_t u, float h) {
                 const uint64_t h2 = pack2(h, h);
-                const float *vr = vb + (size_t)u * 2 * RB + 2 * tl * EV;
+                const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
-                    const float4 v4 = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                    const float4 v4 = *reinterpret_cast<const float4 *>(vr + po(q));
                     acc[2 * q] = ffma2(h2, pack2(v4.x, v4.y), acc[2 * q]);
                     acc[2 * q + 1] = ffma2(h2, pack2(v4.z, v4.w), acc[2 * q + 1]);
                 }
@@ -809,10 +840,10 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         float4 vo[NP];
         {
             const uint64_t hx2 = pack2(hox, hox), hy2 = pack2(hoy, hoy);
-            const float *vr = vb + (size_t)rit * 2 * RB + 2 * tl * EV;
+            const float *vr = vb + (size_t)rit * 2 * RB;
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                vo[q] = *reinterpret_cast<const float4 *>(vr + 2 * q * T * EV);
+                vo[q] = *reinterpret_cast<const float4 *>(vr + po(q));
                 const uint64_t v0 = pack2(vo[q].x, vo[q].y), v1 = pack2(vo[q].z, vo[q].w);
                 pa[2 * q] = ffma2(hx2, v0, pa[2 * q]);
                 pa[2 * q + 1] = ffma2(hx2, v1, pa[2 * q + 1]);
@@ -838,11 +869,10 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         } else {
             if (p.off_w) {
                 // the old W rows came with the stage
-                const float *ws = reinterpret_cast<const float *>(st + p.off_w) + (size_t)rit * 2 * RB +
-                                  2 * tl * EV;
+                const float *ws = reinterpret_cast<const float *>(st + p.off_w) + (size_t)rit * 2 * RB;
 #pragma unroll
                 for (int q = 0; q < NP; q++)
-                    wo[q] = *reinterpret_cast<const float4 *>(ws + 2 * q * T * EV);
+                    wo[q] = *reinterpret_cast<const float4 *>(ws + po(q));
             }
 #pragma unroll
             for (int q = 0; q < NP; q++) {
@@ -853,7 +883,18 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             }
         }
         const int64_t wbase = (lt * (int64_t)C + rit) * cp.ld + cp.col0 + tl * EV;
-        store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, w);
+        if constexpr (kSwap) {
+            // the pieces back in column order for the store
+            float wc[2 * E];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                wc[i] = sw ? w[i + 4] : w[i];
+                wc[i + 4] = sw ? w[i] : w[i + 4];
+            }
+            store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, wc);
+        } else {
+            store_owned<float, T, E>(static_cast<float *>(cp.W), wbase, w);
+        }
         // the next tile's old W, while this one's scalar products are added
         have_w = false;
         if (!p.init && !p.off_w && gt + G < total) {
@@ -867,7 +908,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
                 pe.add(2 * q + 1, w[4 * q + 2], w[4 * q + 3], vo[q].z, vo[q].w);
             }
             if (++nfold == kEtaFold) {
-                pe.fold(team);
+                fold();
                 nfold = 0;
             }
         }
@@ -878,7 +919,7 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
     if (!p.dots)
         return;
     if (cp.cur >= 0) {
-        pe.fold(team);
+        fold();
         flush_eta32<T, E, IMAG>(pe, red, tab[cp.cur], cp.slot, cw, n_cw);
     } else if (p.probs == nullptr) {
         // a single problem's partials are read for every block: a block
