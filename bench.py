@@ -571,9 +571,19 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
         a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
         hs.append((h, a, b))
     t_build = time.perf_counter() - t0
+    # --ensemble-tuned: the layouts and launch shapes an earlier run chose
+    # (its JSON line), for a run under a profiler, whose timings would steer
+    # the autotuners elsewhere
+    fixed = None
+    if getattr(args, "ensemble_tuned", None):
+        fixed = json.loads(open(args.ensemble_tuned).read().strip().splitlines()[-1])
     t0 = time.perf_counter()
     layout = {}
     for R in sorted(set(p["R"] for p in probs)):
+        if fixed:
+            L = fixed["tuned_layout"][str(R)]
+            layout[R] = {"chunk_height": L["C"], "sigma": L["sigma"]}
+            continue
         big = max((i for i, p in enumerate(probs) if p["R"] == R), key=lambda i: hs[i][0]["n"])
         h, a, b = hs[big]
         layout[R] = kpm.autotune_layout(h, a, b, R, precision=kpm.PREC_FP32, sweeps=3,
@@ -597,8 +607,12 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
     for R in sorted(set(Rs)):
         members = [c for c, r in zip(ctxs, Rs) if r == R]
         rep = max(members, key=lambda c: c.n)
-        rep.autotune(R, sweeps=3, stream=stream)
-        shape = rep.get_launch(R)
+        if fixed:
+            shape = fixed["tuned_launch"][str(R)]
+            rep = None
+        else:
+            rep.autotune(R, sweeps=3, stream=stream)
+            shape = rep.get_launch(R)
         for c in members:
             if c is not rep:
                 c.set_launch(R, shape["lanes_per_row"], shape["cols_per_lane"],
@@ -621,6 +635,7 @@ def ensemble_rate(kpm, dev, args, stream, world, hbm_peak):
            "ms_per_run": round(t * 1e3, 1), "runs": args.ensemble_runs, "warmup": 1,
            "algorithmic_bytes_per_run": info["algorithmic_bytes"], "sweeps": info["sweeps"],
            "steps": info["steps"], "graph_kernel_nodes": info["kernel_launches"],
+           "classes": info["classes"], "staged_classes": info["staged_classes"],
            "setup_s": round(t_setup, 1), "autotune_s": round(t_tune, 1), "tuned_launch": tuned,
            "layout_autotune_s": round(t_layout, 1),
            "tuned_layout": {str(R): {"C": L["chunk_height"], "sigma": L["sigma"]}
@@ -897,6 +912,9 @@ def main():
                     help="only run a few sweep launches of one form (for ncu captures)")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="only the 64-problem ensemble (one warm-up and --ensemble-runs timed runs)")
+    ap.add_argument("--ensemble-tuned", default=None,
+                    help="with --ensemble-only: take the layouts and launch shapes from an "
+                         "earlier --ensemble-only JSON line instead of autotuning")
     ap.add_argument("--large", action="store_true",
                     help="only the 240x240x120 lattice: the sweep kernel alone in both forms")
     args = ap.parse_args()

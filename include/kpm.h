@@ -417,8 +417,9 @@ typedef struct kpm_batch kpm_batch;
 typedef struct kpm_batch_info {
     int32_t count;             /* problems */
     int32_t steps;             /* sweep steps = max M/2 */
-    int32_t grid;              /* blocks of each batched sweep launch */
-    int32_t reserved;
+    int32_t grid;              /* blocks of each batched sweep launch (register path) */
+    int16_t classes;           /* block-width classes */
+    int16_t staged_classes;    /* of which run the staged kernel */
     int64_t kernel_launches;   /* kernel nodes in the graph */
     int64_t sweeps;            /* sum over problems of M/2 */
     double algorithmic_bytes;  /* Eq. 4 bytes of one run, summed over problems */

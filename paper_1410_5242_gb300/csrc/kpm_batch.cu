@@ -558,6 +558,10 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     b->info.kernel_launches = launches;
     b->info.algorithmic_bytes = bytes;
     b->info.grid = b->grid;
+    b->info.classes = (int16_t)b->staged.size();
+    b->info.staged_classes = 0;
+    for (const StagedClass &sc : b->staged)
+        b->info.staged_classes += sc.on ? 1 : 0;
     *out = b;
     return KPM_OK;
 }

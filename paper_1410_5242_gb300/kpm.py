@@ -73,7 +73,8 @@ class Info(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("steps", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("classes", ctypes.c_int16), ("staged_classes", ctypes.c_int16),
+                ("kernel_launches", ctypes.c_int64),
                 ("sweeps", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double)]
 
 

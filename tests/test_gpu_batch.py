@@ -184,6 +184,11 @@ def test_batch_classes_take_their_first_problems_launch_shape(kpm, orc):
     # each class is the one with the largest M
     ctxs[0][0].set_launch(16, 4, 4, 128, tile_groups=1, stages=0)
     ctxs[2][0].set_launch(32, 8, 4, 128, stages=1)
+    b = kpm.Batch([c for c, *_ in ctxs], [p[1] for p in probs], [p[2] for p in probs],
+                  [p[3] for p in probs])
+    info = b.info()
+    b.close()
+    assert info["classes"] == 2 and info["staged_classes"] == 1
     etas = kpm.moments_batch([c for c, *_ in ctxs], [p[1] for p in probs], [p[2] for p in probs],
                              [p[3] for p in probs])
     for (ctx, h, a, b), (_, M, R, seed), eta in zip(ctxs, probs, etas):
