@@ -588,6 +588,25 @@ int kpm_set_reduce_interval(kpm_ctx *ctx, int32_t sweeps);
  *                     touch the vector blocks or the eta partials.  Results
  *                     are those of plain launches, bit for bit.
  * KPM_EINVAL for a NULL context or another mode. */
+/* Checked build.  Compiling the library with -DKPM_CHECK (build.py
+ * build(check=True): _build_check/libkpm_check.so, which the Python binding
+ * loads when the environment has KPM_CHECK=1) adds bounds checks to every
+ * access of the staged sweep that depends on the context's device arrays:
+ * each chunk record's entry range, run rows, overflow runs, gathered-row
+ * count and W rows against the arrays' extents and the stage's areas
+ * (checked by the producer warp before it copies anything), and every local
+ * index against the chunk's gathered rows (checked by the consumer warps).
+ * A failed check records KPM_DEVERR_RANGE in the device error word, stops
+ * the launch's blocks, and kpm_check_device_error returns KPM_EINVAL.
+ * kpm_checked_build returns 1 in a checked build, 0 otherwise.
+ * kpm_test_corrupt_record (test hook, checked builds only, else
+ * KPM_EUNSUPPORTED) overwrites word `word` (0..31) of chunk `chunk`'s device
+ * record with (x, y): word 0 = first staged entry (low, high 32 bits), word
+ * 1 = (staged length | real-region length << 16, run count), word 2 =
+ * overflow offset, words 3..31 = inline runs (first row, row count). */
+int kpm_checked_build(void);
+int kpm_test_corrupt_record(kpm_ctx *ctx, int64_t chunk, int32_t word, int32_t x, int32_t y);
+
 #define KPM_OVERLAP_NONE 0
 #define KPM_OVERLAP_PDL 1
 int kpm_set_sweep_overlap(kpm_ctx *ctx, int32_t mode);

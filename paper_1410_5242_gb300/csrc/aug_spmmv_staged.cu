@@ -439,6 +439,28 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
         const int nruns = __shfl_sync(0xffffffffu, word.y, 1);
         const int n_inline = min(nruns, KPM_REC_INLINE_RUNS);
         const bool has_run = lane >= 3 && lane - 3 < n_inline;
+#ifdef KPM_CHECK
+        // checked build: the chunk's record must keep every copy inside the
+        // arrays it reads and the stage areas it fills; else the launch stops
+        // with KPM_DEVERR_RANGE before any copy
+        const StagedProblem &PC = tab[pi];
+        bool bad = len < 1 || nre < 0 || nre > len || nruns < 1 ||
+                   (uint64_t)p.C * len * VSIZE > p.off_lidx - p.off_val ||
+                   (uint64_t)p.C * len * 2 > (p.off_w ? p.off_w : p.stage_bytes) - p.off_lidx ||
+                   e0 < 0 || e0 + (int64_t)p.C * len > PC.entries ||
+                   (nruns > KPM_REC_INLINE_RUNS &&
+                    (ovf0 < 0 || ovf0 + (nruns - KPM_REC_INLINE_RUNS) > PC.n_ovf)) ||
+                   (lt + 1) * p.C > PC.rows;
+        if (has_run && (word.x < 0 || word.y < 0 || (int64_t)word.x + word.y > PC.rows))
+            bad = true;
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0 && p.err) {
+                atomicExch(p.err, KPM_DEVERR_RANGE);
+                *abort_flag = 1;
+            }
+            break;
+        }
+#endif
         const int count = has_run ? word.y : 0;
         const int incl = warp_incl_scan(count, lane);
         uint32_t total_rows = (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
@@ -446,8 +468,22 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             const int2 r = g + lane < nruns
                                ? __ldg(ovfp + ovf0 + (g - KPM_REC_INLINE_RUNS) + lane)
                                : make_int2(0, 0);
+#ifdef KPM_CHECK
+            if (r.x < 0 || r.y < 0 || (int64_t)r.x + r.y > PC.rows)
+                bad = true;
+#endif
             total_rows += (uint32_t)__shfl_sync(0xffffffffu, warp_incl_scan(r.y, lane), 31);
         }
+#ifdef KPM_CHECK
+        if (__any_sync(0xffffffffu, bad || total_rows < (uint32_t)p.C ||
+                                        total_rows > p.off_val / row_bytes)) {
+            if (lane == 0 && p.err) {
+                atomicExch(p.err, KPM_DEVERR_RANGE);
+                *abort_flag = 1;
+            }
+            break;
+        }
+#endif
 
         const uint32_t full = full0 + 8 * s, empty = empty0 + 8 * s;
         if (k >= NS) {
@@ -467,6 +503,9 @@ __device__ __forceinline__ int64_t produce(const StagedParams &p, unsigned char 
             volatile int *meta = reinterpret_cast<volatile int *>(smem + kMetaOffset + 16 * s);
             meta[0] = len;
             meta[1] = nre;
+#ifdef KPM_CHECK
+            meta[2] = (int)total_rows;
+#endif
             mbar_arrive_expect_tx(full, bytes);
         }
         __syncwarp();
@@ -783,10 +822,26 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
         const int len = meta[0];
         const float *vb = reinterpret_cast<const float *>(st);
         const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
+#ifdef KPM_CHECK
+        // checked build: a local index past the chunk's gathered rows reads
+        // row 0 instead and stops the launch with KPM_DEVERR_RANGE
+        const uint32_t ntot = (uint32_t)meta[2];
+        auto check_u = [&](uint32_t &u) {
+            if (u >= ntot) {
+                if (p.err)
+                    atomicExch(p.err, KPM_DEVERR_RANGE);
+                *abort_flag = 1;
+                u = 0;
+            }
+        };
+#endif
 #pragma unroll
         for (int c = 0; c < E; c++)
             pa[c] = pb[c] = 0ull;
         auto entry = [&](uint32_t u, float hx, float hy) {
+#ifdef KPM_CHECK
+            check_u(u);
+#endif
             const uint64_t hx2 = pack2(hx, hx), hy2 = pack2(hy, hy);
             const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
@@ -805,6 +860,9 @@ __device__ __forceinline__ void consume32(const StagedParams &p, unsigned char *
             const float *hv = reinterpret_cast<const float *>(st + p.off_val);
             const int nre = meta[1];
             auto half_entry = [&](uint64_t (&acc)[E], uint32_t u, float h) {
+#ifdef KPM_CHECK
+                check_u(u);
+#endif
                 const uint64_t h2 = pack2(h, h);
                 const float *vr = vb + (size_t)u * 2 * RB;
 #pragma unroll
@@ -991,6 +1049,11 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
         const unsigned char *st = smem + p.bar_bytes + (size_t)s * p.stage_bytes;
         const int len = *reinterpret_cast<const volatile int *>(smem + kMetaOffset + 16 * s);
         const double *vb = reinterpret_cast<const double *>(st);
+#ifdef KPM_CHECK
+        // checked build: as in consume32
+        const uint32_t ntot = (uint32_t)(reinterpret_cast<const volatile int *>(
+            smem + kMetaOffset + 16 * s))[2];
+#endif
         const double2 *vals = reinterpret_cast<const double2 *>(st + p.off_val);
         const uint16_t *lid = reinterpret_cast<const uint16_t *>(st + p.off_lidx);
         double *Wp = static_cast<double *>(cp.W);
@@ -1012,6 +1075,14 @@ __device__ __forceinline__ void consume64(const StagedParams &p, unsigned char *
         for (int q = 0; q < 2 * E; q++)
             a[q] = 0.0;
         auto entry = [&](uint32_t l, const double2 h) {
+#ifdef KPM_CHECK
+            if ((HALF ? (l & 0x7fffu) : l) >= ntot) {
+                if (p.err)
+                    atomicExch(p.err, KPM_DEVERR_RANGE);
+                *abort_flag = 1;
+                l = HALF ? (l & 0x8000u) : 0u;
+            }
+#endif
             if constexpr (HALF) {
                 const int sw = (int)(l >> 15);
                 const double *vr = vb + (size_t)(l & 0x7fffu) * 2 * RB + 2 * tl;

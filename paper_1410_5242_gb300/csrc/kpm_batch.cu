@@ -444,6 +444,9 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             sp.qs = slots;
             sp.ld = bp.ld;
             sp.col0 = 0;
+            sp.rows = c->n_pad + c->n_halo;
+            sp.entries = c->n_staged;
+            sp.n_ovf = c->n_ovf;
         }
         prefix.push_back(prefix.back() + n_tiles);
         const double mat = (double)c->nnz * (sd + 4);

@@ -487,6 +487,9 @@ int staged_params(const kpm_ctx *c, const ColumnBlock &cb, const SweepParams &p,
     q.one.qs = 1;
     q.one.ld = p.ld;
     q.one.col0 = p.col0;
+    q.one.rows = c->n_pad + c->n_halo;
+    q.one.entries = c->n_staged;
+    q.one.n_ovf = c->n_ovf;
     q.probs = nullptr;
     q.n_probs = 1;
     q.parity = 0;
@@ -870,6 +873,8 @@ int kpm_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const doub
                                            cudaMemcpyHostToDevice) == cudaSuccess);
             c->u_max = g.u_max;
             c->l_max = sg.l_max;
+            c->n_staged = sg.n_stored;
+            c->n_ovf = (int64_t)ovf.size();
             const int64_t n_staged = sg.n_stored;
             kpm_staged_release(&sg);
             kpm_gather_release(&g);
@@ -1108,6 +1113,34 @@ int kpm_set_reduce_interval(kpm_ctx *c, int32_t sweeps)
         return KPM_EINVAL;
     c->reduce_interval = sweeps;
     return KPM_OK;
+}
+
+int kpm_checked_build(void)
+{
+#ifdef KPM_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int kpm_test_corrupt_record(kpm_ctx *c, int64_t chunk, int32_t word, int32_t x, int32_t y)
+{
+#ifdef KPM_CHECK
+    if (!c || !c->d_rec || chunk < 0 || chunk >= c->n_chunks || word < 0 || word >= KPM_REC_WORDS)
+        return KPM_EINVAL;
+    DeviceGuard guard(c->device);
+    const int2 v = make_int2(x, y);
+    return cuda_status(cudaMemcpy(c->d_rec + chunk * KPM_REC_WORDS + word, &v, sizeof(v),
+                                  cudaMemcpyHostToDevice));
+#else
+    (void)c;
+    (void)chunk;
+    (void)word;
+    (void)x;
+    (void)y;
+    return KPM_EUNSUPPORTED;
+#endif
 }
 
 int kpm_set_sweep_overlap(kpm_ctx *c, int32_t mode)

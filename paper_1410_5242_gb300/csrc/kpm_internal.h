@@ -75,6 +75,9 @@ struct StagedProblem {
     int64_t tile0, n_tiles;
     int64_t ps, qs;
     int32_t ld, col0;
+    // extents for the bounds checks of a KPM_CHECK build: rows of each
+    // vector block, staged entries, overflow runs
+    int64_t rows, entries, n_ovf;
 };
 
 static_assert(sizeof(StagedProblem) % 8 == 0, "copied to shared memory in 8-byte words");
@@ -248,6 +251,7 @@ struct kpm_ctx {
     uint16_t *d_lidx = nullptr;  // staged local indices (kpm_staged)
     int2 *d_rec = nullptr;       // [n_chunks][KPM_REC_WORDS]
     int2 *d_ovf = nullptr;
+    int64_t n_staged = 0, n_ovf = 0;  // entries of the staged arrays, overflow runs
     int32_t u_max = 0, l_max = 0;
     int overlap = KPM_OVERLAP_PDL;  // kpm_set_sweep_overlap
     int *d_err = nullptr;  // device error word, KPM_DEVERR_*

@@ -13,7 +13,11 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libkpm.so")
+# KPM_CHECK=1 in the environment: the checked build (bounds checks in the
+# staged sweep, include/kpm.h), built by build.build(check=True)
+CHECKED = os.environ.get("KPM_CHECK") == "1"
+LIB_PATH = os.path.join(_PKG, "_build_check", "libkpm_check.so") if CHECKED else \
+    os.path.join(_PKG, "_build", "libkpm.so")
 
 KPM_OK = 0
 KPM_EINVAL = -1
@@ -161,6 +165,8 @@ _SIGS = {
     "kpm_sweep_variant": (_int, [_vp, _i32, _vp, _vp, _i32, _vp]),
     "kpm_set_reduce_interval": (_int, [_vp, _i32]),
     "kpm_set_sweep_overlap": (_int, [_vp, _i32]),
+    "kpm_checked_build": (_int, []),
+    "kpm_test_corrupt_record": (_int, [_vp, _i64, _i32, _i32, _i32]),
     "kpm_naive_create": (_int, [_i64, _pi64, _pi32, _pd, _d, _d, _i32, ctypes.POINTER(_vp)]),
     "kpm_naive_moments": (_int, [_vp, _i32, _i32, _u64, _vp, _vp]),
     "kpm_naive_destroy": (None, [_vp]),
@@ -169,8 +175,9 @@ _SIGS = {
 }
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libkpm.so is not built (%s); run paper_1410_5242_gb300.build.build() "
-                      "or __graft_entry__.build() first" % LIB_PATH)
+    raise ImportError("%s is not built; run paper_1410_5242_gb300.build.build(%s) "
+                      "or __graft_entry__.build() first"
+                      % (LIB_PATH, "check=True" if CHECKED else ""))
 lib = ctypes.CDLL(LIB_PATH)
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -643,6 +650,11 @@ class Context:
 
     def set_reduce_interval(self, sweeps):
         _check(lib.kpm_set_reduce_interval(self.handle, sweeps), "kpm_set_reduce_interval")
+
+    def test_corrupt_record(self, chunk, word, x, y):
+        """kpm_test_corrupt_record (checked builds only)."""
+        _check(lib.kpm_test_corrupt_record(self.handle, chunk, word, x, y),
+               "kpm_test_corrupt_record")
 
     def set_sweep_overlap(self, mode):
         """kpm_set_sweep_overlap: OVERLAP_NONE (one plain launch per sweep)
