@@ -57,11 +57,16 @@ def test_staged_is_the_complex_float_default(kpm):
             l = ctx.get_launch(R)
             assert l["stages"] >= 2 and l["cols_per_lane"] == 4, (R, l)
             assert l["block_threads"] == 32 + 32 * (R // 4)
+        for R in (2, 4):  # the whole row in one lane
+            l = ctx.get_launch(R)
+            assert l["stages"] >= 2 and l["lanes_per_row"] == 1 and l["cols_per_lane"] == R, l
+            assert l["block_threads"] == 32 + 32
+        assert ctx.get_launch(1)["stages"] == 0  # width 1: register path
     with kpm.create(h, a, b, chunk_height=4) as ctx:
         assert ctx.get_launch(32)["stages"] == 0  # no gather lists: register path
 
 
-@pytest.mark.parametrize("R", [8, 16, 24, 32, 64, 100])
+@pytest.mark.parametrize("R", [2, 4, 7, 8, 16, 24, 32, 64, 100])
 @pytest.mark.parametrize("order", ["lattice", "cube"])
 def test_staged_sweep_matches_register_path(kpm, R, order):
     dims = (8, 6, 5)
@@ -80,7 +85,9 @@ def test_staged_sweep_matches_register_path(kpm, R, order):
                     for w in widths:
                         if w >= 8:
                             ctx.set_launch(w, w // 4, 4, 128, stages=stages)
-                        else:  # narrow blocks always run the register path
+                        elif w >= 2:  # the whole row in one lane
+                            ctx.set_launch(w, 1, w, 128, stages=stages)
+                        else:  # width 1 always runs the register path
                             ctx.set_launch(w, 1, w, 128)
                 except kpm.KPMError as e:
                     # more stages of 64-wide rows than shared memory holds
@@ -100,7 +107,7 @@ def test_staged_sweep_matches_register_path(kpm, R, order):
 
 
 @pytest.mark.parametrize("stages", [2, 3, 4])
-@pytest.mark.parametrize("R", [8, 32, 64])
+@pytest.mark.parametrize("R", [2, 4, 8, 32, 64])
 def test_staged_moments_match_oracle(kpm, orc, stages, R):
     h = ham.ti_hamiltonian(6, 7, 5, gamma=1.5, seed=4)
     a, b = scaled(h, kpm)
@@ -109,7 +116,10 @@ def test_staged_moments_match_oracle(kpm, orc, stages, R):
     ref, _ = orc.moments(h, a, b, M, 9, cols)
     with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
         try:
-            ctx.set_launch(R, R // 4, 4, 128, stages=stages)
+            if R >= 8:
+                ctx.set_launch(R, R // 4, 4, 128, stages=stages)
+            else:
+                ctx.set_launch(R, 1, R, 128, stages=stages)
         except kpm.KPMError as e:
             assert e.status == kpm.KPM_EUNSUPPORTED and stages > 2
             pytest.skip("%d stages of %d-wide rows do not fit in shared memory" % (stages, R))
