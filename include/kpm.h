@@ -631,9 +631,9 @@ void kpm_naive_destroy(kpm_naive *nv);
  * the kernel (stages), as chosen by the defaults or the autotuner.  The
  * default is the staged kernel with two stages wherever the context has
  * gather lists (C >= 8), the width is 2..64 (complex float: 4 columns per
- * lane, at widths 2 and 4 the whole row in one lane) or 8..32 (complex
- * double, 2 columns per lane) and two stages fit in shared memory;
- * everything else (width 1, complex double below 8) runs the register-path
+ * lane, at widths 2 and 4 the whole row in one lane) or 1..32 (complex
+ * double: 2 columns per lane, 1 at width 1) and two stages fit in shared
+ * memory; everything else (complex float width 1) runs the register-path
  * kernel.  Complex
  * double contexts with gather lists split R into blocks of at most 32
  * columns (kpm_get_max_block_width).  For a matrix whose every stored
@@ -653,7 +653,8 @@ typedef struct kpm_launch {
                         `stages` shared-memory stages with bulk copies, and C*T/32
                         consumer warps compute from there; block_threads = 32 + C*T;
                         complex float: cols_per_lane 4 (width 4..64) or 2 (width
-                        2..32); complex double: cols_per_lane 2 (width 8..32) */
+                        2..32); complex double: cols_per_lane 2 (width 2..32) or 1
+                        (width 1) */
 } kpm_launch;
 int kpm_get_launch(const kpm_ctx *ctx, int32_t R, kpm_launch *out);
 /* Forces a launch variant for width R (KPM_EUNSUPPORTED if not built). */

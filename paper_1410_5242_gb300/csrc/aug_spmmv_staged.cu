@@ -1214,11 +1214,11 @@ __global__ void __launch_bounds__(KPM_STAGED_MAX_THREADS, StagedMinBlocks<Real, 
 // (T, E) shapes of the staged kernel.  Complex float: 4 columns per lane
 // as two 16-byte pieces (widths 4..64), or 2 as one piece (widths 2..32:
 // twice the lanes per row, for more warps per SM); at widths 2 and 4 one
-// lane holds a whole row.  Complex double: 2
-// columns per lane as two pieces (widths 8..32; a 64-wide stage would not
-// fit twice), each with and without the half-complex shortcut.
+// lane holds a whole row.  Complex double: 2 columns per lane as two
+// pieces (widths 2..32; a 64-wide stage would not fit twice), or 1 (width
+// 1), each with and without the half-complex shortcut.
 #define KPM_STAGED_SHAPES(X) X(1, 4) X(2, 4) X(4, 4) X(8, 4) X(16, 4) X(1, 2) X(4, 2) X(8, 2) X(16, 2)
-#define KPM_STAGED_SHAPES64(X) X(4, 2) X(8, 2) X(16, 2)
+#define KPM_STAGED_SHAPES64(X) X(1, 1) X(1, 2) X(2, 2) X(4, 2) X(8, 2) X(16, 2)
 
 bool staged_shape_supported(int T, int E, bool fp64)
 {

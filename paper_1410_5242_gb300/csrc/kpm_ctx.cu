@@ -321,11 +321,12 @@ LaunchShape default_shape(const kpm_ctx *c, int RB)
     // at widths 16..64 on the 64^3 lattice, a third stage costs the second
     // block), at widths 2 and 4 the whole row in one lane (93 % of HBM at
     // width 4 on the 64^3 lattice against 50 % on the register path);
-    // complex double 2 columns per lane at widths 8..32 (one block per SM
-    // at width 32; measured faster than the register path at widths 8..32
-    // on the 64^3 lattice, with and without the half-complex form).
-    const int E = fp64 ? 2 : std::min(RB, 4);
-    if (c->gather_ok && RB >= (fp64 ? 8 : 2) && RB % E == 0 &&
+    // complex double 2 columns per lane at widths 2..32 and 1 at width 1
+    // (one block per SM at width 32; measured faster than the register path
+    // at every width on the 64^3 lattice, 2.2x at widths 1..4, with and
+    // without the half-complex form).
+    const int E = fp64 ? std::min(RB, 2) : std::min(RB, 4);
+    if (c->gather_ok && RB >= (fp64 ? 1 : 2) && RB % E == 0 &&
         staged_shape_supported(RB / E, E, fp64)) {
         StagedLayout L;
         if (staged_layout(c->C, RB / E, RB, fp64 ? 16 : 8, staged_value_bytes(fp64, c->half_ok),

@@ -87,7 +87,9 @@ def test_staged_is_the_complex_double_default(kpm):
             assert l["stages"] == 2 and l["cols_per_lane"] == 2, (R, l)
             assert l["block_threads"] == 32 + 32 * (R // 2)
         assert ctx.max_block_width() == 32
-        assert ctx.get_launch(4)["stages"] == 0  # narrow blocks: register path
+        for R, T, E in ((1, 1, 1), (2, 1, 2), (4, 2, 2)):  # narrow blocks
+            l = ctx.get_launch(R)
+            assert (l["stages"], l["lanes_per_row"], l["cols_per_lane"]) == (2, T, E), (R, l)
     g = ham.random_hermitian(300, 7, seed=3)
     a, b = scaled(g, kpm)
     with kpm.create(g, a, b) as ctx:
@@ -99,7 +101,7 @@ def test_staged_is_the_complex_double_default(kpm):
         assert ctx.get_launch(32)["stages"] == 0
 
 
-@pytest.mark.parametrize("R", [8, 16, 24, 32, 64, 100])
+@pytest.mark.parametrize("R", [1, 2, 4, 7, 8, 16, 24, 32, 64, 100])
 @pytest.mark.parametrize("form", ["half", "general"])
 def test_staged_fp64_sweep_matches_register_path(kpm, R, form):
     if form == "half":
@@ -123,9 +125,10 @@ def test_staged_fp64_sweep_matches_register_path(kpm, R, form):
             for stages in (0, 1, 2):
                 try:
                     for w in set(plan):
-                        if w >= 8 and stages:
-                            ctx.set_launch(w, w // 2, 2, 128, stages=stages)
-                        elif w >= 8:
+                        e = min(w, 2)
+                        if stages:
+                            ctx.set_launch(w, w // e, e, 128, stages=stages)
+                        else:
                             ctx.set_launch(w, w, 1, 256)  # register path
                 except kpm.KPMError as e:
                     # two stages of the random matrix's 32-wide gather lists
@@ -146,7 +149,7 @@ def test_staged_fp64_sweep_matches_register_path(kpm, R, form):
             assert first is not None
 
 
-@pytest.mark.parametrize("R", [8, 32, 64])
+@pytest.mark.parametrize("R", [1, 4, 8, 32, 64])
 @pytest.mark.parametrize("form", ["half", "general"])
 def test_staged_fp64_moments_match_oracle(kpm, orc, R, form):
     h = ham.ti_hamiltonian(6, 7, 5, gamma=1.5, seed=4)
@@ -154,7 +157,7 @@ def test_staged_fp64_moments_match_oracle(kpm, orc, R, form):
         h = peierls(h)
     a, b = scaled(h, kpm)
     M = 64
-    cols = [0, R // 2, R - 1]
+    cols = sorted({0, R // 2, R - 1})
     ref, _ = orc.moments(h, a, b, M, 9, cols)
     with kpm.create(h, a, b) as ctx:
         assert ctx.info()["half_complex"] == (1 if form == "half" else 0)
