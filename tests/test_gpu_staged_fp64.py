@@ -1,6 +1,7 @@
 """GPU tests of the staged sweep kernel in complex double (include/kpm.h,
-kpm_launch.stages): the default for widths 8..32 wherever the context has
-gather lists, with R split into blocks of at most 32 columns.  Two forms: the
+kpm_launch.stages): the default for every width up to 32 wherever the context
+has gather lists (two columns per lane, one at width 1), with R split into
+blocks of at most 32 columns.  Two forms: the
 general one (four FMAs per entry and column) and the half-complex one for
 matrices whose every stored entry is purely real or purely imaginary, such
 as the topological insulator of Sec. "Application Scenario" (two FMAs: the
