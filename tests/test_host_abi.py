@@ -36,6 +36,24 @@ def test_library_exports_every_declared_function(kpm):
     assert not missing, missing
 
 
+def test_checked_build_compiles_and_exports_every_declared_function(kpm):
+    # the KPM_CHECK build (bounds checks in the staged sweep) is a second
+    # library; without a GPU only its exports and its self-report are checked
+    from paper_1410_5242_gb300 import build
+    path = build.build(check=True)
+    assert path.endswith("libkpm_check.so") and path != kpm.LIB_PATH
+    so = ctypes.CDLL(path)
+    missing = [n for n in header_functions() if not hasattr(so, n)]
+    assert not missing, missing
+    so.kpm_checked_build.restype = ctypes.c_int
+    assert so.kpm_checked_build() == 1 and kpm.lib.kpm_checked_build() == 0
+    so.kpm_test_corrupt_record.restype = ctypes.c_int
+    so.kpm_test_corrupt_record.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32]
+    assert so.kpm_test_corrupt_record(None, 0, 0, 0, 0) == kpm.KPM_EINVAL
+    assert kpm.lib.kpm_test_corrupt_record(None, 0, 0, 0, 0) == kpm.KPM_EUNSUPPORTED
+
+
 def test_gershgorin_and_scale_match_oracle(kpm, orc):
     for h in (ham.ti_hamiltonian(5, 4, 3, gamma=1.3, seed=2),
               ham.random_hermitian(90, 6, seed=1, empty_rows=0.1)):
