@@ -370,6 +370,14 @@ def test_local_and_plane_wave_calls_reject_missing_arguments(kpm):
                                       None) == kpm.KPM_EINVAL
 
 
+def test_sweep_overlap_and_reduce_interval_reject_bad_arguments(kpm):
+    lib = kpm.lib
+    for mode in (kpm.OVERLAP_NONE, kpm.OVERLAP_PDL, -1, 2):
+        assert lib.kpm_set_sweep_overlap(None, mode) == kpm.KPM_EINVAL
+    assert (kpm.OVERLAP_NONE, kpm.OVERLAP_PDL) == (0, 1)
+    assert lib.kpm_set_reduce_interval(None, 1) == kpm.KPM_EINVAL
+
+
 @pytest.mark.parametrize("C,sigma", [(32, 256), (8, 64)])
 def test_conversions_do_not_depend_on_the_host_thread_count(kpm, monkeypatch, C, sigma):
     """kpm_sell_build and kpm_gather_build split rows, sorting windows and
