@@ -58,3 +58,15 @@ def test_programmatic_launches_match_plain_launches(kpm, prec):
             out[mode] = (eta, e.cpu().numpy(), ctx.block_download(R, V))
     for x, y in zip(out[kpm.OVERLAP_NONE], out[kpm.OVERLAP_PDL]):
         np.testing.assert_array_equal(x, y)
+
+
+def test_sweep_overlap_rejects_unknown_modes(kpm):
+    h = ham.ti_hamiltonian(4, 4, 4, gamma=0.5, seed=0)
+    a, b = scaled(h, kpm)
+    with kpm.create(h, a, b, precision=kpm.PREC_FP32) as ctx:
+        for mode in (-1, 2):
+            with pytest.raises(kpm.KPMError) as e:
+                ctx.set_sweep_overlap(mode)
+            assert e.value.status == kpm.KPM_EINVAL
+        ctx.set_sweep_overlap(kpm.OVERLAP_NONE)
+        ctx.set_sweep_overlap(kpm.OVERLAP_PDL)
