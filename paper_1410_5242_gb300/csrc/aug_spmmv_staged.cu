@@ -1265,14 +1265,21 @@ bool staged_layout(int C, int T, int RB, int csize, int vsize, int u_max, int l_
     return o.smem <= max_smem && o.stage_bytes < (1u << 20);
 }
 
+// Host launch helpers: occupancy queries and launches, no device code.
+
 namespace {
 
+// Blocks per SM at smem bytes of dynamic shared memory.  The query needs the
+// kernel's dynamic shared-memory limit at least smem; it only ever raises
+// the limit, through the same per-device record the launches use, so that a
+// query for a small layout never lowers it under a larger layout that an
+// earlier launch or a captured graph of the same instantiation relies on.
 template <typename Real, int T, int E, bool IMAG, bool HALF>
 int occupancy_of(int threads, size_t smem)
 {
     int nb = 0;
-    if (cudaFuncSetAttribute(aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (ensure_max_dynamic_smem((const void *)aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>,
+                                smem) != KPM_OK ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &nb, aug_spmmv_staged_kernel<Real, T, E, IMAG, HALF>, threads, smem) != cudaSuccess) {
         cudaGetLastError();

@@ -196,3 +196,34 @@ def test_batch_classes_take_their_first_problems_launch_shape(kpm, orc):
         assert np.abs(kpm.eta_to_mu(eta[[0, R - 1]]) - orc.eta_to_mu(ref)).max() <= 1e-5
     for c, *_ in ctxs:
         c.close()
+
+
+def test_smaller_layout_between_batch_launches(kpm):
+    """A batch's captured graph keeps launching after another context has
+    planned and run the same staged instantiation with a smaller shared-
+    memory layout: the occupancy queries and launches only ever raise the
+    kernel's dynamic shared-memory limit, so the graph's larger stages stay
+    allowed and its moments do not change."""
+    big = []
+    for h in (ham.ti_hamiltonian(10, 10, 8, gamma=1.0, seed=21),
+              ham.ti_hamiltonian(8, 8, 6, gamma=0.5, seed=22)):
+        a, b = kpm.scale_from_bounds(*kpm.gershgorin(h), 0.01)
+        big.append(kpm.create(h, a, b, precision=kpm.PREC_FP32, chunk_height=32))
+    h3 = ham.ti_hamiltonian(6, 6, 6, gamma=2.0, seed=23)
+    a3, b3 = kpm.scale_from_bounds(*kpm.gershgorin(h3), 0.01)
+    with kpm.Batch(big, [48, 32], [32, 32], [5, 6]) as batch, \
+            kpm.create(h3, a3, b3, precision=kpm.PREC_FP32, chunk_height=8) as small:
+        assert batch.info()["staged_classes"] == 1
+        batch.launch()
+        first = [batch.eta(0), batch.eta(1)]
+        ls, lb = small.get_launch(32), big[0].get_launch(32)
+        assert ls["stages"] >= 1 and lb["stages"] >= 1
+        assert (ls["lanes_per_row"], ls["cols_per_lane"]) == (lb["lanes_per_row"],
+                                                               lb["cols_per_lane"])
+        small.moments(16, 32, 7)  # plans and runs the smaller layout
+        batch.launch()
+        np.testing.assert_array_equal(batch.eta(0), first[0])
+        np.testing.assert_array_equal(batch.eta(1), first[1])
+        small.check_device_error()
+    for c in big:
+        c.close()
