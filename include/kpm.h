@@ -391,19 +391,21 @@ int kpm_moments_plane_wave(kpm_ctx *ctx, int32_t M, int32_t R, int32_t nx, int32
  * problem is the KPM-DOS of Sec. "Problem Description" and Fig. 5, run as
  * in kpm_moments): count independent problems (each its own context, all on the
  * same device and of the same precision), problem p with M[p] moments
- * (even, >= 2), R[p] random-phase vectors from seed[p] (R[p] a power of two
- * <= 64, else KPM_EUNSUPPORTED); eta[p] is host double[R[p]][M[p]].
- * All problems advance together.  Problems whose R[p] round to the same
- * lane shape (the same power of two) form a class; every sweep step is, per
- * class, one batched launch covering the class's problems still running
- * plus one batched eta reduction, and the whole schedule is captured into a
- * CUDA graph and run as one graph launch.  Complex float classes of width
- * 8..64 whose contexts all have gather lists with one chunk height run the
- * staged kernel (kpm_launch.stages) over the class's chunks, the others the
- * register-path kernel.  A class takes the launch shape and stage count
- * that its first problem's context (the one with the largest M) uses for
- * the width -- the default, or what kpm_autotune / kpm_set_launch chose --
- * with fewer stages where the class's widest gather list needs it.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
+ * (even, >= 2), R[p] >= 1 random-phase vectors from seed[p]; eta[p] is host
+ * double[R[p]][M[p]].  All problems advance together.  Each problem's R[p]
+ * columns are split into column blocks of power-of-two widths up to 64,
+ * widest first (one block where R[p] is such a power), as kpm_moments splits
+ * them; the blocks of one width, across all problems, form a class.  Every
+ * sweep step is, per class, one batched launch covering the class's blocks
+ * still running plus one batched eta reduction, and the whole schedule is
+ * captured into a CUDA graph and run as one graph launch.  Complex float
+ * classes of width 8..64 whose contexts all have gather lists with one chunk
+ * height run the staged kernel (kpm_launch.stages) over the class's chunks,
+ * the others the register-path kernel.  A class takes the launch shape and
+ * stage count that the context of its first block (the one with the largest
+ * M) uses for the width -- the default, or what kpm_autotune /
+ * kpm_set_launch chose -- with fewer stages where the class's widest gather
+ * list needs it.  Synchronous.  Equivalent to kpm_batch_create + kpm_batch_launch
  * + kpm_batch_eta for every problem + kpm_batch_destroy. */
 int kpm_moments_batch(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const int32_t *R,
                       const uint64_t *seed, double *const *eta, void *stream);

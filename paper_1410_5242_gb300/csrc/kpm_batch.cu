@@ -1,14 +1,16 @@
 // Ensembles of independent KPM-DOS problems (disorder realisations of
 // different sizes, moment counts M and block widths R) advanced together.
 //
-// Problems are grouped into classes of equal block width R.  Every sweep
+// Each problem's R columns are split into column blocks of power-of-two
+// widths up to 64 (one block where R is such a power), and the blocks --
+// the units below -- are grouped into classes of equal width.  Every sweep
 // step is, per class, one launch of batch_sweep_kernel over the tiles of
-// the class's problems still running at that step (sorted by M, so the
+// the class's units still running at that step (sorted by M, so the
 // running set is always a prefix; blocks stride over the concatenated tile
 // list and keep their eta terms in registers for as long as they stay in
-// one problem), followed by one launch of batch_reduce_kernel that turns
+// one unit), followed by one launch of batch_reduce_kernel that turns
 // the per-block eta partials of the step into eta_{2m}, eta_{2m+1} of every
-// running problem of the class.  The whole schedule (start
+// running unit's columns.  The whole schedule (start
 // vectors, the initial sweep, the M/2 - 1 sweeps of the longest problem)
 // is captured once into a CUDA graph and replayed with one graph launch.
 #define KPM_SWEEP_MAX_THREADS 512
@@ -34,17 +36,18 @@ constexpr int kBatchThreads = 128;  // 4 warps per block
 constexpr int kBatchTileGroups[2] = {4, 1};  // [precision]
 constexpr int kReduceThreads = 128;
 
+// One unit: columns col0 .. col0 + RB - 1 of a problem's vector block.
 struct BatchProblem {
     const int64_t *chunk_ptr;
     const int32_t *chunk_len;
     const int32_t *col;
     const void *val;
     void *buf0, *buf1;  // nu_0 lives in buf0; sweep s reads buf[s & 1], writes the other
-    double *partial;    // [3 * RB][n_tiles]
-    double *eta;        // [RB][M]
+    double *partial;    // [3 * RB][slots], the unit's own
+    double *eta;        // [RB][M]: rows col0 .. of the problem's eta
     int64_t n_pad, n_tiles, tile_rows;
-    int64_t slots;  // min(grid, n_tiles): blocks that touch the problem in a step
-    int32_t log2C, ld, RB, shape, tile_groups, M;
+    int64_t slots;  // min(grid, n_tiles): blocks that touch the unit in a step
+    int32_t log2C, ld, RB, shape, tile_groups, M, col0;  // ld: the problem's row stride
 };
 
 // L2 prefetch of a run's first tile (the later ones are prefetched one tile
@@ -107,12 +110,12 @@ __device__ __forceinline__ void batch_run(const BatchProblem &bp, int64_t t0, in
     p.n_pad = bp.n_pad;
     p.log2C = bp.log2C;
     p.ld = bp.ld;
-    p.col0 = 0;
+    p.col0 = bp.col0;
     p.tile_groups = bp.tile_groups;
     p.with_imag = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int tl = lane % T, team = lane / T;
-    const int64_t cbase = (int64_t)tl * Pieces<Real, E>::EV;
+    const int64_t cbase = (int64_t)p.col0 + tl * Pieces<Real, E>::EV;
     const Real *__restrict__ val = static_cast<const Real *>(p.val);
     const Real *__restrict__ V = static_cast<const Real *>(p.V);
     Real *W = static_cast<Real *>(p.W);
@@ -168,8 +171,8 @@ __global__ void __launch_bounds__(KPM_SWEEP_MAX_THREADS, KPM_SWEEP_MIN_BLOCKS)
     }
 }
 
-// One block per (running problem, quantity q in {<V|V>, Re<W|V>}, column r):
-// sums the problem's per-block partials of this step in slot order.
+// One block per (running unit, quantity q in {<V|V>, Re<W|V>}, column r):
+// sums the unit's per-block partials of this step in slot order.
 __global__ void batch_reduce_kernel(const BatchProblem *__restrict__ probs, int n_active, int step)
 {
     __shared__ double red[kReduceThreads];
@@ -219,15 +222,14 @@ struct StagedClass {
 };
 
 struct kpm_batch {
-    int device = 0, precision = 0, count = 0, steps = 0, grid = 0;
+    int device = 0, precision = 0, count = 0, n_units = 0, steps = 0, grid = 0;
     std::vector<StagedClass> staged;       // per class
-    StagedProblem *d_sprobs = nullptr;     // per sorted problem (staged classes)
+    StagedProblem *d_sprobs = nullptr;     // per sorted unit (staged classes)
     std::vector<kpm_ctx *> ctx;      // original order
     std::vector<int> M, R;           // original order
-    std::vector<int> n_active;       // [step][class]: running problems of each class
-    std::vector<int> class_first;    // first sorted problem of each class (+ count)
+    std::vector<int> n_active;       // [step][class]: running units of each class
+    std::vector<int> class_first;    // first sorted unit of each class (+ n_units)
     std::vector<int> class_prefix;   // offset of each class's tile prefix array
-    std::vector<int> sorted_to_orig;
     BatchProblem *d_probs = nullptr;
     int64_t *d_prefix = nullptr;
     cudaStream_t capture = nullptr;
@@ -273,8 +275,6 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             return KPM_EINVAL;
         if (ctx[p]->n_halo > 0)
             return KPM_EUNSUPPORTED;  // a part runs its sweeps with halo exchanges
-        if (R[p] > 64 || (R[p] & (R[p] - 1)))
-            return KPM_EUNSUPPORTED;
         if (ctx[p]->device != ctx[0]->device || ctx[p]->precision != ctx[0]->precision)
             return KPM_EINVAL;
         for (int32_t q = 0; q < p; q++)
@@ -298,48 +298,62 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     if (!guard.ok)
         return fail(KPM_ECUDA);
 
-    // Problems grouped by lane shape (one batched launch per shape class and
-    // step: a launch whose blocks all run the same (T, E) loop keeps the SMs
+    // Units: each problem's columns in power-of-two blocks of at most 64,
+    // widest first, as the single-problem sweeps split them (a block's first
+    // column is a multiple of its width, which keeps its accesses aligned).
+    struct Unit {
+        int p, col0, RB, shape;  // shape = log2(RB)
+    };
+    std::vector<Unit> units;
+    for (int p = 0; p < count; p++) {
+        int col0 = 0;
+        for (int RB : column_widths(R[p], 64)) {
+            int shape = 0;
+            while ((1 << shape) < RB)
+                shape++;
+            units.push_back({p, col0, RB, shape});
+            col0 += RB;
+        }
+    }
+    const int n_units = (int)units.size();
+    b->n_units = n_units;
+    // Units grouped by width (one batched launch per width class and step:
+    // a launch whose blocks all run the same (T, E) loop keeps the SMs
     // evenly loaded; mixing widths in one launch ran 12% slower on the
     // 64-lattice ensemble), each class by decreasing M, so that the running
     // set of a class is a prefix of it.
-    auto shape_of = [&](int p) {
-        int s = 0;
-        while ((1 << s) < R[p])
-            s++;
-        return s;
-    };
-    std::vector<int> order(count);
+    std::vector<int> order(n_units);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (shape_of(x) != shape_of(y))
-            return shape_of(x) < shape_of(y);
-        return M[x] > M[y];
+        if (units[x].shape != units[y].shape)
+            return units[x].shape < units[y].shape;
+        return M[units[x].p] > M[units[y].p];
     });
-    b->sorted_to_orig = order;
+    auto unit_ctx = [&](int i) { return ctx[units[order[i]].p]; };  // i: sorted unit
     const bool fp64 = b->precision == KPM_PREC_FP64;
     const int sd = fp64 ? 16 : 8;
     b->grid = fp64 ? batch_grid<double>(ctx[0]->n_sm) : batch_grid<float>(ctx[0]->n_sm);
     if (b->grid < 1)
         return fail(KPM_ECUDA);
-    std::vector<BatchProblem> probs(count);
-    std::vector<StagedProblem> sprobs(count);
-    std::vector<int64_t> prefix;  // per class: tile prefix over its problems (count_c + 1)
+    std::vector<BatchProblem> probs(n_units);
+    std::vector<StagedProblem> sprobs(n_units);
+    std::vector<int64_t> prefix;  // per class: tile prefix over its units (count_c + 1)
     double bytes = 0.0;
-    for (int i = 0; i < count; i++)
-        if (i == 0 || shape_of(order[i]) != shape_of(order[i - 1]))
+    for (int i = 0; i < n_units; i++)
+        if (i == 0 || units[order[i]].shape != units[order[i - 1]].shape)
             b->class_first.push_back(i);
-    b->class_first.push_back(count);
-    // Complex float classes run the staged kernel when every problem has
-    // gather lists with one chunk height and the stages fit.  The class takes
-    // the lane shape and stage count its first problem's context uses for
-    // width R (as tuned by kpm_autotune or kpm_set_launch, else the default);
-    // a register-path choice there keeps the class on the register path.
+    b->class_first.push_back(n_units);
+    // Complex float classes run the staged kernel when every unit's context
+    // has gather lists with one chunk height and the stages fit.  The class
+    // takes the lane shape and stage count its first unit's context uses for
+    // the width (as tuned by kpm_autotune or kpm_set_launch, else the
+    // default); a register-path choice there keeps the class on the register
+    // path.
     b->staged.assign(b->class_first.size() - 1, StagedClass());
     for (size_t cl = 0; cl + 1 < b->class_first.size() && !fp64; cl++) {
         const int first = b->class_first[cl], last = b->class_first[cl + 1];
-        const int RB = R[order[first]];
-        const kpm_ctx *c0 = ctx[order[first]];
+        const int RB = units[order[first]].RB;
+        const kpm_ctx *c0 = unit_ctx(first);
         auto it = c0->shapes.find(RB);
         const LaunchShape sh = it != c0->shapes.end() ? it->second : default_shape(c0, RB);
         StagedClass &sc = b->staged[cl];
@@ -349,13 +363,13 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
                   staged_shape_supported(sc.T, sc.E, false);
         int u_max = 0, l_max = 0;
         for (int i = first; i < last && ok; i++) {
-            const kpm_ctx *c = ctx[order[i]];
+            const kpm_ctx *c = unit_ctx(i);
             ok = c->gather_ok && c->C == c0->C && c->half_ok == c0->half_ok;
             u_max = std::max(u_max, c->u_max);
             l_max = std::max(l_max, c->l_max);
         }
         // the class's stage count, or fewer where the wider gather lists of
-        // other problems (or the problem table) do not leave room; the old
+        // other units (or the unit table) do not leave room; the old
         // W rows travel with the stages where that keeps the blocks per SM
         bool fits = false;
         const int vs = staged_value_bytes(false, c0->half_ok);
@@ -381,35 +395,55 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         sc.on = ok;
         sc.half = ok && c0->half_ok;
     }
-    for (int i = 0; i < count; i++) {
+    // Pass 1: every unit's tiles and partial slots, and its partials'
+    // offset within its context's partial buffer (the units of a problem
+    // share its context's buffers: V and W at their own columns, eta at
+    // their own rows, partials one after the other).
+    auto class_of = [&](int i) {
         int cl = 0;
         while (b->class_first[cl + 1] <= i)
             cl++;
+        return cl;
+    };
+    std::vector<int64_t> u_tiles(n_units), u_rows(n_units), u_slots(n_units), u_poff(n_units);
+    std::vector<int64_t> p_partial(count, 0);
+    for (int i = 0; i < n_units; i++) {
+        const Unit &u = units[order[i]];
+        const StagedClass &sc = b->staged[class_of(i)];
+        const kpm_ctx *c = ctx[u.p];
+        const int T = fp64 ? batch_team<double>(u.shape) : batch_team<float>(u.shape);
+        const int rows_per_group = (kBatchThreads / 32) * (32 / T);
+        const int tg = kBatchTileGroups[fp64 ? 0 : 1];
+        u_rows[i] = sc.on ? c->C : (int64_t)rows_per_group * tg;
+        u_tiles[i] = (c->n_pad + u_rows[i] - 1) / u_rows[i];
+        u_slots[i] = std::min<int64_t>(sc.on ? sc.grid : b->grid, u_tiles[i]);
+        u_poff[i] = p_partial[u.p];
+        p_partial[u.p] += 3 * (int64_t)u.RB * u_slots[i];
+    }
+    for (int p = 0; p < count; p++) {
+        kpm_ctx *c = ctx[p];
+        int rc = ensure_vectors(c, R[p]);
+        if (!rc)
+            rc = ensure_partial(c, p_partial[p]);
+        if (!rc)
+            rc = ensure_eta(c, (int64_t)M[p] * R[p]);
+        if (rc)
+            return fail(rc);
+        const double mat = (double)c->nnz * (sd + 4);
+        bytes += mat + 2.0 * R[p] * sd * c->n + (M[p] / 2 - 1) * (mat + 3.0 * R[p] * sd * c->n);
+        b->info.sweeps += M[p] / 2;
+    }
+    // Pass 2: the unit tables, with the buffers in place.
+    for (int i = 0; i < n_units; i++) {
+        const int cl = class_of(i);
         if (i == b->class_first[cl]) {
             b->class_prefix.push_back((int)prefix.size());
             prefix.push_back(0);
         }
         const StagedClass &sc = b->staged[cl];
-        const int p = order[i];
+        const Unit &u = units[order[i]];
+        const int p = u.p;
         kpm_ctx *c = ctx[p];
-        int rc = ensure_vectors(c, R[p]);
-        if (rc)
-            return fail(rc);
-        int shape = 0;
-        while ((1 << shape) < R[p])
-            shape++;
-        const int T = fp64 ? batch_team<double>(shape) : batch_team<float>(shape);
-        const int rows_per_group = (kBatchThreads / 32) * (32 / T);
-        const int tg = kBatchTileGroups[fp64 ? 0 : 1];
-        const int64_t tile_rows = sc.on ? c->C : (int64_t)rows_per_group * tg;
-        const int64_t n_tiles = (c->n_pad + tile_rows - 1) / tile_rows;
-        const int64_t slots = std::min<int64_t>(sc.on ? sc.grid : b->grid, n_tiles);
-        rc = ensure_partial(c, 3 * (int64_t)R[p] * slots);
-        if (rc)
-            return fail(rc);
-        rc = ensure_eta(c, (int64_t)M[p] * R[p]);
-        if (rc)
-            return fail(rc);
         BatchProblem &bp = probs[i];
         bp.chunk_ptr = c->d_chunk_ptr;
         bp.chunk_len = c->d_chunk_len;
@@ -417,18 +451,19 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         bp.val = c->d_val;
         bp.buf0 = c->d_V;
         bp.buf1 = c->d_W;
-        bp.partial = c->d_partial;
-        bp.eta = c->d_eta;
+        bp.partial = c->d_partial + u_poff[i];
+        bp.eta = c->d_eta + (int64_t)u.col0 * M[p];
         bp.n_pad = c->n_pad;
-        bp.n_tiles = n_tiles;
-        bp.tile_rows = tile_rows;
-        bp.slots = slots;
+        bp.n_tiles = u_tiles[i];
+        bp.tile_rows = u_rows[i];
+        bp.slots = u_slots[i];
         bp.log2C = c->log2C;
         bp.ld = (int32_t)block_ld(c, R[p]);
-        bp.RB = R[p];
-        bp.shape = shape;
-        bp.tile_groups = tg;
+        bp.RB = u.RB;
+        bp.shape = u.shape;
+        bp.tile_groups = kBatchTileGroups[fp64 ? 0 : 1];
         bp.M = M[p];
+        bp.col0 = u.col0;
         if (sc.on) {
             StagedProblem &sp = sprobs[i];
             sp.rec = c->d_rec;
@@ -437,40 +472,37 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             sp.val = c->d_val_staged;
             sp.buf[0] = c->d_V;
             sp.buf[1] = c->d_W;
-            sp.partial = c->d_partial;  // [3*RB][slots]
+            sp.partial = bp.partial;  // [3*RB][slots]
             sp.tile0 = prefix.back();
-            sp.n_tiles = n_tiles;
+            sp.n_tiles = u_tiles[i];
             sp.ps = 1;
-            sp.qs = slots;
+            sp.qs = u_slots[i];
             sp.ld = bp.ld;
-            sp.col0 = 0;
+            sp.col0 = u.col0;
             sp.rows = c->n_pad + c->n_halo;
             sp.entries = c->n_staged;
             sp.n_ovf = c->n_ovf;
         }
-        prefix.push_back(prefix.back() + n_tiles);
-        const double mat = (double)c->nnz * (sd + 4);
-        bytes += mat + 2.0 * R[p] * sd * c->n + (M[p] / 2 - 1) * (mat + 3.0 * R[p] * sd * c->n);
-        b->info.sweeps += M[p] / 2;
+        prefix.push_back(prefix.back() + u_tiles[i]);
     }
     b->steps = 0;
-    for (int i = 0; i < count; i++)
-        b->steps = std::max(b->steps, M[order[i]] / 2);
+    for (int p = 0; p < count; p++)
+        b->steps = std::max(b->steps, M[p] / 2);
     const int n_classes = (int)b->class_first.size() - 1;
     b->n_active.assign((size_t)b->steps * n_classes, 0);
     for (int cl = 0; cl < n_classes; cl++)
         for (int s = 0; s < b->steps; s++) {
             int k = b->class_first[cl];
-            while (k < b->class_first[cl + 1] && M[order[k]] / 2 > s)
+            while (k < b->class_first[cl + 1] && M[units[order[k]].p] / 2 > s)
                 k++;
             b->n_active[(size_t)s * n_classes + cl] = k - b->class_first[cl];
         }
 
-    b->d_probs = (BatchProblem *)dev_alloc(ctx[0], sizeof(BatchProblem) * count);
+    b->d_probs = (BatchProblem *)dev_alloc(ctx[0], sizeof(BatchProblem) * n_units);
     b->d_prefix = (int64_t *)dev_alloc(ctx[0], sizeof(int64_t) * prefix.size());
     if (!b->d_probs || !b->d_prefix)
         return fail(KPM_ENOMEM);
-    if (cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblem) * count,
+    if (cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblem) * n_units,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int64_t) * prefix.size(),
                    cudaMemcpyHostToDevice) != cudaSuccess)
@@ -479,10 +511,10 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
     for (const StagedClass &sc : b->staged)
         any_staged = any_staged || sc.on;
     if (any_staged) {
-        b->d_sprobs = (StagedProblem *)dev_alloc(ctx[0], sizeof(StagedProblem) * count);
+        b->d_sprobs = (StagedProblem *)dev_alloc(ctx[0], sizeof(StagedProblem) * n_units);
         if (!b->d_sprobs)
             return fail(KPM_ENOMEM);
-        if (cudaMemcpy(b->d_sprobs, sprobs.data(), sizeof(StagedProblem) * count,
+        if (cudaMemcpy(b->d_sprobs, sprobs.data(), sizeof(StagedProblem) * n_units,
                        cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(KPM_ECUDA);
     }
@@ -495,9 +527,8 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
         return fail(KPM_ECUDA);
     int rc = KPM_OK;
     int64_t launches = 0;
-    for (int i = 0; i < count && rc == KPM_OK; i++) {
-        const int p = order[i];
-        rc = launch_phases(ctx[p], probs[i].buf0, R[p], seed[p], b->capture);
+    for (int p = 0; p < count && rc == KPM_OK; p++) {
+        rc = launch_phases(ctx[p], ctx[p]->d_V, R[p], seed[p], b->capture);
         launches++;
     }
     const size_t smem = (size_t)(kBatchThreads / 32) * 3 * 64 * sizeof(double);
@@ -512,12 +543,12 @@ int kpm_batch_create(kpm_ctx *const *ctx, int32_t count, const int32_t *M, const
             const int64_t *cpre = b->d_prefix + b->class_prefix[cl];
             const StagedClass &sc = b->staged[cl];
             if (sc.on) {
-                // the running problems are a prefix of the class: a table of na
+                // the running units are a prefix of the class: a table of na
                 StagedParams q{};
                 q.probs = b->d_sprobs + b->class_first[cl];
                 q.n_probs = na;
                 q.parity = s & 1;
-                q.C = ctx[order[b->class_first[cl]]]->C;
+                q.C = unit_ctx(b->class_first[cl])->C;
                 q.stages = sc.L.stages;
                 q.with_imag = 0;
                 q.init = s == 0 ? 1 : 0;

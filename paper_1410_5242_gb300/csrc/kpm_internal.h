@@ -281,6 +281,8 @@ namespace kpm {
 void *dev_alloc(kpm_ctx *c, size_t bytes);
 void dev_free(kpm_ctx *c, void *p);
 int64_t block_ld(const kpm_ctx *c, int R);
+// R split into power-of-two column blocks <= cap, widest first.
+std::vector<int> column_widths(int R, int cap);
 int ensure_vectors(kpm_ctx *c, int R);
 int ensure_partial(kpm_ctx *c, int64_t doubles);
 int ensure_eta(kpm_ctx *c, int64_t doubles);

@@ -92,10 +92,9 @@ def test_batch_rejects_bad_requests(kpm):
     probs = problems()[:2]
     ctxs = contexts(kpm, probs, 1)
     c0, c1 = ctxs[0][0], ctxs[1][0]
-    for Ms, Rs, cs, status in (([64, 30], [8, 24], [c0, c1], kpm.KPM_EUNSUPPORTED),
+    for Ms, Rs, cs, status in (([64, 30], [8, 0], [c0, c1], kpm.KPM_EINVAL),
                                ([64, 31], [8, 8], [c0, c1], kpm.KPM_EINVAL),
-                               ([64, 30], [8, 8], [c0, c0], kpm.KPM_EINVAL),
-                               ([64, 30], [8, 128], [c0, c1], kpm.KPM_EUNSUPPORTED)):
+                               ([64, 30], [8, 8], [c0, c0], kpm.KPM_EINVAL)):
         with pytest.raises(kpm.KPMError) as e:
             kpm.moments_batch(cs, Ms, Rs, [1, 2])
         assert e.value.status == status
@@ -105,6 +104,63 @@ def test_batch_rejects_bad_requests(kpm):
         with pytest.raises(kpm.KPMError) as e:
             kpm.moments_batch([c0, c64], [8, 8], [8, 8], [1, 2])
         assert e.value.status == kpm.KPM_EINVAL
+    for c, *_ in ctxs:
+        c.close()
+
+
+def widths(R):
+    """Power-of-two column blocks of at most 64, widest first."""
+    out, rest, w = [], R, 64
+    while rest:
+        while rest >= w:
+            out.append(w)
+            rest -= w
+        w //= 2
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_any_block_width(kpm, orc, prec):
+    """Block widths that are not a power of two, or above 64, are split into
+    column blocks that join the classes of their widths (two blocks of one
+    problem in one class where R = 128): every problem's moments must equal
+    the single-problem path's, which splits the same way, and the oracle's
+    on its first, middle and last vectors."""
+    probs = [
+        (ham.ti_hamiltonian(6, 5, 4, gamma=1.0, seed=31), 40, 48, 41),
+        (ham.ti_hamiltonian(5, 5, 5, gamma=0.5, seed=32), 24, 7, 42),
+        (ham.ti_hamiltonian(4, 6, 5, gamma=2.0, seed=33), 32, 100, 43),
+        (ham.ti_hamiltonian(7, 4, 3, gamma=1.5, seed=34), 16, 128, 44),
+        (ham.ti_hamiltonian(3, 3, 4, gamma=0.7, seed=35), 12, 3, 45),
+        (ham.ti_hamiltonian(4, 4, 4, gamma=1.0, seed=36), 20, 16, 46),
+    ]
+    ctxs = contexts(kpm, probs, prec)
+    Ms, Rs, seeds = [p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs]
+    with kpm.Batch([c for c, *_ in ctxs], Ms, Rs, seeds) as batch:
+        info = batch.info()
+        blocks = {}  # width -> longest M among its blocks
+        for M, R in zip(Ms, Rs):
+            for w in widths(R):
+                blocks[w] = max(blocks.get(w, 0), M // 2)
+        assert info["count"] == len(probs) and info["classes"] == len(blocks)
+        assert info["kernel_launches"] == len(probs) + 2 * sum(blocks.values())
+        assert info["sweeps"] == sum(M // 2 for M in Ms)
+        if prec == 1:
+            assert info["staged_classes"] == sum(1 for w in blocks if w >= 8)
+        batch.launch()
+        etas = [batch.eta(p) for p in range(len(probs))]
+    for (ctx, h, a, b), (_, M, R, seed), eta in zip(ctxs, probs, etas):
+        assert eta.shape == (R, M)
+        single = ctx.moments(M, R, seed)
+        cols = sorted({0, R // 2, R - 1})
+        ref, _ = orc.moments(h, a, b, M, seed, cols)
+        eta0 = ref[:, :1]
+        if prec == 0:
+            assert np.all(np.abs(eta - single) <= 1e-12 * np.abs(single[:, :1]))
+            assert np.all(np.abs(eta[cols] - ref) <= 1e-10 * eta0)
+        else:
+            assert np.abs(kpm.eta_to_mu(eta) - kpm.eta_to_mu(single)).max() <= 1e-6
+            assert np.abs(kpm.eta_to_mu(eta[cols]) - orc.eta_to_mu(ref)).max() <= 1e-5
     for c, *_ in ctxs:
         c.close()
 
