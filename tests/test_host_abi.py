@@ -208,6 +208,25 @@ def test_invalid_input_is_rejected(kpm):
         kpm.scale_from_bounds(2.0, 1.0)
 
 
+def test_empty_matrix_and_too_few_planes_are_rejected(kpm):
+    """n = 0 has no spectrum to expand (every call takes n >= 1), and a
+    partition needs at least one plane of align rows per part."""
+    empty = {"n": 0, "row_ptr": np.zeros(1, dtype=np.int64), "col": np.zeros(0, dtype=np.int32),
+             "val": np.zeros(0, dtype=np.complex128)}
+    for call in (lambda: kpm.gershgorin(empty), lambda: kpm.lanczos_bounds(empty),
+                 lambda: kpm.sell_build(empty, 0.1, 0.0), lambda: kpm.gather_build(empty, 0.1, 0.0),
+                 lambda: kpm.staged_build(empty, 0.1, 0.0, "half32"),
+                 lambda: kpm.Context(empty, 0.1, 0.0, torch_allocator=False)):
+        with pytest.raises(kpm.KPMError) as e:
+            call()
+        assert e.value.status == kpm.KPM_EINVAL
+    for n, parts, align in ((0, 1, 1), (1, 2, 1), (12, 4, 4), (10, 2, 4)):
+        with pytest.raises(kpm.KPMError) as e:
+            kpm.partition_rows(n, parts, align=align)
+        assert e.value.status == kpm.KPM_EINVAL
+    assert list(kpm.partition_rows(12, 3, align=4)) == [0, 4, 8, 12]
+
+
 def test_create_rejects_bad_arguments_before_touching_a_device(kpm):
     h = ham.ti_hamiltonian(3, 3, 3)
     col = h["col"].copy()
