@@ -55,6 +55,16 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+    # the rest of the line's contract: same keys as the GPU arm, the CPU run
+    # described, no host-device bytes
+    for k in ("metric", "unit", "ms_per_step", "higher_is_better", "scaling", "vs_baseline",
+              "dtype", "data", "config", "e2e"):
+        assert k in d, k
+    assert d["steps"] == 1 and d["warmup"] == 3 and "workload" in d["config"]
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
 
 
 def _part_main(rank, world, port, out_dir):
