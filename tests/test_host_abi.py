@@ -208,6 +208,27 @@ def test_invalid_input_is_rejected(kpm):
         kpm.scale_from_bounds(2.0, 1.0)
 
 
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """The package's Python files without their built library: importing the
+    binding raises (no fallback path), in both the normal and the checked
+    build's selection."""
+    import shutil
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = tmp_path / "paper_1410_5242_gb300"
+    pkg.mkdir()
+    for f in ("__init__.py", "kpm.py", "build.py", "model.py", "partition.py"):
+        shutil.copy(os.path.join(root, "paper_1410_5242_gb300", f), pkg / f)
+    for check in ("0", "1"):
+        env = dict(os.environ, PYTHONPATH=str(tmp_path), KPM_CHECK=check)
+        r = subprocess.run([sys.executable, "-c", "import paper_1410_5242_gb300.kpm"],
+                           cwd=str(tmp_path), env=env, capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode != 0
+        assert "ImportError" in r.stderr and "is not built" in r.stderr, r.stderr[-500:]
+
+
 def test_empty_matrix_and_too_few_planes_are_rejected(kpm):
     """n = 0 has no spectrum to expand (every call takes n >= 1), and a
     partition needs at least one plane of align rows per part."""
